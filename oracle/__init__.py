@@ -1,0 +1,279 @@
+"""Plain FP64 CPU oracle for Stein ICP -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  It is the slow, obviously correct
+statement of the method (see `oracle.c` for the readings of the paper it
+follows) and shares no code with the CUDA library.
+
+Parity status of each function (what pins it in `tests/test_oracle.py`):
+  splitmix64_at   published splitmix64 output vectors
+  minibatch       selection invariants and per-index frequency
+  rotation        scipy's rotation from fixed-axis angles; orthogonality;
+                  central differences for the partial derivatives
+  nn / nn2        scipy cKDTree; exact duplicates and self-queries
+  icp_grad        central differences of L/2; single-point closed form
+  bandwidths      numpy.median; two-particle closed form
+  stein_phi       two-particle closed form (incl. wrap across +-pi);
+                  SVGD on a Gaussian target; K = 1 reduces to G
+  adam            closed form under a constant gradient
+  register        K = 1 recovery of a known pose on noise-free data
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (no FMA contraction, so x86 and Arm agree)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _setup(_lib)
+    return _lib
+
+
+_p = ctypes.c_void_p
+_i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("T", _i32), ("m", _i32), ("lr", _f64), ("beta1", _f64), ("beta2", _f64),
+                ("eps", _f64), ("seed", _u64), ("prior", _i32), ("mu", _f64 * 6),
+                ("sigma", _f64 * 3), ("kappa", _f64 * 3)]
+
+
+def _setup(L):
+    sig = {
+        "or_splitmix64_at": (_u64, [_u64, _u64]),
+        "or_mb_key": (_u64, [_u64, _i64, _i64]),
+        "or_minibatch": (ctypes.c_int, [_u64, _i64, _i64, _i32, _p]),
+        "or_rotation": (None, [_p, _p, _p]),
+        "or_nn": (None, [_p, _i64, _p, _i64, _p, _p]),
+        "or_nn2": (None, [_p, _i64, _p, _i64, _p, _p, _p]),
+        "or_icp_grad": (None, [_p, _i64, _p, _p, _i32, _p, _i32, _p, _p, _p]),
+        "or_icp_grad_given_nn": (None, [_p, _p, _p, _i32, _p, _i32, _p, _p]),
+        "or_log_post_grad": (None, [_p, _p, _i32, _f64, _i32, _p, _p, _p, _p]),
+        "or_median": (_f64, [_p, _i64]),
+        "or_bandwidths": (None, [_p, _i32, _p, _p]),
+        "or_stein_phi": (None, [_p, _p, _i32, _f64, _f64, _p]),
+        "or_adam": (None, [_p, _p, _p, _p, _i64, _i64, _f64, _f64, _f64, _f64]),
+        "or_moments": (None, [_p, _i32, _p, _p]),
+        "or_step": (None, [_p, _i64, _p, _i64, _p, _p, _p, _i32, _p, _i64, _p, _p, _p, _p]),
+        "or_register": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _p, _p, _p, _p]),
+        "or_num_threads": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64a(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass
+class Params:
+    """Run parameters (Sec. V: Adam step 0.01-0.03, minibatch 150-300)."""
+    T: int = 100
+    m: int = 100
+    lr: float = 0.01
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    seed: int = 0
+    prior: int = 0
+    mu: tuple = (0.0,) * 6
+    sigma: tuple = (1.0,) * 3
+    kappa: tuple = (1.0,) * 3
+
+    def c(self) -> _Params:
+        p = _Params()
+        p.T, p.m, p.lr, p.beta1, p.beta2, p.eps = self.T, self.m, self.lr, self.beta1, self.beta2, self.eps
+        p.seed, p.prior = self.seed & ((1 << 64) - 1), self.prior
+        p.mu[:] = list(self.mu)
+        p.sigma[:] = list(self.sigma)
+        p.kappa[:] = list(self.kappa)
+        return p
+
+
+def num_threads() -> int:
+    return _L().or_num_threads()
+
+
+def splitmix64_at(state: int, k: int) -> int:
+    return int(_L().or_splitmix64_at(state & ((1 << 64) - 1), k))
+
+
+def mb_key(seed: int, t: int, i: int) -> int:
+    return int(_L().or_mb_key(seed & ((1 << 64) - 1), t, i))
+
+
+def minibatch(seed: int, t: int, N: int, m: int) -> np.ndarray:
+    out = np.empty(m, np.int32)
+    rc = _L().or_minibatch(seed & ((1 << 64) - 1), t, N, m, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"or_minibatch rc={rc}")
+    return out
+
+
+def rotation(theta):
+    th = _f64a(theta)
+    R = np.empty(9)
+    dR = np.empty(27)
+    _L().or_rotation(_ptr(th), _ptr(R), _ptr(dR))
+    return R.reshape(3, 3), dR.reshape(3, 3, 3)
+
+
+def nn(ref, q):
+    ref, q = _f32(ref), _f64a(q)
+    n = q.shape[0]
+    idx = np.empty(n, np.int64)
+    d2 = np.empty(n)
+    _L().or_nn(_ptr(ref), ref.shape[0], _ptr(q), n, _ptr(idx), _ptr(d2))
+    return idx, d2
+
+
+def nn2(ref, q):
+    ref, q = _f32(ref), _f64a(q)
+    n = q.shape[0]
+    idx = np.empty(n, np.int64)
+    d2 = np.empty(n)
+    d2b = np.empty(n)
+    _L().or_nn2(_ptr(ref), ref.shape[0], _ptr(q), n, _ptr(idx), _ptr(d2), _ptr(d2b))
+    return idx, d2, d2b
+
+
+def transform(theta, pts):
+    """R(theta) p + u for each row of pts (float64 result)."""
+    R, _ = rotation(theta)
+    return np.asarray(pts, np.float64) @ R.T + np.asarray(theta[:3], np.float64)
+
+
+def icp_grad(ref, src, mb, theta):
+    ref, src = _f32(ref), _f32(src)
+    mb = np.ascontiguousarray(mb, np.int32)
+    th = _f64a(theta).reshape(-1, 6)
+    K, m = th.shape[0], mb.shape[0]
+    g = np.empty((K, 6))
+    nnk = np.empty((K, m), np.int64)
+    loss = np.empty(K)
+    _L().or_icp_grad(_ptr(ref), ref.shape[0], _ptr(src), _ptr(mb), m, _ptr(th), K, _ptr(g),
+                     _ptr(nnk), _ptr(loss))
+    return g, nnk, loss
+
+
+def icp_grad_given_nn(ref, src, mb, theta, nnk):
+    ref, src = _f32(ref), _f32(src)
+    mb = np.ascontiguousarray(mb, np.int32)
+    th = _f64a(theta).reshape(-1, 6)
+    K, m = th.shape[0], mb.shape[0]
+    nnk = np.ascontiguousarray(nnk, np.int64).reshape(K, m)
+    g = np.empty((K, 6))
+    _L().or_icp_grad_given_nn(_ptr(ref), _ptr(src), _ptr(mb), m, _ptr(th), K, _ptr(nnk), _ptr(g))
+    return g
+
+
+def log_post_grad(theta, gbar, N, prior=0, mu=(0,) * 6, sigma=(1,) * 3, kappa=(1,) * 3):
+    th = _f64a(theta).reshape(-1, 6)
+    gb = _f64a(gbar).reshape(-1, 6)
+    K = th.shape[0]
+    G = np.empty((K, 6))
+    _L().or_log_post_grad(_ptr(th), _ptr(gb), K, float(N), prior, _ptr(_f64a(mu)),
+                          _ptr(_f64a(sigma)), _ptr(_f64a(kappa)), _ptr(G))
+    return G
+
+
+def median(x) -> float:
+    x = _f64a(x).ravel()
+    return float(_L().or_median(_ptr(x), x.size))
+
+
+def bandwidths(theta):
+    th = _f64a(theta).reshape(-1, 6)
+    ht, hr = _f64(), _f64()
+    _L().or_bandwidths(_ptr(th), th.shape[0], ctypes.byref(ht), ctypes.byref(hr))
+    return ht.value, hr.value
+
+
+def stein_phi(theta, G, h_t, h_r):
+    th = _f64a(theta).reshape(-1, 6)
+    G = _f64a(G).reshape(-1, 6)
+    phi = np.empty_like(th)
+    _L().or_stein_phi(_ptr(th), _ptr(G), th.shape[0], float(h_t), float(h_r), _ptr(phi))
+    return phi
+
+
+def adam(x, mom, vel, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays x, mom, vel."""
+    for a in (x, mom, vel):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64a(g)
+    _L().or_adam(_ptr(x), _ptr(mom), _ptr(vel), _ptr(g), x.size, t, lr, beta1, beta2, eps)
+
+
+def moments(theta):
+    th = _f64a(theta).reshape(-1, 6)
+    mean = np.empty(6)
+    cov = np.empty(36)
+    _L().or_moments(_ptr(th), th.shape[0], _ptr(mean), _ptr(cov))
+    return mean, cov.reshape(6, 6)
+
+
+def step(ref, src, th, mom, vel, params: Params, t: int):
+    """Iteration t in place on th, mom, vel (float64 K x 6); returns the
+    iteration's gbar, G, phi and (h_t, h_r)."""
+    ref, src = _f32(ref), _f32(src)
+    for a in (th, mom, vel):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    K = th.shape[0]
+    gbar, G, phi, h = np.empty((K, 6)), np.empty((K, 6)), np.empty((K, 6)), np.empty(2)
+    p = params.c()
+    _L().or_step(_ptr(ref), ref.shape[0], _ptr(src), src.shape[0], _ptr(th), _ptr(mom), _ptr(vel),
+                 K, ctypes.byref(p), t, _ptr(gbar), _ptr(G), _ptr(phi), _ptr(h))
+    return dict(gbar=gbar, G=G, phi=phi, h=(h[0], h[1]))
+
+
+def register(ref, src, theta0, params: Params):
+    ref, src, th0 = _f32(ref), _f32(src), _f32(theta0).reshape(-1, 6)
+    K = th0.shape[0]
+    th = np.empty((K, 6))
+    mean = np.empty(6)
+    cov = np.empty(36)
+    p = params.c()
+    rc = _L().or_register(_ptr(ref), ref.shape[0], _ptr(src), src.shape[0], _ptr(th0), K,
+                          ctypes.byref(p), _ptr(th), _ptr(mean), _ptr(cov))
+    if rc != 0:
+        raise ValueError(f"or_register rc={rc}")
+    return th, mean, cov.reshape(6, 6)

@@ -1,0 +1,346 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix.
+
+None of these re-types the oracle's formula: each compares it with a library
+routine (scipy, numpy), a closed form, an invariant, published generator
+outputs, finite differences of an independently computed cost, or recovery
+of a known pose.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+import oracle as O
+from paper_2106_03287_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- minibatch RNG
+
+def test_splitmix64_published_vectors():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert [O.splitmix64_at(1234567, k) for k in range(1, 6)] == vals
+
+
+def test_mb_key_is_a_stream_of_a_stream():
+    for seed, t, i in [(0, 0, 0), (7, 3, 11), (2**63 + 5, 199, 99_999)]:
+        base = O.splitmix64_at(seed, t + 1)
+        assert O.mb_key(seed, t, i) == O.splitmix64_at(base, i + 1)
+
+
+@pytest.mark.parametrize("N,m", [(50, 10), (1000, 100), (777, 777), (10, 1)])
+def test_minibatch_is_the_m_smallest_keys(N, m):
+    for t in (0, 1, 57):
+        mb = O.minibatch(11, t, N, m)
+        assert mb.shape == (m,)
+        assert np.all(np.diff(mb) > 0) and mb.min() >= 0 and mb.max() < N
+        keys = np.array([O.mb_key(11, t, i) for i in range(N)], dtype=np.uint64)
+        assert len(np.unique(keys)) == N                 # keys of one iteration are distinct
+        sel = np.zeros(N, bool)
+        sel[mb] = True
+        if m < N:
+            assert keys[sel].max() < keys[~sel].min()
+
+
+def test_minibatch_rejects_bad_sizes():
+    with pytest.raises(ValueError):
+        O.minibatch(0, 0, 10, 11)
+    with pytest.raises(ValueError):
+        O.minibatch(0, 0, 10, 0)
+
+
+def test_minibatch_frequencies_are_uniform():
+    N, m, T = 40, 8, 3000
+    cnt = np.zeros(N)
+    for t in range(T):
+        cnt[O.minibatch(5, t, N, m)] += 1
+    expect = T * m / N
+    chi2 = ((cnt - expect) ** 2 / expect).sum()
+    assert chi2 < 80.0          # 39 dof: p(chi2 > 80) < 1e-4
+
+
+# ---------------------------------------------------------------- rotation
+
+def test_rotation_matches_scipy_fixed_axis_angles():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        ang = rng.uniform(-math.pi, math.pi, 3)
+        R, _ = O.rotation(np.r_[0, 0, 0, ang])
+        ref = Rotation.from_euler("xyz", ang).as_matrix()
+        assert np.abs(R - ref).max() < 1e-14
+        assert np.abs(R.T @ R - np.eye(3)).max() < 1e-14
+        assert abs(np.linalg.det(R) - 1) < 1e-14
+
+
+def test_rotation_single_axes_are_textbook():
+    a = 0.3
+    c, s = math.cos(a), math.sin(a)
+    Rx, _ = O.rotation([0, 0, 0, a, 0, 0])
+    Ry, _ = O.rotation([0, 0, 0, 0, a, 0])
+    Rz, _ = O.rotation([0, 0, 0, 0, 0, a])
+    assert np.allclose(Rx, [[1, 0, 0], [0, c, -s], [0, s, c]], atol=1e-15)
+    assert np.allclose(Ry, [[c, 0, s], [0, 1, 0], [-s, 0, c]], atol=1e-15)
+    assert np.allclose(Rz, [[c, -s, 0], [s, c, 0], [0, 0, 1]], atol=1e-15)
+
+
+def test_rotation_partials_central_differences():
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    for _ in range(20):
+        th = np.r_[rng.normal(size=3), rng.uniform(-3, 3, 3)]
+        _, dR = O.rotation(th)
+        for a in range(3):
+            tp, tm = th.copy(), th.copy()
+            tp[3 + a] += h
+            tm[3 + a] -= h
+            fd = (O.rotation(tp)[0] - O.rotation(tm)[0]) / (2 * h)
+            assert np.abs(fd - dR[a]).max() < 1e-9
+
+
+# ---------------------------------------------------------------- correspondences
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "box"])
+def test_nn_matches_kdtree(kind):
+    rng = np.random.default_rng(3)
+    if kind == "uniform":
+        ref = rng.uniform(-1, 1, (2000, 3))
+    elif kind == "clustered":
+        c = rng.uniform(-1, 1, (10, 3))
+        ref = c[rng.integers(0, 10, 2000)] + rng.normal(0, 0.01, (2000, 3))
+    else:
+        ref = synth.make_box_problem(3)["ref"]
+    ref = ref.astype(np.float32)
+    q = rng.uniform(-1.2, 1.2, (500, 3))
+    idx, d2 = O.nn(ref, q)
+    dd, ii = cKDTree(ref.astype(np.float64)).query(q, k=2)
+    unique = dd[:, 1] ** 2 - dd[:, 0] ** 2 > 1e-12
+    assert np.array_equal(idx[unique], ii[unique, 0])
+    assert np.allclose(d2, dd[:, 0] ** 2, rtol=1e-12, atol=1e-15)
+
+
+def test_nn_ties_go_to_lowest_index_and_self_queries_are_exact():
+    rng = np.random.default_rng(4)
+    base = rng.uniform(-1, 1, (100, 3)).astype(np.float32)
+    ref = np.concatenate([base, base[:50]])          # duplicates at indices 100..149
+    perm = rng.permutation(150)
+    ref = ref[perm]
+    idx, d2 = O.nn(ref, ref.astype(np.float64))
+    assert np.all(d2 == 0.0)
+    for r in range(150):
+        same = np.flatnonzero(np.all(ref == ref[r], axis=1))
+        assert idx[r] == same.min()
+
+
+# ---------------------------------------------------------------- ICP gradient
+
+def _half_loss(theta, ref, src_mb):
+    """L/2 of Eq. (icp-objective1) over a minibatch, with nearest neighbours
+    recomputed: scipy rotation + cKDTree, independent of the oracle."""
+    R = Rotation.from_euler("xyz", theta[3:]).as_matrix()
+    q = src_mb.astype(np.float64) @ R.T + theta[:3]
+    d, i = cKDTree(ref.astype(np.float64)).query(q)
+    return 0.5 * np.mean(d ** 2), i
+
+
+def test_icp_gradient_central_differences():
+    rng = np.random.default_rng(5)
+    ref = rng.uniform(-1, 1, (400, 3)).astype(np.float32)
+    src = rng.uniform(-1, 1, (200, 3)).astype(np.float32)
+    mb = O.minibatch(3, 0, 200, 60)
+    h = 1e-6
+    checked = 0
+    for trial in range(10):
+        th = np.r_[rng.normal(0, 0.1, 3), rng.uniform(-0.5, 0.5, 3)]
+        g, nnk, loss = O.icp_grad(ref, src, mb, th[None])
+        l0, i0 = _half_loss(th, ref, src[mb])
+        assert abs(loss[0] - l0) < 1e-12 * max(1.0, l0)
+        assert np.array_equal(nnk[0], i0)
+        fd = np.empty(6)
+        stable = True
+        for a in range(6):
+            tp, tm = th.copy(), th.copy()
+            tp[a] += h
+            tm[a] -= h
+            lp, ip = _half_loss(tp, ref, src[mb])
+            lm, im = _half_loss(tm, ref, src[mb])
+            stable &= np.array_equal(ip, i0) and np.array_equal(im, i0)
+            fd[a] = (lp - lm) / (2 * h)
+        if not stable:
+            continue                     # a correspondence switched inside +-h
+        checked += 1
+        assert np.abs(fd - g[0]).max() <= 1e-7 * np.abs(g[0]).max() + 1e-12
+    assert checked >= 5
+
+
+def test_icp_gradient_single_point_closed_form():
+    ref = np.array([[0.3, -0.2, 0.5]], np.float32)
+    src = np.array([[0.1, 0.4, -0.2]], np.float32)
+    th = np.array([0.05, -0.1, 0.2, 0.3, -0.4, 0.7])
+    g, nnk, _ = O.icp_grad(ref, src, np.array([0], np.int32), th[None])
+    R = Rotation.from_euler("xyz", th[3:]).as_matrix()
+    e = R @ src[0].astype(np.float64) + th[:3] - ref[0]
+    assert np.abs(g[0, :3] - e).max() < 1e-15
+    assert nnk[0, 0] == 0
+
+
+def test_icp_gradient_given_nn_matches_search():
+    d = synth.make_box_problem(6, K=4)
+    mb = O.minibatch(1, 0, d["src"].shape[0], 100)
+    th = d["particles"].astype(np.float64)
+    g, nnk, _ = O.icp_grad(d["ref"], d["src"], mb, th)
+    g2 = O.icp_grad_given_nn(d["ref"], d["src"], mb, th, nnk)
+    assert np.array_equal(g, g2)
+
+
+# ---------------------------------------------------------------- priors
+
+def test_prior_gradients_closed_form():
+    th = np.array([[0.1, 0.2, 0.3, 0.5, -0.5, 3.0]])
+    mu = np.array([0.0, 0.1, 0.2, 0.4, -0.4, -3.0])
+    sigma = np.array([0.5, 0.25, 2.0])
+    kappa = np.array([2.0, 3.0, 4.0])
+    gb = np.zeros((1, 6))
+    G = O.log_post_grad(th, gb, 1000, 1, mu, sigma, kappa)
+    assert np.allclose(G[0, :3], -(th[0, :3] - mu[:3]) / sigma, atol=1e-15)
+    assert np.allclose(G[0, 3:], -kappa * np.sin(th[0, 3:] - mu[3:]), atol=1e-15)
+    G0 = O.log_post_grad(th, np.ones((1, 6)), 1000, 0)
+    assert np.all(G0 == -1000.0)
+
+
+# ---------------------------------------------------------------- bandwidth & Stein
+
+def test_median_matches_numpy():
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 9, 100, 10_000):
+        x = rng.normal(size=n)
+        assert O.median(x) == np.median(x)
+
+
+def _two_particles(d_t, d_r):
+    th = np.zeros((2, 6))
+    th[0, :3] = [0.1, 0.2, -0.1]
+    th[1, :3] = th[0, :3] + d_t
+    th[0, 3:] = [3.1, 0.2, -0.3]
+    th[1, 3:] = th[0, 3:] + d_r
+    return th
+
+
+def test_two_particle_bandwidth_closed_form():
+    # K = 2: the four squared distances are {0, 0, d^2, d^2}: median d^2/2, h = d^2 / (2 ln 3)
+    d_t = np.array([0.03, -0.04, 0.12])
+    d_r = np.array([0.2, 0.1, -0.05])
+    h_t, h_r = O.bandwidths(_two_particles(d_t, d_r))
+    assert abs(h_t - (d_t @ d_t) / (2 * math.log(3))) < 1e-15
+    assert abs(h_r - (d_r @ d_r) / (2 * math.log(3))) < 1e-15
+
+
+@pytest.mark.parametrize("cross_pi", [False, True])
+def test_two_particle_stein_closed_form(cross_pi):
+    d_t = np.array([0.03, -0.04, 0.12])
+    d_r = np.array([0.2, 0.1, -0.05])
+    th = _two_particles(d_t, d_r)
+    if cross_pi:
+        th[1, 3] = -3.1           # roll difference 3.1 - (-3.1) wraps to 6.2 - 2 pi
+    rng = np.random.default_rng(8)
+    G = rng.normal(size=(2, 6))
+    h_t, h_r = O.bandwidths(th)
+    phi = O.stein_phi(th, G, h_t, h_r)
+    # with h = d^2/(2 ln 3) the off-diagonal kernel is exp(-2 ln 3) = 1/9
+    dw = th[0, 3:] - th[1, 3:]
+    dw = (dw + np.pi) % (2 * np.pi) - np.pi
+    d_r_eff = -dw
+    assert abs(h_r - (d_r_eff @ d_r_eff) / (2 * math.log(3))) < 1e-14
+    for i, j in ((0, 1), (1, 0)):
+        dt = th[i, :3] - th[j, :3]
+        dr = (th[i, 3:] - th[j, 3:] + np.pi) % (2 * np.pi) - np.pi
+        exp_t = 0.5 * (G[i, :3] + G[j, :3] / 9 + (2 / h_t) * dt / 9)
+        exp_r = 0.5 * (G[i, 3:] + G[j, 3:] / 9 + (2 / h_r) * dr / 9)
+        assert np.abs(phi[i, :3] - exp_t).max() < 1e-12 * max(1, np.abs(exp_t).max())
+        assert np.abs(phi[i, 3:] - exp_r).max() < 1e-12 * max(1, np.abs(exp_r).max())
+
+
+def test_single_particle_stein_is_the_gradient():
+    th = np.array([[0.1, 0.2, 0.3, 0.4, 0.5, 0.6]])
+    G = np.array([[1.0, -2.0, 3.0, -4.0, 5.0, -6.0]])
+    h_t, h_r = O.bandwidths(th)
+    assert h_t == 1.0 and h_r == 1.0
+    assert np.array_equal(O.stein_phi(th, G, h_t, h_r), G)
+
+
+def test_svgd_recovers_a_gaussian_target():
+    """SVGD with the median heuristic transports particles to a 6-D Gaussian:
+    mean within sigma/sqrt(K), per-axis spread within 10%."""
+    rng = np.random.default_rng(0)
+    K = 200
+    mu = np.array([0.3, -0.2, 0.1, 0.2, -0.1, 0.3])
+    sig = np.array([0.05, 0.1, 0.02, 0.1, 0.05, 0.2])
+    th = np.ascontiguousarray(rng.uniform(-0.5, 0.5, (K, 6)))
+    mom, vel = np.zeros_like(th), np.zeros_like(th)
+    for t in range(1, 801):
+        G = -(th - mu) / sig ** 2
+        phi = O.stein_phi(th, G, *O.bandwidths(th))
+        O.adam(th, mom, vel, -phi, t, 0.01)
+    assert np.all(np.abs(th.mean(0) - mu) < sig / math.sqrt(K))
+    ratio = th.std(0, ddof=1) / sig
+    assert np.all((ratio > 0.9) & (ratio < 1.1)), ratio
+
+
+# ---------------------------------------------------------------- Adam
+
+def test_adam_constant_gradient_closed_form():
+    # bias correction makes mhat = g and vhat = g^2 for a constant g, so each
+    # step is lr * g / (|g| + eps)
+    g = np.array([3.0, -1e-3, 2e-9, 0.0, -5.0, 1e-7])
+    x = np.zeros(6)
+    mom, vel = np.zeros(6), np.zeros(6)
+    for t in range(1, 11):
+        O.adam(x, mom, vel, g, t, 0.01)
+        assert np.allclose(x, -t * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- moments & whole run
+
+def test_moments_match_numpy():
+    rng = np.random.default_rng(9)
+    th = rng.normal(size=(37, 6))
+    mean, cov = O.moments(th)
+    assert np.allclose(mean, th.mean(0), atol=1e-15)
+    assert np.allclose(cov, np.cov(th.T), atol=1e-14)
+    m1, c1 = O.moments(th[:1])
+    assert np.array_equal(m1, th[0]) and np.all(c1 == 0)
+
+
+def test_single_particle_recovers_known_pose_noise_free():
+    """K = 1 reduces Stein ICP to SGD-ICP with Adam; on a noise-free box it
+    must land on the generating pose (1 mm, 0.05 deg)."""
+    d = synth.make_box_problem(0, K=1, noise=0.0)
+    th, mean, cov = O.register(d["ref"], d["src"], d["particles"], O.Params(T=300, m=100, seed=7))
+    err = th[0] - d["theta_true"]
+    assert np.abs(err[:3]).max() < 1e-3
+    assert np.abs(err[3:]).max() < math.radians(0.05)
+
+
+def test_run_is_deterministic_and_T0_returns_input():
+    d = synth.make_box_problem(1, M=300, N=100, K=5)
+    p = O.Params(T=5, m=20, seed=3)
+    a = O.register(d["ref"], d["src"], d["particles"], p)
+    b = O.register(d["ref"], d["src"], d["particles"], p)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    th, mean, _ = O.register(d["ref"], d["src"], d["particles"], O.Params(T=0, m=20))
+    assert np.array_equal(th, d["particles"].astype(np.float64))
+
+
+def test_step_loop_equals_register():
+    d = synth.make_box_problem(2, M=400, N=120, K=6)
+    p = O.Params(T=4, m=30, seed=9)
+    th = d["particles"].astype(np.float64).copy()
+    mom, vel = np.zeros_like(th), np.zeros_like(th)
+    for t in range(p.T):
+        O.step(d["ref"], d["src"], th, mom, vel, p, t)
+    th2, _, _ = O.register(d["ref"], d["src"], d["particles"], p)
+    assert np.array_equal(th, th2)
