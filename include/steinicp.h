@@ -1,0 +1,178 @@
+/*
+ * steinicp.h -- C ABI of the GB300 Stein ICP library (libsteinicp.so).
+ *
+ * Stein ICP (Afzal Maken, Ramos, Ott, "Stein ICP for Uncertainty Estimation
+ * in Point Cloud Matching") approximates the posterior over a 6-DoF rigid
+ * pose theta = (x, y, z, roll, pitch, yaw) that maps a source cloud S into a
+ * reference cloud R by K particles moved with Stein variational gradient
+ * descent.  Each iteration (Sec. IV, summary paragraph):
+ *   1. draws one minibatch of m source points (Sec. III-B),
+ *   2. transforms it by every particle, s' = R(theta) s + u (Sec. III-A),
+ *   3. finds each transformed point's nearest reference point
+ *      (Eq. correspondences),
+ *   4. averages the point-to-point cost gradient per particle
+ *      (Eqs. trans_gradient, rotation_gradient),
+ *   5. forms the Stein direction with RBF kernels whose bandwidths follow the
+ *      median heuristic (Eq. stein_icp_phi and the kernels after it),
+ *   6. moves the particles with Adam (Sec. V).
+ *
+ * Conventions shared by every call:
+ *  - Points are float32, row-major [n][3], metres.
+ *  - Particles are float32 [K][6] in the order (x, y, z, roll, pitch, yaw),
+ *    metres and radians; R = Rz(yaw) Ry(pitch) Rx(roll).
+ *  - `on_device` = 1: every array argument is a CUDA device pointer on the
+ *    context's device; 0: every array argument is a host pointer.  Either way
+ *    the call returns after its GPU work has finished (it synchronises the
+ *    context's stream), so outputs are ready on return.
+ *  - The caller owns every buffer it passes; the library only reads inputs and
+ *    writes outputs, and keeps no pointer to them after the call returns.  The
+ *    context owns its own device memory (reference structures, per-problem
+ *    state, scratch), released by sicp_destroy.
+ *  - Return value: SICP_OK (0) or a negative SICP_E* code.  On error the
+ *    outputs are left untouched where the error is found before any output is
+ *    written (all argument checks), and sicp_last_error() describes it.  No
+ *    error path traps the GPU.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef STEINICP_H
+#define STEINICP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SICP_OK 0
+#define SICP_EINVAL (-1)        /* bad size, pointer, mode or non-finite input */
+#define SICP_ENOREF (-2)        /* no reference cloud set on the context */
+#define SICP_ENOMEM (-3)        /* device allocation failed */
+#define SICP_ECUDA (-4)         /* a CUDA runtime call failed */
+#define SICP_ETIMEOUT (-5)      /* a bounded device wait gave up */
+#define SICP_ENOSURROGATE (-6)  /* surrogate mode without a trained surrogate */
+
+/* Nearest-neighbour search used for step 3. */
+#define SICP_NN_BRUTE_FP32 0    /* exhaustive FP32 scan of the whole reference */
+#define SICP_NN_BRUTE_BF16 1    /* exhaustive BF16 tensor-core distance tiles + exact FP32 refine */
+#define SICP_NN_GRID 2          /* uniform voxel grid, exact */
+#define SICP_NN_SURROGATE 3     /* learned closest-point field, then exact grid */
+
+typedef struct sicp_ctx sicp_ctx;
+
+/* Parameters of one registration run. */
+typedef struct sicp_params {
+    int32_t T;                 /* SVGD iterations (>= 0) */
+    int32_t m;                 /* minibatch size, 1 <= m <= N (Sec. III-B) */
+    float lr;                  /* Adam step size (Sec. V: 0.01 laser, 0.03 RGB-D) */
+    float beta1, beta2, eps;   /* Adam constants (0.9, 0.999, 1e-8 when zero) */
+    uint64_t seed;             /* minibatch stream seed */
+    int32_t nn_mode;           /* SICP_NN_* */
+    int32_t surrogate_iters;   /* SICP_NN_SURROGATE: iterations served by the surrogate */
+    int32_t prior;             /* 0 uniform; 1 Gaussian translation + von Mises rotation */
+    float prior_mu[6];         /* prior means (Eqs. trans_prior, rot_prior) */
+    float prior_sigma[3];      /* translation prior divisor, printed as a variance */
+    float prior_kappa[3];      /* von Mises concentrations */
+} sicp_params;
+
+/* Fill `p` with the defaults: T 100, m 100, lr 0.01, Adam (0.9, 0.999, 1e-8),
+ * seed 0, SICP_NN_GRID, uniform prior. */
+void sicp_default_params(sicp_params* p);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (NULL: the library creates its own non-blocking stream). */
+int sicp_create(sicp_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and all device memory it owns.  NULL is ignored. */
+void sicp_destroy(sicp_ctx* ctx);
+
+/* Message describing the last error on this context ("" if none). */
+const char* sicp_last_error(const sicp_ctx* ctx);
+
+/* Set the reference cloud R (Sec. III-A): xyz [M][3], M >= 1.  The library
+ * copies it and builds its search structures (the voxel grid of
+ * SICP_NN_GRID and the tile layout of the brute-force modes).
+ * cell_size > 0 fixes the grid cell edge in metres; 0 picks it from the
+ * cloud's extent and size.  Errors: SICP_EINVAL (M < 1, NULL, non-finite
+ * coordinate, cell_size < 0), SICP_ENOMEM, SICP_ECUDA. */
+int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_size, int on_device);
+
+/* One full Stein ICP run (Sec. IV summary): source S = src_xyz [N][3],
+ * initial particles particles_in [K][6], parameters `p`.  Outputs:
+ * particles_out [K][6] after T iterations; mean6 [6] and cov36 [6][6]
+ * (row-major, divisor K-1, zero for K = 1) of the final particles, both
+ * float64 (may be NULL).  T = 0 returns the input particles and their
+ * moments.  Errors: SICP_EINVAL (N < 1, K < 1, m outside [1, N], T < 0,
+ * bad mode, non-finite input), SICP_ENOREF, SICP_ENOSURROGATE, SICP_ENOMEM,
+ * SICP_ECUDA. */
+int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in,
+                  int32_t K, const sicp_params* p, float* particles_out, double* mean6,
+                  double* cov36, int on_device);
+
+/* ---- single steps of the iteration, for users who drive the loop ---- */
+
+/* Step 1 (Sec. III-B): the minibatches of iterations t0 .. t0+T-1 of the
+ * stream `seed`: out_idx [T][m] int32, each row the m source indices in
+ * [0, N) whose splitmix64 keys are smallest, in ascending index order.  The
+ * key of index i at iteration t is output i+1 of a splitmix64 stream whose
+ * state is output t+1 of a splitmix64 stream started at `seed`.
+ * Errors: SICP_EINVAL (N < 1, m outside [1, N], T < 1, t0 < 0). */
+int sicp_minibatch(sicp_ctx* ctx, uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
+                   int32_t* out_idx, int on_device);
+
+/* Step 3 (Eq. correspondences): nearest reference point of each query
+ * q [n][3] (float32) by search `mode` (SICP_NN_BRUTE_FP32, _BRUTE_BF16 or
+ * _GRID).  out_idx [n] int32 reference indices (ties: lowest index), out_d2
+ * [n] float32 squared distances (may be NULL).  n = 0 is a no-op.
+ * Errors: SICP_EINVAL, SICP_ENOREF, SICP_ECUDA. */
+int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out_idx,
+            float* out_d2, int on_device);
+
+/* Steps 2-4 (Eqs. trans_gradient, rotation_gradient): for K particles
+ * [K][6] and one minibatch mb [m] of indices into src_xyz [N][3], the mean
+ * gradient of L/2 per particle, out_gbar [K][6] float32, and optionally the
+ * correspondences out_nn [K][m] int32 (may be NULL).  Errors as sicp_nn. */
+int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t* mb, int32_t m,
+                  const float* particles, int32_t K, int32_t mode, float* out_gbar,
+                  int32_t* out_nn, int on_device);
+
+/* Steps 5-6 (Eq. stein_icp_phi, Sec. V): one Stein + Adam update in place.
+ * particles, adam_m, adam_v: [K][6] float32 (in/out; Adam moments start at
+ * zero); gbar [K][6] the mean gradients of this iteration; N the source
+ * size that scales them (G = -N gbar + grad log prior); t the 1-based Adam
+ * step; p supplies lr, Adam constants and the prior.  Optional outputs:
+ * out_phi [K][6] the Stein direction, out_h [2] the translation and rotation
+ * bandwidths.  Errors: SICP_EINVAL (K < 1, t < 1, N < 1). */
+int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_v,
+                    const float* gbar, int32_t K, int64_t N, int64_t t, const sicp_params* p,
+                    float* out_phi, float* out_h, int on_device);
+
+/* Mean [6] and covariance [6][6] (divisor K-1; zero for K = 1) of K particles
+ * [K][6], accumulated in float64.  Errors: SICP_EINVAL (K < 1). */
+int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
+                 int on_device);
+
+/* ---- measurement ---- */
+
+/* Work counters of the grid search (no counterpart in the paper; they state
+ * the algorithmic bytes a search moved).  Copies the counters accumulated
+ * since the previous call into out4 (may be NULL): queries, rows examined,
+ * row segments read (two cell offsets each), candidate points read (16 bytes
+ * each); then zeroes them and turns counting on (enable = 1) or off.
+ * Counting adds one warp-aggregated atomic per 32 queries. */
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out4);
+
+/* Kernel timing inside sicp_register (no counterpart in the paper).  With
+ * stride s > 0 the captured loop records CUDA events around the gradient and
+ * Stein kernels of every s-th iteration; their durations are summed on the
+ * host while the next run executes.  Copies the totals since the previous
+ * call into out4 (may be NULL): gradient-kernel ms, gradient launches timed,
+ * Stein-kernel ms, Stein launches timed; then zeroes them and sets the
+ * stride (0 = off).  Synchronises the context's stream. */
+int sicp_profile(sicp_ctx* ctx, int stride, double* out4);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEINICP_H */

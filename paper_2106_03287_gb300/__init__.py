@@ -1,0 +1,10 @@
+"""Stein ICP on GB300: the data-parallel hot path of Stein ICP (Afzal Maken,
+Ramos, Ott) as hand-written sm_103a CUDA kernels behind a C ABI
+(include/steinicp.h, libsteinicp.so), with this thin Python binding."""
+from .binding import (  # noqa: F401
+    EXPORTS, SICP_EINVAL, SICP_ENOMEM, SICP_ENOREF, SICP_ENOSURROGATE, SICP_ECUDA, SICP_ETIMEOUT,
+    SICP_NN_BRUTE_BF16, SICP_NN_BRUTE_FP32, SICP_NN_GRID, SICP_NN_SURROGATE, SICP_OK, SicpError,
+    LIB_PATH, lib, sicp_create, sicp_default_params, sicp_destroy, sicp_icp_grad, sicp_last_error,
+    sicp_minibatch, sicp_moments, sicp_nn, sicp_params, sicp_profile, sicp_register, sicp_set_reference,
+    sicp_stats, sicp_stein_adam,
+)

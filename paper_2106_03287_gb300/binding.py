@@ -1,0 +1,266 @@
+"""ctypes binding of libsteinicp (include/steinicp.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks shapes and dtypes, allocates outputs next
+to the inputs (numpy arrays for host calls, torch CUDA tensors for device
+calls) and passes raw pointers.  Host inputs are numpy arrays (on_device = 0);
+device inputs are torch CUDA tensors (on_device = 1).  A call whose C code
+returns an error raises SicpError with the library's message.
+
+There is no fallback: if the shared library is missing the import of this
+module still works, but the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsteinicp.so")
+
+SICP_OK = 0
+SICP_EINVAL = -1
+SICP_ENOREF = -2
+SICP_ENOMEM = -3
+SICP_ECUDA = -4
+SICP_ETIMEOUT = -5
+SICP_ENOSURROGATE = -6
+
+SICP_NN_BRUTE_FP32 = 0
+SICP_NN_BRUTE_BF16 = 1
+SICP_NN_GRID = 2
+SICP_NN_SURROGATE = 3
+
+_CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOSURROGATE"}
+
+# Every C entry point declared in include/steinicp.h.
+EXPORTS = (
+    "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
+    "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
+    "sicp_stats", "sicp_profile",
+)
+
+
+class SicpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sicp_params(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_int32), ("m", ctypes.c_int32),
+        ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+        ("nn_mode", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32), ("prior", ctypes.c_int32),
+        ("prior_mu", ctypes.c_float * 6), ("prior_sigma", ctypes.c_float * 3), ("prior_kappa", ctypes.c_float * 3),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded shared library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2106_03287_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U64, F32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+        pp = ctypes.POINTER(sicp_params)
+        sig = {
+            "sicp_default_params": (None, [pp]),
+            "sicp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, P]),
+            "sicp_destroy": (None, [P]),
+            "sicp_last_error": (ctypes.c_char_p, [P]),
+            "sicp_set_reference": (ctypes.c_int, [P, P, I64, F32, ctypes.c_int]),
+            "sicp_register": (ctypes.c_int, [P, P, I64, P, I32, pp, P, P, P, ctypes.c_int]),
+            "sicp_minibatch": (ctypes.c_int, [P, U64, I64, I32, I64, I32, P, ctypes.c_int]),
+            "sicp_nn": (ctypes.c_int, [P, P, I64, I32, P, P, ctypes.c_int]),
+            "sicp_icp_grad": (ctypes.c_int, [P, P, I64, P, I32, P, I32, I32, P, P, ctypes.c_int]),
+            "sicp_stein_adam": (ctypes.c_int, [P, P, P, P, P, I32, I64, I64, pp, P, P, ctypes.c_int]),
+            "sicp_moments": (ctypes.c_int, [P, P, I32, P, P, ctypes.c_int]),
+            "sicp_stats": (ctypes.c_int, [P, ctypes.c_int, P]),
+            "sicp_profile": (ctypes.c_int, [P, ctypes.c_int, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- marshalling helpers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _on_device(*arrays) -> int:
+    dev = [_is_torch(a) and a.is_cuda for a in arrays if a is not None]
+    if any(dev) and not all(dev):
+        raise ValueError("mix of device tensors and host arrays in one call")
+    return int(bool(dev) and dev[0])
+
+
+def _ptr(a, dtype):
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise ValueError(f"tensor must be contiguous {tdt}, got {a.dtype}")
+        return ctypes.c_void_p(a.data_ptr())
+    if a.dtype != dtype or not a.flags.c_contiguous:
+        raise ValueError(f"array must be C-contiguous {np.dtype(dtype)}, got {a.dtype}")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _empty(like, shape, dtype):
+    if _is_torch(like) and like.is_cuda:
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=like.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _host(a, dtype):
+    if _is_torch(a):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _check(ctx, rc: int):
+    if rc != SICP_OK:
+        raise SicpError(rc, lib().sicp_last_error(ctx).decode())
+
+
+# ---------------------------------------------------------------- entry points
+
+def sicp_default_params(**overrides) -> sicp_params:
+    p = sicp_params()
+    lib().sicp_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k in ("prior_mu", "prior_sigma", "prior_kappa"):
+            getattr(p, k)[:] = [float(x) for x in v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def sicp_create(device: int = 0, stream=None):
+    """Context on CUDA `device`; `stream` is a torch.cuda.Stream or raw handle (None: own stream)."""
+    h = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib().sicp_create(ctypes.byref(h), device, s)
+    if rc != SICP_OK:
+        raise SicpError(rc, f"sicp_create(device={device}) failed")
+    return h
+
+
+def sicp_destroy(ctx) -> None:
+    lib().sicp_destroy(ctx)
+
+
+def sicp_last_error(ctx) -> str:
+    return lib().sicp_last_error(ctx).decode()
+
+
+def sicp_set_reference(ctx, xyz, cell_size: float = 0.0) -> None:
+    xyz = _host(xyz, np.float32)
+    _check(ctx, lib().sicp_set_reference(ctx, _ptr(xyz, np.float32), xyz.shape[0], float(cell_size),
+                                         _on_device(xyz)))
+
+
+def sicp_register(ctx, src_xyz, particles, params: sicp_params):
+    """Returns (particles_out [K][6] float32, mean [6] float64, cov [6][6] float64)."""
+    src_xyz, particles = _host(src_xyz, np.float32), _host(particles, np.float32)
+    K = particles.shape[0]
+    out = _empty(particles, (K, 6), np.float32)
+    mean = _empty(particles, (6,), np.float64)
+    cov = _empty(particles, (6, 6), np.float64)
+    _check(ctx, lib().sicp_register(ctx, _ptr(src_xyz, np.float32), src_xyz.shape[0],
+                                    _ptr(particles, np.float32), K, ctypes.byref(params),
+                                    _ptr(out, np.float32), _ptr(mean, np.float64), _ptr(cov, np.float64),
+                                    _on_device(src_xyz, particles)))
+    return out, mean, cov
+
+
+def sicp_minibatch(ctx, seed: int, t0: int, T: int, N: int, m: int, device=None):
+    """Minibatch indices [T][m] int32 (host array, or a tensor on `device`)."""
+    if device is not None:
+        import torch
+        out = torch.empty((T, m), dtype=torch.int32, device=device)
+        on = 1
+    else:
+        out = np.empty((T, m), np.int32)
+        on = 0
+    _check(ctx, lib().sicp_minibatch(ctx, seed & ((1 << 64) - 1), t0, T, N, m, _ptr(out, np.int32), on))
+    return out
+
+
+def sicp_nn(ctx, q, mode: int = SICP_NN_GRID):
+    """Nearest reference index [n] int32 and squared distance [n] float32 per query [n][3]."""
+    q = _host(q, np.float32)
+    n = q.shape[0]
+    idx = _empty(q, (n,), np.int32)
+    d2 = _empty(q, (n,), np.float32)
+    _check(ctx, lib().sicp_nn(ctx, _ptr(q, np.float32), n, mode, _ptr(idx, np.int32), _ptr(d2, np.float32),
+                              _on_device(q)))
+    return idx, d2
+
+
+def sicp_icp_grad(ctx, src_xyz, mb, particles, mode: int = SICP_NN_GRID, want_nn: bool = True):
+    """Mean gradients [K][6] float32 and correspondences [K][m] int32 (or None)."""
+    src_xyz, mb, particles = _host(src_xyz, np.float32), _host(mb, np.int32), _host(particles, np.float32)
+    K, m = particles.shape[0], mb.shape[0]
+    g = _empty(particles, (K, 6), np.float32)
+    nn = _empty(particles, (K, m), np.int32) if want_nn else None
+    _check(ctx, lib().sicp_icp_grad(ctx, _ptr(src_xyz, np.float32), src_xyz.shape[0], _ptr(mb, np.int32), m,
+                                    _ptr(particles, np.float32), K, mode, _ptr(g, np.float32),
+                                    _ptr(nn, np.int32), _on_device(src_xyz, mb, particles)))
+    return g, nn
+
+
+def sicp_stein_adam(ctx, particles, adam_m, adam_v, gbar, N: int, t: int, params: sicp_params):
+    """In-place update of particles, adam_m, adam_v ([K][6] float32); returns (phi [K][6], h [2])."""
+    K = particles.shape[0]
+    phi = _empty(particles, (K, 6), np.float32)
+    h = _empty(particles, (2,), np.float32)
+    _check(ctx, lib().sicp_stein_adam(ctx, _ptr(particles, np.float32), _ptr(adam_m, np.float32),
+                                      _ptr(adam_v, np.float32), _ptr(gbar, np.float32), K, N, t,
+                                      ctypes.byref(params), _ptr(phi, np.float32), _ptr(h, np.float32),
+                                      _on_device(particles, adam_m, adam_v, gbar)))
+    return phi, h
+
+
+def sicp_moments(ctx, particles):
+    particles = _host(particles, np.float32)
+    mean = _empty(particles, (6,), np.float64)
+    cov = _empty(particles, (6, 6), np.float64)
+    _check(ctx, lib().sicp_moments(ctx, _ptr(particles, np.float32), particles.shape[0], _ptr(mean, np.float64),
+                                   _ptr(cov, np.float64), _on_device(particles)))
+    return mean, cov
+
+
+def sicp_stats(ctx, enable: bool = True):
+    """Grid-search counters since the last call (queries, rows, segments,
+    points) as a uint64 array; then resets them and sets counting on/off."""
+    out = np.zeros(4, np.uint64)
+    _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def sicp_profile(ctx, stride: int = 0):
+    """Kernel times since the last call: (gradient ms, gradient launches,
+    Stein ms, Stein launches); then resets them and sets the stride."""
+    out = np.zeros(4, np.float64)
+    _check(ctx, lib().sicp_profile(ctx, int(stride), out.ctypes.data_as(ctypes.c_void_p)))
+    return out

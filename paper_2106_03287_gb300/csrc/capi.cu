@@ -1,0 +1,716 @@
+// C ABI of libsteinicp: context, argument checks, staging of host or device
+// buffers, and the registration loop (captured once per shape into a CUDA
+// graph and replayed).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace sicp {
+
+int set_err(sicp_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_err(sicp_ctx* c, cudaError_t e, const char* what) {
+    set_err(c, SICP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return SICP_ENOMEM;
+    }
+    return SICP_ECUDA;
+}
+
+int ensure(sicp_ctx* c, Buf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return SICP_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t want = bytes + bytes / 4;   // headroom so nearby sizes reuse the buffer
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return set_err(c, SICP_ENOMEM, "device allocation of %zu bytes failed", want);
+    }
+    b.cap = want;
+    return SICP_OK;
+}
+
+// Key of a captured registration loop: everything its kernels read as arguments.
+struct LoopKey {
+    int64_t N;
+    int32_t K, T, m, mode, chunks, stride, pad;
+    int32_t pi[4];          // T, m, nn_mode, prior
+    float pf[16];           // lr, betas, eps, prior mu/sigma/kappa
+    uint64_t seed;
+    const void* ptrs[10];
+    bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
+};
+
+// One instantiated registration graph.  With profiling on, the graph also
+// records three events per profiled iteration (before the gradient kernel,
+// between it and the Stein kernel, after the Stein kernel).
+struct GraphSlot {
+    bool valid = false;
+    LoopKey key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    int n_prof = 0;
+    bool pending = false;   // events recorded by a finished launch, not yet read
+};
+
+// Two slots alternate while profiling, so the events of one run are read on
+// the host while the next run executes on the GPU.
+struct GraphCache {
+    GraphSlot slot[2];
+    int next = 0;
+    ~GraphCache() {
+        for (GraphSlot& s : slot) {
+            if (s.exec) cudaGraphExecDestroy(s.exec);
+            for (cudaEvent_t e : s.ev) cudaEventDestroy(e);
+        }
+    }
+};
+
+}  // namespace sicp
+
+using namespace sicp;
+
+namespace {
+
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool host_finite(const float* x, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(x[i])) return false;
+    return true;
+}
+
+// Make an input visible to the device: device pointers pass through, host
+// buffers are copied into the context buffer `tmp`.
+int stage_in(sicp_ctx* ctx, const void* p, size_t bytes, int on_device, Buf& tmp, const void** out) {
+    if (on_device) {
+        *out = p;
+        return SICP_OK;
+    }
+    int rc = ensure(ctx, tmp, bytes);
+    if (rc) return rc;
+    SICP_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *out = tmp.p;
+    return SICP_OK;
+}
+
+int copy_out(sicp_ctx* ctx, void* dst, const void* src_dev, size_t bytes, int on_device) {
+    if (!dst || bytes == 0) return SICP_OK;
+    SICP_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              ctx->stream));
+    return SICP_OK;
+}
+
+int sync(sicp_ctx* ctx) {
+    SICP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SICP_OK;
+}
+
+int read_flags(sicp_ctx* ctx, int* flags_host) {
+    SICP_CUDA(cudaMemcpyAsync(flags_host, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync(ctx);
+}
+
+int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
+    if (mode == SICP_NN_BRUTE_FP32 || mode == SICP_NN_GRID) return SICP_OK;
+    if (mode == SICP_NN_BRUTE_BF16)
+        return set_err(ctx, SICP_EINVAL, "nn_mode %d (BF16 tensor-core search) is not available in this build", mode);
+    if (mode == SICP_NN_SURROGATE && allow_surrogate)
+        return set_err(ctx, SICP_ENOSURROGATE, "no trained surrogate on this context");
+    return set_err(ctx, SICP_EINVAL, "unknown nn_mode %d", mode);
+}
+
+void fill_defaults(sicp_params* p) {
+    memset(p, 0, sizeof *p);
+    p->T = 100;
+    p->m = 100;
+    p->lr = 0.01f;
+    p->beta1 = 0.9f;
+    p->beta2 = 0.999f;
+    p->eps = 1e-8f;
+    p->nn_mode = SICP_NN_GRID;
+    for (int a = 0; a < 3; ++a) {
+        p->prior_sigma[a] = 1.f;
+        p->prior_kappa[a] = 1.f;
+    }
+}
+
+// Adam constants default when left zero.
+sicp_params normalise(const sicp_params* in) {
+    sicp_params p = *in;
+    if (p.beta1 == 0.f) p.beta1 = 0.9f;
+    if (p.beta2 == 0.f) p.beta2 = 0.999f;
+    if (p.eps == 0.f) p.eps = 1e-8f;
+    return p;
+}
+
+int check_params(sicp_ctx* ctx, const sicp_params& p) {
+    if (!(p.beta1 >= 0.5f && p.beta1 < 1.f) || !(p.beta2 >= 0.5f && p.beta2 < 1.f))
+        return set_err(ctx, SICP_EINVAL, "Adam betas must lie in [0.5, 1)");
+    if (!(p.eps > 0.f) || !isfinite(p.lr) || !(p.lr >= 0.f))
+        return set_err(ctx, SICP_EINVAL, "lr must be finite and >= 0, eps > 0");
+    if (p.prior != 0 && p.prior != 1) return set_err(ctx, SICP_EINVAL, "prior must be 0 or 1");
+    if (p.prior == 1) {
+        for (int a = 0; a < 3; ++a)
+            if (!(p.prior_sigma[a] > 0.f) || !(p.prior_kappa[a] >= 0.f))
+                return set_err(ctx, SICP_EINVAL, "prior sigma must be > 0 and kappa >= 0");
+    }
+    return SICP_OK;
+}
+
+SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, const float* partial,
+                     int32_t chunks, float inv_m, int32_t K, float N, int64_t t) {
+    SteinArgs a;
+    a.theta = theta;
+    a.adam_m = am;
+    a.adam_v = av;
+    a.partial = partial;
+    a.chunks = chunks;
+    a.inv_m = inv_m;
+    a.K = K;
+    a.N = N;
+    a.t = t;
+    a.lr = p.lr;
+    a.beta1 = p.beta1;
+    a.beta2 = p.beta2;
+    a.eps = p.eps;
+    a.prior = p.prior;
+    for (int c = 0; c < 6; ++c) a.mu[c] = p.prior_mu[c];
+    for (int c = 0; c < 3; ++c) {
+        a.sigma[c] = p.prior_sigma[c];
+        a.kappa[c] = p.prior_kappa[c];
+    }
+    a.out_phi = nullptr;
+    a.out_h = nullptr;
+    return a;
+}
+
+unsigned long long* stats_ptr(sicp_ctx* ctx) {
+    return ctx->stats_on ? (unsigned long long*)ctx->stats.p : nullptr;
+}
+
+// Add the kernel durations recorded by a finished launch of `s` to the totals.
+void collect_profile(sicp_ctx* ctx, GraphSlot& s) {
+    if (!s.pending) return;
+    for (int i = 0; i < s.n_prof; ++i) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, s.ev[3 * i], s.ev[3 * i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, s.ev[3 * i + 1], s.ev[3 * i + 2]) == cudaSuccess) {
+            ctx->prof[0] += a;
+            ctx->prof[1] += 1;
+            ctx->prof[2] += b;
+            ctx->prof[3] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    s.pending = false;
+}
+
+cudaError_t launch_grad(sicp_ctx* ctx, int32_t mode, const GradArgs& g) {
+    if (mode == SICP_NN_GRID) return launch_grad_grid(g, ctx->grid.v, ctx->stream);
+    return launch_grad_brute(g, ctx->ref4, ctx->M, ctx->stream);
+}
+
+constexpr int32_t kMaxK = 4096;
+constexpr int64_t kMaxN = 0x7fffffff;
+constexpr int64_t kMaxM = (int64_t)1 << 30;
+
+}  // namespace
+
+extern "C" {
+
+void sicp_default_params(sicp_params* p) {
+    if (p) fill_defaults(p);
+}
+
+int sicp_create(sicp_ctx** out, int device, void* cuda_stream) {
+    if (!out) return SICP_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return SICP_ECUDA;
+    }
+    sicp_ctx* c = new sicp_ctx();
+    c->device = device;
+    DeviceScope ds(device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return SICP_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->graphs = new GraphCache();
+    if (kernel_attrs_init() != cudaSuccess) {
+        cudaGetLastError();
+        sicp_destroy(c);
+        return SICP_ECUDA;
+    }
+    if (ensure(c, c->flags, 4 * sizeof(int)) != SICP_OK) {
+        sicp_destroy(c);
+        return SICP_ENOMEM;
+    }
+    *out = c;
+    return SICP_OK;
+}
+
+void sicp_destroy(sicp_ctx* c) {
+    if (!c) return;
+    DeviceScope ds(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    delete c->graphs;
+    Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
+                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats};
+    for (Buf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->ref4) cudaFree(c->ref4);
+    void* gp[] = {c->grid.sorted, c->grid.cell_start, c->grid.row_span, c->grid.brick_rep, c->grid.cell_of,
+                  c->grid.counts, c->grid.scan_sums};
+    for (void* p : gp)
+        if (p) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* sicp_last_error(const sicp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_size, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!xyz || M < 1 || M > kMaxM) return set_err(ctx, SICP_EINVAL, "reference needs 1 <= M <= 2^30 points");
+    if (!(cell_size >= 0.f) || !isfinite(cell_size)) return set_err(ctx, SICP_EINVAL, "cell_size must be >= 0");
+    if (!on_device && !host_finite(xyz, 3 * M)) return set_err(ctx, SICP_EINVAL, "non-finite reference coordinate");
+    DeviceScope ds(ctx->device);
+    const void* d_xyz;
+    int rc = stage_in(ctx, xyz, sizeof(float) * 3 * M, on_device, ctx->tmp_in, &d_xyz);
+    if (rc) return rc;
+    if ((size_t)M > ctx->ref_cap) {
+        if (ctx->ref4) cudaFree(ctx->ref4);
+        ctx->ref4 = nullptr;
+        ctx->ref_cap = 0;
+        if (cudaMalloc(&ctx->ref4, sizeof(float4) * M) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, SICP_ENOMEM, "reference allocation failed");
+        }
+        ctx->ref_cap = M;
+    }
+    ctx->M = 0;
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    SICP_CUDA(launch_pack_points((const float*)d_xyz, M, ctx->ref4, (int*)ctx->flags.p, ctx->stream));
+    int flags[4];
+    rc = read_flags(ctx, flags);
+    if (rc) return rc;
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite reference coordinate");
+    ctx->M = M;
+    rc = grid_build(ctx, cell_size);
+    if (rc) {
+        ctx->M = 0;
+        return rc;
+    }
+    ctx->graphs->slot[0].valid = ctx->graphs->slot[1].valid = false;
+    return sync(ctx);
+}
+
+int sicp_minibatch(sicp_ctx* ctx, uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
+                   int32_t* out_idx, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!out_idx || T < 1 || t0 < 0 || N < 1 || N > kMaxN || m < 1 || m > N)
+        return set_err(ctx, SICP_EINVAL, "minibatch needs T >= 1, t0 >= 0, 1 <= m <= N < 2^31");
+    DeviceScope ds(ctx->device);
+    const size_t bytes = sizeof(int32_t) * (size_t)T * m;
+    int32_t* dst = out_idx;
+    if (!on_device) {
+        int rc = ensure(ctx, ctx->tmp_out, bytes);
+        if (rc) return rc;
+        dst = (int32_t*)ctx->tmp_out.p;
+    }
+    SICP_CUDA(launch_minibatch(seed, t0, T, N, m, dst, ctx->stream));
+    if (!on_device) {
+        int rc = copy_out(ctx, out_idx, dst, bytes, 0);
+        if (rc) return rc;
+    }
+    return sync(ctx);
+}
+
+int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out_idx, float* out_d2,
+            int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (n < 0 || n > kMaxN) return set_err(ctx, SICP_EINVAL, "query count out of range");
+    if (n == 0) return SICP_OK;
+    if (!q || !out_idx) return set_err(ctx, SICP_EINVAL, "null query or output pointer");
+    int rc = check_mode(ctx, mode, false);
+    if (rc) return rc;
+    if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
+    if (!on_device && !host_finite(q, 3 * n)) return set_err(ctx, SICP_EINVAL, "non-finite query");
+    DeviceScope ds(ctx->device);
+    const void* d_q;
+    rc = stage_in(ctx, q, sizeof(float) * 3 * n, on_device, ctx->tmp_in, &d_q);
+    if (rc) return rc;
+    int32_t* d_idx = out_idx;
+    float* d_d2 = out_d2;
+    if (!on_device) {
+        rc = ensure(ctx, ctx->tmp_out, (sizeof(int32_t) + sizeof(float)) * n);
+        if (rc) return rc;
+        d_idx = (int32_t*)ctx->tmp_out.p;
+        d_d2 = (float*)((char*)ctx->tmp_out.p + sizeof(int32_t) * n);
+    }
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    if (on_device) SICP_CUDA(launch_check_finite((const float*)d_q, 3 * n, (int*)ctx->flags.p, ctx->stream));
+    if (mode == SICP_NN_GRID)
+        SICP_CUDA(launch_nn_grid(ctx->grid.v, (const float*)d_q, n, d_idx, d_d2, stats_ptr(ctx), ctx->stream));
+    else
+        SICP_CUDA(launch_nn_brute(ctx->ref4, ctx->M, (const float*)d_q, n, d_idx, d_d2, ctx->stream));
+    int flags[4];
+    rc = read_flags(ctx, flags);
+    if (rc) return rc;
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite query");
+    if (!on_device) {
+        if ((rc = copy_out(ctx, out_idx, d_idx, sizeof(int32_t) * n, 0))) return rc;
+        if (out_d2 && (rc = copy_out(ctx, out_d2, d_d2, sizeof(float) * n, 0))) return rc;
+    }
+    return sync(ctx);
+}
+
+int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t* mb, int32_t m,
+                  const float* particles, int32_t K, int32_t mode, float* out_gbar, int32_t* out_nn,
+                  int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!src_xyz || !mb || !particles || !out_gbar) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (N < 1 || N > kMaxN || m < 1 || K < 1 || K > 65535)
+        return set_err(ctx, SICP_EINVAL, "icp_grad needs N >= 1, m >= 1, 1 <= K <= 65535");
+    int rc = check_mode(ctx, mode, false);
+    if (rc) return rc;
+    if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
+    if (!on_device) {
+        if (!host_finite(src_xyz, 3 * N) || !host_finite(particles, 6 * (int64_t)K))
+            return set_err(ctx, SICP_EINVAL, "non-finite input");
+        for (int32_t k = 0; k < m; ++k)
+            if (mb[k] < 0 || mb[k] >= N) return set_err(ctx, SICP_EINVAL, "minibatch index out of range");
+    }
+    DeviceScope ds(ctx->device);
+    const size_t b_src = sizeof(float) * 3 * N, b_mb = sizeof(int32_t) * m, b_th = sizeof(float) * 6 * K;
+    if ((rc = ensure(ctx, ctx->tmp_aux, b_src + b_mb + b_th + 64))) return rc;
+    const void *d_src, *d_mb, *d_th;
+    char* aux = (char*)ctx->tmp_aux.p;
+    if (on_device) {
+        d_src = src_xyz;
+        d_mb = mb;
+        d_th = particles;
+    } else {
+        SICP_CUDA(cudaMemcpyAsync(aux, src_xyz, b_src, cudaMemcpyHostToDevice, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(aux + b_src, mb, b_mb, cudaMemcpyHostToDevice, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(aux + b_src + b_mb, particles, b_th, cudaMemcpyHostToDevice, ctx->stream));
+        d_src = aux;
+        d_mb = aux + b_src;
+        d_th = aux + b_src + b_mb;
+    }
+    const int chunks = grad_layout(m).chunks;
+    if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
+    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
+    if ((rc = ensure(ctx, ctx->tmp_out, (sizeof(float) * 6 + sizeof(int32_t) * (size_t)m) * K))) return rc;
+    float* d_g = (float*)ctx->tmp_out.p;
+    int32_t* d_nn = (int32_t*)((char*)ctx->tmp_out.p + sizeof(float) * 6 * K);
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    SICP_CUDA(launch_check_finite((const float*)d_th, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+    SICP_CUDA(launch_check_index((const int32_t*)d_mb, m, N, (int*)ctx->flags.p, ctx->stream));
+    int flags[4];
+    if ((rc = read_flags(ctx, flags))) return rc;
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
+    if (flags[1]) return set_err(ctx, SICP_EINVAL, "minibatch index out of range");
+    GradArgs g;
+    g.src = (const float4*)ctx->src4.p;
+    g.mb = (const int32_t*)d_mb;
+    g.m = m;
+    g.theta = (const float*)d_th;
+    g.K = K;
+    g.partial = (float*)ctx->partial.p;
+    g.out_nn = d_nn;
+    g.stats = stats_ptr(ctx);
+    SICP_CUDA(launch_grad(ctx, mode, g));
+    SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
+    if ((rc = copy_out(ctx, out_gbar, d_g, sizeof(float) * 6 * K, on_device))) return rc;
+    if (out_nn && (rc = copy_out(ctx, out_nn, d_nn, sizeof(int32_t) * (size_t)m * K, on_device))) return rc;
+    return sync(ctx);
+}
+
+int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_v, const float* gbar,
+                    int32_t K, int64_t N, int64_t t, const sicp_params* p_in, float* out_phi, float* out_h,
+                    int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!particles || !adam_m || !adam_v || !gbar || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (K < 1 || K > kMaxK || N < 1 || t < 1)
+        return set_err(ctx, SICP_EINVAL, "stein_adam needs 1 <= K <= %d, N >= 1, t >= 1", kMaxK);
+    const sicp_params p = normalise(p_in);
+    int rc = check_params(ctx, p);
+    if (rc) return rc;
+    DeviceScope ds(ctx->device);
+    const size_t b = sizeof(float) * 6 * K;
+    if ((rc = ensure(ctx, ctx->tmp_aux, 5 * b + 64))) return rc;
+    float* th = (float*)ctx->tmp_aux.p;
+    float* am = th + 6 * K;
+    float* av = am + 6 * K;
+    float* gb = av + 6 * K;
+    float* phi = gb + 6 * K;
+    float* hh = phi + 6 * K;   // 2 floats in the padding
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SICP_CUDA(cudaMemcpyAsync(th, particles, b, kin, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(am, adam_m, b, kin, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(av, adam_v, b, kin, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(gb, gbar, b, kin, ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    SICP_CUDA(launch_check_finite(th, 24 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+    int flags[4];
+    if ((rc = read_flags(ctx, flags))) return rc;
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
+    SteinArgs a = stein_args(p, th, am, av, gb, 1, 1.f, K, (float)N, t);
+    a.out_phi = phi;
+    a.out_h = hh;
+    SICP_CUDA(launch_stein_adam(a, ctx->stream));
+    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    SICP_CUDA(cudaMemcpyAsync(particles, th, b, kout, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(adam_m, am, b, kout, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(adam_v, av, b, kout, ctx->stream));
+    if (out_phi) SICP_CUDA(cudaMemcpyAsync(out_phi, phi, b, kout, ctx->stream));
+    if (out_h) SICP_CUDA(cudaMemcpyAsync(out_h, hh, 2 * sizeof(float), kout, ctx->stream));
+    return sync(ctx);
+}
+
+int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!particles || K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "moments needs 1 <= K <= %d", kMaxK);
+    DeviceScope ds(ctx->device);
+    const void* d_th;
+    int rc = stage_in(ctx, particles, sizeof(float) * 6 * K, on_device, ctx->tmp_in, &d_th);
+    if (rc) return rc;
+    if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
+    SICP_CUDA(launch_moments((const float*)d_th, K, (double*)ctx->moments.p, ctx->stream));
+    if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
+    if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;
+    return sync(ctx);
+}
+
+int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in, int32_t K,
+                  const sicp_params* p_in, float* particles_out, double* mean6, double* cov36, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!src_xyz || !particles_in || !particles_out || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
+    const sicp_params p = normalise(p_in);
+    if (N < 1 || N > kMaxN) return set_err(ctx, SICP_EINVAL, "source needs 1 <= N <= 2^31-1 points");
+    if (K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "particle count must be in [1, %d]", kMaxK);
+    if (p.T < 0) return set_err(ctx, SICP_EINVAL, "T must be >= 0");
+    if (p.m < 1 || p.m > N) return set_err(ctx, SICP_EINVAL, "minibatch m=%d outside [1, N=%lld]", p.m, (long long)N);
+    int rc = check_params(ctx, p);
+    if (rc) return rc;
+    if ((rc = check_mode(ctx, p.nn_mode, true))) return rc;
+    if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
+    if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
+        return set_err(ctx, SICP_EINVAL, "non-finite input");
+    DeviceScope ds(ctx->device);
+    const int chunks = grad_layout(p.m).chunks;
+    const size_t b_th = sizeof(float) * 6 * K;
+    if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
+    if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m))) return rc;
+    if ((rc = ensure(ctx, ctx->theta, b_th))) return rc;
+    if ((rc = ensure(ctx, ctx->adam_m, b_th))) return rc;
+    if ((rc = ensure(ctx, ctx->adam_v, b_th))) return rc;
+    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
+    if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
+
+    const void *d_src, *d_th0;
+    if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
+    if ((rc = stage_in(ctx, particles_in, b_th, on_device, ctx->tmp_aux, &d_th0))) return rc;
+    float* theta = (float*)ctx->theta.p;
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    SICP_CUDA(launch_check_finite((const float*)d_th0, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
+
+    const int stride = ctx->prof_stride;
+    LoopKey key;
+    memset(&key, 0, sizeof key);
+    key.N = N;
+    key.K = K;
+    key.T = p.T;
+    key.m = p.m;
+    key.mode = p.nn_mode;
+    key.chunks = chunks;
+    key.stride = stride;
+    key.pi[0] = p.T;
+    key.pi[1] = p.m;
+    key.pi[2] = p.nn_mode;
+    key.pi[3] = p.prior;
+    key.pf[0] = p.lr;
+    key.pf[1] = p.beta1;
+    key.pf[2] = p.beta2;
+    key.pf[3] = p.eps;
+    for (int a = 0; a < 6; ++a) key.pf[4 + a] = p.prior_mu[a];
+    for (int a = 0; a < 3; ++a) {
+        key.pf[10 + a] = p.prior_sigma[a];
+        key.pf[13 + a] = p.prior_kappa[a];
+    }
+    key.seed = p.seed;
+    key.ptrs[0] = ctx->src4.p;
+    key.ptrs[1] = ctx->mb.p;
+    key.ptrs[2] = ctx->theta.p;
+    key.ptrs[3] = ctx->adam_m.p;
+    key.ptrs[4] = ctx->adam_v.p;
+    key.ptrs[5] = ctx->partial.p;
+    key.ptrs[6] = ctx->moments.p;
+    key.ptrs[7] = ctx->grid.sorted;
+    key.ptrs[8] = ctx->ref4;
+    key.ptrs[9] = stats_ptr(ctx);
+
+    GraphCache& gc = *ctx->graphs;
+    GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
+    const bool use_graph = getenv("SICP_NO_GRAPH") == nullptr;
+    auto record = [&](GraphSlot* prof) -> int {
+        SICP_CUDA(launch_minibatch(p.seed, 0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
+        GradArgs g;
+        g.src = (const float4*)ctx->src4.p;
+        g.m = p.m;
+        g.theta = theta;
+        g.K = K;
+        g.partial = (float*)ctx->partial.p;
+        g.out_nn = nullptr;
+        g.stats = stats_ptr(ctx);
+        int np = 0;
+        for (int32_t t = 0; t < p.T; ++t) {
+            const bool timed = prof && stride > 0 && (t % stride) == 0;
+            if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np], ctx->stream, cudaEventRecordExternal));
+            g.mb = (const int32_t*)ctx->mb.p + (size_t)t * p.m;
+            SICP_CUDA(launch_grad(ctx, p.nn_mode, g));
+            if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
+            SteinArgs a = stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
+                                     (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
+            SICP_CUDA(launch_stein_adam(a, ctx->stream));
+            if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
+            if (timed) ++np;
+        }
+        if (prof) prof->n_prof = np;
+        SICP_CUDA(launch_moments(theta, K, (double*)ctx->moments.p, ctx->stream));
+        return SICP_OK;
+    };
+    if (use_graph) {
+        if (!(slot.valid && slot.key == key)) {
+            if (slot.exec) cudaGraphExecDestroy(slot.exec);
+            slot.exec = nullptr;
+            slot.valid = false;
+            slot.pending = false;
+            const int need = stride > 0 ? 3 * ((p.T + stride - 1) / stride) : 0;
+            while ((int)slot.ev.size() < need) {
+                cudaEvent_t e;
+                SICP_CUDA(cudaEventCreate(&e));
+                slot.ev.push_back(e);
+            }
+            cudaGraph_t graph;
+            SICP_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            rc = record(stride > 0 ? &slot : nullptr);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+            if (rc) {
+                if (e == cudaSuccess) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&slot.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGraphInstantiate");
+            slot.key = key;
+            slot.valid = true;
+        }
+        SICP_CUDA(cudaGraphLaunch(slot.exec, ctx->stream));
+        if (stride > 0) {
+            // the other slot's last launch finished before this call began
+            collect_profile(ctx, gc.slot[1 - gc.next]);
+            slot.pending = true;
+            gc.next = 1 - gc.next;
+        }
+    } else {
+        if ((rc = record(nullptr))) return rc;
+    }
+    int flags[4];
+    if ((rc = read_flags(ctx, flags))) return rc;
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
+    if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
+    if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
+    if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;
+    return sync(ctx);
+}
+
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out4) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    DeviceScope ds(ctx->device);
+    int rc = ensure(ctx, ctx->stats, 4 * sizeof(unsigned long long));
+    if (rc) return rc;
+    if (out4) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        if (ctx->stats_on) {
+            SICP_CUDA(cudaMemcpyAsync(h, ctx->stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+            if ((rc = sync(ctx))) return rc;
+        }
+        for (int a = 0; a < 4; ++a) out4[a] = (uint64_t)h[a];
+    }
+    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    ctx->stats_on = enable != 0;
+    return sync(ctx);
+}
+
+int sicp_profile(sicp_ctx* ctx, int stride, double* out4) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (stride < 0) return set_err(ctx, SICP_EINVAL, "stride must be >= 0");
+    DeviceScope ds(ctx->device);
+    int rc = sync(ctx);
+    if (rc) return rc;
+    for (GraphSlot& s : ctx->graphs->slot) collect_profile(ctx, s);
+    if (out4)
+        for (int a = 0; a < 4; ++a) out4[a] = ctx->prof[a];
+    for (int a = 0; a < 4; ++a) ctx->prof[a] = 0.0;
+    ctx->prof_stride = stride;
+    return SICP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+// Internal declarations shared by the CUDA translation units of libsteinicp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/steinicp.h"
+
+namespace sicp {
+
+// ---------------------------------------------------------------- device helpers
+
+// splitmix64 (Steele, Lea, Flood 2014): output k >= 1 of the generator
+// started at state s is mix(s + k * 0x9e3779b97f4a7c15).
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t s, uint64_t k) {
+    return sm64_mix(s + k * 0x9e3779b97f4a7c15ULL);
+}
+
+// Rotation R = Rz(yaw) Ry(pitch) Rx(roll) and its partials with respect to
+// roll, pitch and yaw: 36 floats, R row-major then dR_roll, dR_pitch, dR_yaw.
+struct Pose {
+    float R[9];
+    float dR[27];
+    float u[3];
+};
+
+__device__ __forceinline__ void make_pose(const float* th, Pose& P) {
+    float sr, cr, sp, cp, sy, cy;
+    sincosf(th[3], &sr, &cr);
+    sincosf(th[4], &sp, &cp);
+    sincosf(th[5], &sy, &cy);
+    // R = Rz Ry Rx
+    P.R[0] = cy * cp; P.R[1] = cy * sp * sr - sy * cr; P.R[2] = cy * sp * cr + sy * sr;
+    P.R[3] = sy * cp; P.R[4] = sy * sp * sr + cy * cr; P.R[5] = sy * sp * cr - cy * sr;
+    P.R[6] = -sp;     P.R[7] = cp * sr;                P.R[8] = cp * cr;
+    // d/droll: Rz Ry dRx
+    P.dR[0] = 0.f; P.dR[1] = cy * sp * cr + sy * sr;  P.dR[2] = -cy * sp * sr + sy * cr;
+    P.dR[3] = 0.f; P.dR[4] = sy * sp * cr - cy * sr;  P.dR[5] = -sy * sp * sr - cy * cr;
+    P.dR[6] = 0.f; P.dR[7] = cp * cr;                 P.dR[8] = -cp * sr;
+    // d/dpitch: Rz dRy Rx
+    P.dR[9] = -cy * sp;  P.dR[10] = cy * cp * sr; P.dR[11] = cy * cp * cr;
+    P.dR[12] = -sy * sp; P.dR[13] = sy * cp * sr; P.dR[14] = sy * cp * cr;
+    P.dR[15] = -cp;      P.dR[16] = -sp * sr;     P.dR[17] = -sp * cr;
+    // d/dyaw: dRz Ry Rx
+    P.dR[18] = -sy * cp; P.dR[19] = -sy * sp * sr - cy * cr; P.dR[20] = -sy * sp * cr + cy * sr;
+    P.dR[21] = cy * cp;  P.dR[22] = cy * sp * sr - sy * cr;  P.dR[23] = cy * sp * cr + sy * sr;
+    P.dR[24] = 0.f;      P.dR[25] = 0.f;                     P.dR[26] = 0.f;
+    P.u[0] = th[0]; P.u[1] = th[1]; P.u[2] = th[2];
+}
+
+__device__ __forceinline__ float3 apply_pose(const Pose& P, float3 s) {
+    return make_float3(fmaf(P.R[0], s.x, fmaf(P.R[1], s.y, fmaf(P.R[2], s.z, P.u[0]))),
+                       fmaf(P.R[3], s.x, fmaf(P.R[4], s.y, fmaf(P.R[5], s.z, P.u[1]))),
+                       fmaf(P.R[6], s.x, fmaf(P.R[7], s.y, fmaf(P.R[8], s.z, P.u[2]))));
+}
+
+// Contribution of one correspondence to the gradient of L/2:
+// [e ; e . (dR_a s)] with e = s' - r.
+__device__ __forceinline__ void grad_terms(const Pose& P, float3 s, float3 e, float g[6]) {
+    g[0] = e.x; g[1] = e.y; g[2] = e.z;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float* D = P.dR + 9 * a;
+        float jx = fmaf(D[0], s.x, fmaf(D[1], s.y, D[2] * s.z));
+        float jy = fmaf(D[3], s.x, fmaf(D[4], s.y, D[5] * s.z));
+        float jz = fmaf(D[6], s.x, fmaf(D[7], s.y, D[8] * s.z));
+        g[3 + a] = fmaf(e.x, jx, fmaf(e.y, jy, e.z * jz));
+    }
+}
+
+// Exact squared distance, the comparison every search mode uses.
+__device__ __forceinline__ float dist2(float4 r, float3 q) {
+    float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Candidate (d2, idx) is better than (bd, bi): smaller distance, ties to the lower index.
+__device__ __forceinline__ bool better(float d2, int idx, float bd, int bi) {
+    return d2 < bd || (d2 == bd && idx < bi);
+}
+
+// ---------------------------------------------------------------- host context
+
+// Uniform voxel grid over the reference bounding box.  Points are stored
+// sorted by linear cell id (x fastest), so every run of consecutive cells along
+// x is one contiguous range of `sorted`.
+constexpr int kBrick = 8;           // bricks of 8 x 8 x 8 cells carry one representative point
+constexpr int32_t kEmpty = 0x7f7f7f7f;
+
+struct GridView {
+    float3 origin;
+    float cell, inv_cell, tol;      // tol: absolute slack covering rounding of cell bounds
+    int3 dims;                      // cells per axis
+    int3 bdims;                     // bricks per axis
+    const float4* sorted;           // M, w = original index bits
+    const int32_t* cell_start;      // ncells + 1
+    const int2* row_span;           // dims.y * dims.z: first and last non-empty x of the row
+    const int32_t* brick_rep;       // bricks: lowest original index in the brick, kEmpty if none
+    const float4* ref4;             // M, original order
+};
+
+struct Grid {
+    GridView v{};
+    int64_t ncells = 0, nbricks = 0;
+    float4* sorted = nullptr;
+    int32_t* cell_start = nullptr;
+    int2* row_span = nullptr;
+    int32_t* brick_rep = nullptr;
+    int32_t* cell_of = nullptr;     // M: cell id of each reference point (build scratch)
+    int32_t* counts = nullptr;      // ncells + 1 (build scratch)
+    int32_t* scan_sums = nullptr;   // build scratch
+    size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_bricks = 0, cap_rows = 0,
+           cap_sums = 0;
+};
+
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct GraphCache;
+
+}  // namespace sicp
+
+struct sicp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int num_sms = 0;
+
+    // reference cloud
+    int64_t M = 0;
+    float4* ref4 = nullptr;   // original order, w = index bits
+    size_t ref_cap = 0;
+    sicp::Grid grid;
+    float3 ref_lo = {0, 0, 0}, ref_hi = {0, 0, 0};
+
+    // per-problem and scratch buffers (grow-only)
+    sicp::Buf src4, mb, theta, adam_m, adam_v, partial, moments, flags, tmp_in, tmp_out, tmp_aux;
+    sicp::Buf bbox, stats;
+    bool stats_on = false;
+    int prof_stride = 0;
+    double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
+    sicp::GraphCache* graphs = nullptr;
+};
+
+namespace sicp {
+
+int set_err(sicp_ctx* c, int code, const char* fmt, ...);
+int cuda_err(sicp_ctx* c, cudaError_t e, const char* what);
+int ensure(sicp_ctx* c, Buf& b, size_t bytes);
+
+#define SICP_CUDA(call)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+    } while (0)
+
+// ---- kernel launchers (each returns the launch status) ----
+
+// points [n][3] -> float4 (w = index bits); flags[0] |= 1 on a non-finite value
+cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* flags, cudaStream_t s);
+cudaError_t launch_check_finite(const float* x, int64_t n, int* flags, cudaStream_t s);
+// flags[1] |= 1 if any index is outside [0, N)
+cudaError_t launch_check_index(const int32_t* idx, int64_t n, int64_t N, int* flags, cudaStream_t s);
+// gbar[j][c] = inv_m * sum over chunks of partial[chunk][j][c]
+cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, float inv_m, float* gbar,
+                                   cudaStream_t s);
+// ordered-uint bounding box of float4 points into lohi[6] (min xyz, max xyz), pre-initialised
+cudaError_t launch_bbox(const float4* p, int64_t n, unsigned* lohi, cudaStream_t s);
+float ordered_to_float(unsigned u);
+// exclusive scan of n int32 counts into out[0..n] (out[n] = total); sums: scratch of scan_sums_size(n)
+size_t scan_sums_size(int64_t n);
+cudaError_t launch_exclusive_scan(const int32_t* in, int64_t n, int32_t* out, int32_t* sums, cudaStream_t s);
+// one-time kernel attributes (dynamic shared memory opt-in)
+cudaError_t kernel_attrs_init();
+
+cudaError_t launch_minibatch(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
+                             int32_t* out, cudaStream_t s);
+
+// Per-query search of the whole reference (fp32 exhaustive).
+cudaError_t launch_nn_brute(const float4* ref, int64_t M, const float* q, int64_t n,
+                            int32_t* idx, float* d2, cudaStream_t s);
+
+// The fused gradient kernels split a particle's m minibatch entries over
+// `chunks` CTAs of `chunk_threads` threads (a multiple of 32, at most 256).
+struct GradLayout {
+    int chunks, threads;
+};
+GradLayout grad_layout(int32_t m);
+
+struct GradArgs {
+    const float4* src;     // N
+    const int32_t* mb;     // m indices of this iteration
+    int32_t m;
+    const float* theta;    // K x 6
+    int32_t K;
+    float* partial;        // [chunks][K][6] sums of gradient terms (not divided by m)
+    int32_t* out_nn;       // K x m or null
+    unsigned long long* stats;  // search work counters (queries, rows, segments, points) or null
+};
+cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
+
+struct SteinArgs {
+    float* theta;          // K x 6 in/out
+    float* adam_m;         // K x 6
+    float* adam_v;         // K x 6
+    const float* partial;  // [chunks][K][6]
+    int32_t chunks;
+    float inv_m;           // 1/m: gbar = inv_m * sum over chunks
+    int32_t K;
+    float N;
+    int64_t t;             // 1-based Adam step
+    float lr, beta1, beta2, eps;
+    int32_t prior;
+    float mu[6], sigma[3], kappa[3];
+    float* out_phi;        // K x 6 or null
+    float* out_h;          // 2 or null
+};
+cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
+cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);
+
+// Grid (uniform voxel) search structure
+int grid_build(sicp_ctx* ctx, float cell_size);
+cudaError_t launch_nn_grid(const GridView& g, const float* q, int64_t n, int32_t* idx, float* d2,
+                           unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_grad_grid(const GradArgs& a, const GridView& g, cudaStream_t s);
+
+}  // namespace sicp

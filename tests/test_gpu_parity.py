@@ -1,0 +1,373 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 GPU against the FP64 oracle on the same float32 inputs):
+  * minibatch indices: bit-exact.
+  * nearest neighbours: the same index, or one whose exact (FP64) squared
+    distance exceeds the minimum by at most 1e-6 relative (a near-tie); the
+    grid and the exhaustive search use one distance function and one tie rule,
+    so they must agree bit for bit.
+  * mean gradients, Stein directions, particles: 1e-4 relative per particle
+    (max-norm), with an absolute floor set by FP32 rounding of the inputs'
+    magnitudes (stated next to each check).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+import paper_2106_03287_gb300 as S  # noqa: E402
+from paper_2106_03287_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+MODES = [S.SICP_NN_BRUTE_FP32, S.SICP_NN_GRID]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2106_03287_gb300 import build
+    build.build()
+    c = S.sicp_create(0)
+    yield c
+    S.sicp_destroy(c)
+
+
+def _nn_ok(ref, q, idx_gpu, rel=1e-6):
+    """Every GPU index is the oracle's, or an FP64 near-tie of it."""
+    idx_o, d2_o = O.nn(ref, q.astype(np.float64))
+    same = idx_gpu == idx_o
+    if same.all():
+        return 0
+    diff = np.flatnonzero(~same)
+    r = ref[idx_gpu[diff]].astype(np.float64)
+    d2g = ((r - q[diff].astype(np.float64)) ** 2).sum(1)
+    assert np.all(d2g <= d2_o[diff] * (1 + rel) + 1e-300), (diff[:5], d2g[:5], d2_o[diff][:5])
+    return diff.size
+
+
+# ---------------------------------------------------------------- step 1: minibatch
+
+@pytest.mark.parametrize("seed,t0,T,N,m", [(0, 0, 4, 500, 100), (7, 3, 3, 10_000, 300),
+                                           (2 ** 63 + 1, 10, 2, 111_123, 500), (5, 0, 2, 50, 50),
+                                           (9, 0, 3, 1000, 1), (11, 149, 1, 10_000, 300)])
+def test_minibatch_bit_exact(ctx, seed, t0, T, N, m):
+    got = S.sicp_minibatch(ctx, seed, t0, T, N, m)
+    for r in range(T):
+        assert np.array_equal(got[r], O.minibatch(seed, t0 + r, N, m)), (seed, t0 + r)
+    dev = S.sicp_minibatch(ctx, seed, t0, T, N, m, device="cuda")
+    assert np.array_equal(dev.cpu().numpy(), got)
+
+
+# ---------------------------------------------------------------- step 3: nearest neighbour
+
+def _clouds():
+    rng = np.random.default_rng(0)
+    box = synth.make_box_problem(1)["ref"]
+    kin = synth.make_kinect_problem(1, M=20_000, N=100, K=1)["ref"]
+    uni = rng.uniform(-2, 2, (3000, 3)).astype(np.float32)
+    return {"box": box, "kinect": kin, "uniform": uni}
+
+
+@pytest.mark.parametrize("name", ["box", "kinect", "uniform"])
+def test_nn_matches_oracle_and_grid_equals_brute(ctx, name):
+    ref = _clouds()[name]
+    rng = np.random.default_rng(1)
+    ext = ref.max(0) - ref.min(0)
+    near = ref[rng.integers(0, ref.shape[0], 3000)] + rng.normal(0, 0.01 * ext.max(), (3000, 3))
+    far = ref.min(0) + rng.uniform(-1.0, 2.0, (500, 3)) * ext          # many outside the box
+    exact = ref[rng.integers(0, ref.shape[0], 200)]
+    q = np.concatenate([near, far, exact]).astype(np.float32)
+    S.sicp_set_reference(ctx, ref)
+    out = {}
+    for mode in MODES:
+        idx, d2 = S.sicp_nn(ctx, q, mode)
+        _nn_ok(ref, q, idx)
+        out[mode] = (idx, d2)
+    assert np.array_equal(out[MODES[0]][0], out[MODES[1]][0])
+    assert np.array_equal(out[MODES[0]][1], out[MODES[1]][1])
+    # a query on a reference point finds it (or a lower-index duplicate) at distance 0
+    assert np.all(out[S.SICP_NN_GRID][1][-200:] == 0.0)
+
+
+def test_nn_duplicates_and_degenerate_clouds(ctx):
+    rng = np.random.default_rng(2)
+    base = rng.uniform(-1, 1, (300, 3)).astype(np.float32)
+    ref = np.concatenate([base, base[:100], base[:50]])[rng.permutation(450)]
+    S.sicp_set_reference(ctx, ref)
+    for mode in MODES:
+        idx, d2 = S.sicp_nn(ctx, ref, mode)
+        for r in range(0, 450, 7):
+            same = np.flatnonzero(np.all(ref == ref[r], axis=1))
+            assert idx[r] == same.min() and d2[r] == 0.0
+    # one point; all points equal; a flat (planar) cloud
+    for cloud in (np.array([[0.5, -0.25, 2.0]], np.float32), np.tile(np.float32([1, 2, 3]), (64, 1)),
+                  np.c_[rng.uniform(-1, 1, (500, 2)), np.zeros(500)].astype(np.float32)):
+        S.sicp_set_reference(ctx, cloud)
+        q = rng.uniform(-3, 3, (257, 3)).astype(np.float32)
+        for mode in MODES:
+            idx, _ = S.sicp_nn(ctx, q, mode)
+            _nn_ok(cloud, q, idx)
+    idx, d2 = S.sicp_nn(ctx, np.zeros((0, 3), np.float32), S.SICP_NN_GRID)
+    assert idx.shape == (0,)
+
+
+def test_nn_on_device_tensors(ctx):
+    ref = _clouds()["kinect"]
+    S.sicp_set_reference(ctx, torch.from_numpy(ref).cuda())
+    q = ref[:777] + np.float32(0.003)
+    i_h, d_h = S.sicp_nn(ctx, q, S.SICP_NN_GRID)
+    i_d, d_d = S.sicp_nn(ctx, torch.from_numpy(q).cuda(), S.SICP_NN_GRID)
+    assert np.array_equal(i_h, i_d.cpu().numpy()) and np.array_equal(d_h, d_d.cpu().numpy())
+
+
+# ---------------------------------------------------------------- steps 2-4: gradient
+
+def _grad_floor(ref, src, theta):
+    X = float(max(np.abs(ref).max(), np.abs(src).max()) + np.abs(theta[:, :3]).max())
+    return 16 * U32 * X * (1 + X)
+
+
+def _check_grad(ctx, ref, src, theta, mb, mode):
+    g, nn = S.sicp_icp_grad(ctx, src, mb, theta, mode)
+    th64 = theta.astype(np.float64)
+    # teacher-forced: the oracle's gradient with the GPU's correspondences
+    g_ref = O.icp_grad_given_nn(ref, src, mb, th64, nn)
+    floor = _grad_floor(ref, src, theta)
+    err = np.abs(g - g_ref).max(1)
+    bound = np.maximum(1e-4 * np.abs(g_ref).max(1), floor)
+    assert np.all(err <= bound), (err / np.abs(g_ref).max(1)).max()
+    # the GPU's correspondences are the oracle's up to near-ties of the FP32 transform
+    g_o, nn_o, _ = O.icp_grad(ref, src, mb, th64)
+    flips = nn != nn_o
+    if flips.any():
+        j, k = np.nonzero(flips)
+        q = np.stack([O.transform(th64[jj], src[mb[kk]][None])[0] for jj, kk in zip(j, k)])
+        d_gpu = np.linalg.norm(ref[nn[j, k]].astype(np.float64) - q, axis=1)
+        d_min = np.linalg.norm(ref[nn_o[j, k]].astype(np.float64) - q, axis=1)
+        assert np.all(d_gpu - d_min <= 8 * floor), (d_gpu - d_min).max()
+        assert flips.mean() < 0.01
+    return np.max(err / np.maximum(np.abs(g_ref).max(1), 1e-300)), int(flips.sum())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_icp_grad_box(ctx, mode):
+    d = synth.make_box_problem(3)
+    S.sicp_set_reference(ctx, d["ref"])
+    mb = O.minibatch(5, 0, d["src"].shape[0], 100)
+    _check_grad(ctx, d["ref"], d["src"], d["particles"], mb, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_icp_grad_kinect_small(ctx, mode):
+    d = synth.make_kinect_problem(4, M=20_000, N=4000, K=24)
+    S.sicp_set_reference(ctx, d["ref"])
+    mb = O.minibatch(6, 3, d["src"].shape[0], 300)
+    _check_grad(ctx, d["ref"], d["src"], d["particles"], mb, mode)
+
+
+def test_icp_grad_ragged_chunks(ctx):
+    """m that is not a multiple of the chunk size; single particle; m = N."""
+    d = synth.make_box_problem(8, M=700, N=333, K=3)
+    S.sicp_set_reference(ctx, d["ref"])
+    for m in (1, 33, 257, 333):
+        mb = O.minibatch(2, 1, 333, m)
+        for mode in MODES:
+            _check_grad(ctx, d["ref"], d["src"], d["particles"], mb, mode)
+            _check_grad(ctx, d["ref"], d["src"], d["particles"][:1], mb, mode)
+
+
+# ---------------------------------------------------------------- steps 5-6: Stein + Adam
+
+def _stein_case(K, seed, t, p):
+    rng = np.random.default_rng(seed)
+    th = np.c_[rng.uniform(-0.15, 0.15, (K, 3)), rng.uniform(-0.35, 0.35, (K, 3))].astype(np.float32)
+    if K > 3:
+        th[0, 3] = 3.1                      # rotation differences that cross +-pi
+        th[1, 3] = -3.1
+    gbar = (rng.normal(0, 1e-3, (K, 6))).astype(np.float32)
+    if t == 1:
+        am = np.zeros((K, 6), np.float32)
+        av = np.zeros((K, 6), np.float32)
+    else:
+        am = rng.normal(0, 1.0, (K, 6)).astype(np.float32)
+        av = rng.uniform(0.5, 4.0, (K, 6)).astype(np.float32)
+    return th, am, av, gbar
+
+
+@pytest.mark.parametrize("K", [1, 2, 32, 100, 200, 1500])
+@pytest.mark.parametrize("t", [1, 7])
+def test_stein_adam_matches_oracle(ctx, K, t):
+    p = S.sicp_default_params(lr=0.01)
+    N = 10_000
+    th, am, av, gbar = _stein_case(K, K * 10 + t, t, p)
+    th_g, am_g, av_g = th.copy(), am.copy(), av.copy()
+    phi, h = S.sicp_stein_adam(ctx, th_g, am_g, av_g, gbar, N, t, p)
+    th64 = th.astype(np.float64)
+    G = O.log_post_grad(th64, gbar.astype(np.float64), N)
+    h_t, h_r = O.bandwidths(th64)
+    assert abs(h[0] - h_t) <= 1e-5 * h_t and abs(h[1] - h_r) <= 1e-5 * h_r
+    phi_ref = O.stein_phi(th64, G, h_t, h_r)
+    err = np.abs(phi - phi_ref).max(1)
+    assert np.all(err <= np.maximum(1e-4 * np.abs(phi_ref).max(1), 1e-5 * np.abs(G).max())), err.max()
+    # Adam with the float32 constants the GPU used
+    x, mo, ve = th64.copy(), am.astype(np.float64), av.astype(np.float64)
+    O.adam(x, mo, ve, -phi_ref, t, float(np.float32(p.lr)), float(np.float32(p.beta1)),
+           float(np.float32(p.beta2)), float(np.float32(p.eps)))
+    g_ref, dg = -phi_ref, np.abs(phi - phi_ref)
+    lr = float(np.float32(p.lr))
+    bound = 2 * lr * np.minimum(1.0, 2 * dg / (np.abs(g_ref) + 1e-8)) + 1e-4 * lr + 4 * U32 * np.abs(x)
+    assert np.all(np.abs(th_g - x) <= bound)
+    assert np.allclose(am_g, mo, rtol=1e-4, atol=1e-4 * np.abs(mo).max())
+
+
+def test_moments_match_oracle(ctx):
+    rng = np.random.default_rng(3)
+    for K in (1, 2, 100, 4096):
+        th = rng.normal(0, 0.2, (K, 6)).astype(np.float32)
+        mean, cov = S.sicp_moments(ctx, th)
+        mo, co = O.moments(th.astype(np.float64))
+        assert np.allclose(mean, mo, rtol=1e-12, atol=1e-15)
+        assert np.allclose(cov, co, rtol=1e-10, atol=1e-15)
+
+
+# ---------------------------------------------------------------- whole run
+
+def _teacher_forced_run(ctx, d, params, mode, T):
+    """At every iteration feed the oracle's state to one GPU iteration (gradient,
+    then Stein + Adam on the GPU's gradient) and compare; advance the oracle
+    with its own step."""
+    ref, src = d["ref"], d["src"]
+    th = d["particles"].astype(np.float64).copy()
+    mom, vel = np.zeros_like(th), np.zeros_like(th)
+    N = src.shape[0]
+    p = S.sicp_default_params(T=T, m=params.m, lr=params.lr, seed=params.seed, nn_mode=mode)
+    worst_g = worst_phi = 0.0
+    flips = 0
+    for t in range(T):
+        mb = O.minibatch(params.seed, t, N, params.m)
+        th32 = th.astype(np.float32)
+        rel, nf = _check_grad(ctx, ref, src, th32, mb, mode)
+        worst_g, flips = max(worst_g, rel), flips + nf
+        g_gpu, _ = S.sicp_icp_grad(ctx, src, mb, th32, mode, want_nn=False)
+        tg, mg, vg = th32.copy(), mom.astype(np.float32), vel.astype(np.float32)
+        phi, _ = S.sicp_stein_adam(ctx, tg, mg, vg, g_gpu, N, t + 1, p)
+        th_in = th32.astype(np.float64)
+        G = O.log_post_grad(th_in, g_gpu.astype(np.float64), N)
+        phi_ref = O.stein_phi(th_in, G, *O.bandwidths(th_in))
+        e = (np.abs(phi - phi_ref).max(1) / np.maximum(np.abs(phi_ref).max(1), 1e-5 * np.abs(G).max()))
+        worst_phi = max(worst_phi, e.max())
+        O.step(ref, src, th, mom, vel, params, t)
+    return worst_g, worst_phi, flips
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_teacher_forced_box_run(ctx, mode):
+    d = synth.make_box_problem(0)
+    S.sicp_set_reference(ctx, d["ref"])
+    params = O.Params(T=100, m=100, lr=float(np.float32(0.01)), seed=7)
+    wg, wp, flips = _teacher_forced_run(ctx, d, params, mode, 100)
+    print(f"box mode={mode}: worst gbar rel err {wg:.2e}, worst phi rel err {wp:.2e}, NN near-tie flips {flips}")
+    assert wp <= 1e-4
+
+
+def test_teacher_forced_kinect_grid(ctx):
+    d = synth.make_kinect_problem(2, M=20_000, N=4000, K=32)
+    S.sicp_set_reference(ctx, d["ref"])
+    params = O.Params(T=12, m=300, lr=float(np.float32(0.01)), seed=3)
+    wg, wp, flips = _teacher_forced_run(ctx, d, params, S.SICP_NN_GRID, 12)
+    print(f"kinect grid: worst gbar rel err {wg:.2e}, worst phi rel err {wp:.2e}, NN near-tie flips {flips}")
+    assert wp <= 1e-4
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_free_run_box_against_oracle(ctx, mode):
+    d = synth.make_box_problem(0)
+    S.sicp_set_reference(ctx, d["ref"])
+    p = S.sicp_default_params(T=100, m=100, lr=0.01, seed=7, nn_mode=mode)
+    th, mean, cov = S.sicp_register(ctx, d["src"], d["particles"], p)
+    th_o, mean_o, cov_o = O.register(d["ref"], d["src"], d["particles"],
+                                     O.Params(T=100, m=100, lr=float(np.float32(0.01)), seed=7))
+    dm = np.abs(mean - mean_o)
+    rel = np.abs(th - th_o).max() / np.abs(th_o).max()
+    print(f"box free run mode={mode}: particle rel err {rel:.2e}, mean err t {dm[:3].max():.2e} m, "
+          f"r {math.degrees(dm[3:].max()):.2e} deg")
+    # the moments the library returns are those of the particles it returns
+    mo, co = O.moments(th.astype(np.float64))
+    assert np.allclose(mean, mo, atol=1e-12) and np.allclose(cov, co, atol=1e-12)
+    assert np.all(np.isfinite(th))
+
+
+def test_register_special_cases_and_residency(ctx):
+    d = synth.make_box_problem(5, K=8)
+    S.sicp_set_reference(ctx, d["ref"])
+    p0 = S.sicp_default_params(T=0, m=50, nn_mode=S.SICP_NN_GRID)
+    th, mean, cov = S.sicp_register(ctx, d["src"], d["particles"], p0)
+    assert np.array_equal(th, d["particles"])
+    mo, co = O.moments(d["particles"].astype(np.float64))
+    assert np.allclose(mean, mo, atol=1e-12)
+    p = S.sicp_default_params(T=20, m=50, seed=4, nn_mode=S.SICP_NN_GRID)
+    a = S.sicp_register(ctx, d["src"], d["particles"], p)
+    b = S.sicp_register(ctx, torch.from_numpy(d["src"]).cuda(), torch.from_numpy(d["particles"]).cuda(), p)
+    assert np.array_equal(a[0], b[0].cpu().numpy()) and np.array_equal(a[1], b[1].cpu().numpy())
+    c = S.sicp_register(ctx, d["src"], d["particles"], p)          # replay of the captured graph
+    assert np.array_equal(a[0], c[0])
+    k1 = S.sicp_register(ctx, d["src"], d["particles"][:1], p)     # K = 1: SGD-ICP with Adam
+    assert np.all(np.isfinite(k1[0])) and np.all(k1[2] == 0)
+
+
+def test_errors_are_codes_not_faults(ctx):
+    d = synth.make_box_problem(6, K=4)
+    fresh = S.sicp_create(0)
+    try:
+        with pytest.raises(S.SicpError) as e:
+            S.sicp_register(fresh, d["src"], d["particles"], S.sicp_default_params(T=2, m=10))
+        assert e.value.code == S.SICP_ENOREF
+    finally:
+        S.sicp_destroy(fresh)
+    S.sicp_set_reference(ctx, d["ref"])
+    bad = d["src"].copy()
+    bad[3, 1] = np.nan
+    cases = [(d["src"], d["particles"], dict(m=10_000)), (bad, d["particles"], dict(m=10)),
+             (d["src"], d["particles"], dict(m=10, nn_mode=9)), (d["src"], d["particles"], dict(m=10, T=-1)),
+             (d["src"], np.zeros((0, 6), np.float32), dict(m=10))]
+    for src, parts, kw in cases:
+        with pytest.raises(S.SicpError) as e:
+            S.sicp_register(ctx, src, parts, S.sicp_default_params(**{"T": 2, **kw}))
+        assert e.value.code == S.SICP_EINVAL
+    with pytest.raises(S.SicpError):
+        S.sicp_set_reference(ctx, np.full((3, 3), np.inf, np.float32))
+    S.sicp_set_reference(ctx, d["ref"])                 # the context is still usable
+    out = S.sicp_register(ctx, d["src"], d["particles"], S.sicp_default_params(T=2, m=10))
+    assert np.all(np.isfinite(out[0]))
+
+
+# ---------------------------------------------------------------- full size, bench launch configuration
+
+def test_full_size_kinect_sampled(ctx):
+    """The benchmark's workload (50k-point reference, 10k source, 100 particles,
+    minibatch 300, 150 iterations, grid search) in its launch configuration:
+    minibatches of sampled iterations bit-exact, the first iteration's gradient
+    teacher-forced against the oracle, the returned moments consistent."""
+    d = synth.make_kinect_problem(0)
+    cfg = synth.WORKLOADS["kinect"]
+    S.sicp_set_reference(ctx, d["ref"])
+    p = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, nn_mode=S.SICP_NN_GRID)
+    S.sicp_profile(ctx, 5)
+    S.sicp_stats(ctx, True)
+    th, mean, cov = S.sicp_register(ctx, d["src"], d["particles"], p)
+    st = S.sicp_stats(ctx, False)
+    prof = S.sicp_profile(ctx, 0)
+    assert st[0] == cfg["T"] * cfg["m"] * d["particles"].shape[0]
+    assert prof[1] == 30 and prof[0] > 0
+    N = d["src"].shape[0]
+    mbs = S.sicp_minibatch(ctx, 0, 0, cfg["T"], N, cfg["m"])
+    for t in (0, 74, 149):
+        assert np.array_equal(mbs[t], O.minibatch(0, t, N, cfg["m"]))
+    _check_grad(ctx, d["ref"], d["src"], d["particles"], mbs[0], S.SICP_NN_GRID)
+    mo, co = O.moments(th.astype(np.float64))
+    assert np.allclose(mean, mo, atol=1e-12) and np.allclose(cov, co, atol=1e-12)
+    assert np.all(np.isfinite(th))
