@@ -263,11 +263,13 @@ def run_ours(args):
     st = S.sicp_stats(ctx, False).astype(np.float64)
     queries = st[0]
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
+    coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
     bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q
-    S.sicp_profile(ctx, args.profile_stride)
-    step()   # capture the profiling graphs outside the timed region
-    step()
-    S.sicp_profile(ctx, args.profile_stride)   # reset totals
+    if args.profile_stride > 0:
+        S.sicp_profile(ctx, args.profile_stride)
+        step()   # capture the profiling graphs outside the timed region
+        step()
+        S.sicp_profile(ctx, args.profile_stride)   # reset totals
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -306,7 +308,8 @@ def run_ours(args):
                 "traffic": tpq * queries_per_launch if tpq else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
                 "launches_timed": int(prof[1]),
-                "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query},
+                "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
+                              "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
                 "stein_adam_avg_launch_us": 1e3 * prof[2] / prof[3] if prof[3] else None}
 
     e2e = None

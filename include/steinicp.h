@@ -102,7 +102,8 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
  * particles_out [K][6] after T iterations; mean6 [6] and cov36 [6][6]
  * (row-major, divisor K-1, zero for K = 1) of the final particles, both
  * float64 (may be NULL).  T = 0 returns the input particles and their
- * moments.  Errors: SICP_EINVAL (N < 1, K < 1, m outside [1, N], T < 0,
+ * moments.  1 <= K <= 2048.  Errors: SICP_EINVAL (N < 1, K outside [1, 2048],
+ * m outside [1, N], T < 0,
  * bad mode, non-finite input), SICP_ENOREF, SICP_ENOSURROGATE, SICP_ENOMEM,
  * SICP_ECUDA. */
 int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in,
@@ -156,11 +157,13 @@ int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6
 
 /* Work counters of the grid search (no counterpart in the paper; they state
  * the algorithmic bytes a search moved).  Copies the counters accumulated
- * since the previous call into out4 (may be NULL): queries, rows examined,
- * row segments read (two cell offsets each), candidate points read (16 bytes
- * each); then zeroes them and turns counting on (enable = 1) or off.
- * Counting adds one warp-aggregated atomic per 32 queries. */
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out4);
+ * since the previous call into out6 (may be NULL): queries, rows examined
+ * (one row span each), row segments read (two cell offsets each), candidate
+ * points read (16 bytes each), queries that went on to the coarse level,
+ * queries that went on to the exhaustive scan; then zeroes them and turns
+ * counting on (enable = 1) or off.  Counting adds six warp-aggregated atomics
+ * per 32 lanes. */
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out6);
 
 /* Kernel timing inside sicp_register (no counterpart in the paper).  With
  * stride s > 0 the captured loop records CUDA events around the gradient and

@@ -252,8 +252,9 @@ def sicp_moments(ctx, particles):
 
 def sicp_stats(ctx, enable: bool = True):
     """Grid-search counters since the last call (queries, rows, segments,
-    points) as a uint64 array; then resets them and sets counting on/off."""
-    out = np.zeros(4, np.uint64)
+    points, coarse-level queries, exhaustive-scan queries) as a uint64 array;
+    then resets them and sets counting on/off."""
+    out = np.zeros(6, np.uint64)
     _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 

@@ -56,7 +56,7 @@ struct LoopKey {
     int32_t pi[4];          // T, m, nn_mode, prior
     float pf[16];           // lr, betas, eps, prior mu/sigma/kappa
     uint64_t seed;
-    const void* ptrs[10];
+    const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -238,11 +238,11 @@ void collect_profile(sicp_ctx* ctx, GraphSlot& s) {
 }
 
 cudaError_t launch_grad(sicp_ctx* ctx, int32_t mode, const GradArgs& g) {
-    if (mode == SICP_NN_GRID) return launch_grad_grid(g, ctx->grid.v, ctx->stream);
+    if (mode == SICP_NN_GRID) return launch_grad_grid(g, ctx->search, ctx->stream);
     return launch_grad_brute(g, ctx->ref4, ctx->M, ctx->stream);
 }
 
-constexpr int32_t kMaxK = 4096;
+constexpr int32_t kMaxK = 2048;
 constexpr int64_t kMaxN = 0x7fffffff;
 constexpr int64_t kMaxM = (int64_t)1 << 30;
 
@@ -281,6 +281,10 @@ int sicp_create(sicp_ctx** out, int device, void* cuda_stream) {
         sicp_destroy(c);
         return SICP_ECUDA;
     }
+    if (search_table_init(c) != SICP_OK) {
+        sicp_destroy(c);
+        return SICP_ENOMEM;
+    }
     if (ensure(c, c->flags, 4 * sizeof(int)) != SICP_OK) {
         sicp_destroy(c);
         return SICP_ENOMEM;
@@ -295,14 +299,18 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     delete c->graphs;
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
-                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats};
+                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
-    void* gp[] = {c->grid.sorted, c->grid.cell_start, c->grid.row_span, c->grid.brick_rep, c->grid.cell_of,
-                  c->grid.counts, c->grid.scan_sums};
-    for (void* p : gp)
-        if (p) cudaFree(p);
+    for (Grid* g : {&c->grid, &c->grid2}) {
+        void* gp[] = {g->sorted, g->cell_start, g->row_span, g->cell_of, g->counts, g->scan_sums, g->seed,
+                      g->seed_tmp};
+        for (void* p : gp)
+            if (p) cudaFree(p);
+    }
+    if (c->tab_off) cudaFree(c->tab_off);
+    if (c->tab_lb2) cudaFree(c->tab_lb2);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -394,7 +402,7 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     if (on_device) SICP_CUDA(launch_check_finite((const float*)d_q, 3 * n, (int*)ctx->flags.p, ctx->stream));
     if (mode == SICP_NN_GRID)
-        SICP_CUDA(launch_nn_grid(ctx->grid.v, (const float*)d_q, n, d_idx, d_d2, stats_ptr(ctx), ctx->stream));
+        SICP_CUDA(launch_nn_grid(ctx->search, (const float*)d_q, n, d_idx, d_d2, stats_ptr(ctx), ctx->stream));
     else
         SICP_CUDA(launch_nn_brute(ctx->ref4, ctx->M, (const float*)d_q, n, d_idx, d_d2, ctx->stream));
     int flags[4];
@@ -442,7 +450,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
         d_mb = aux + b_src;
         d_th = aux + b_src + b_mb;
     }
-    const int chunks = grad_layout(m).chunks;
+    const int chunks = (mode == SICP_NN_GRID ? grad_layout_grid(m) : grad_layout(m)).chunks;
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
     if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
     if ((rc = ensure(ctx, ctx->tmp_out, (sizeof(float) * 6 + sizeof(int32_t) * (size_t)m) * K))) return rc;
@@ -465,8 +473,14 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.partial = (float*)ctx->partial.p;
     g.out_nn = d_nn;
     g.stats = stats_ptr(ctx);
+    g.gbar = d_g;
+    g.inv_m = 1.f / (float)m;
+    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)(K / 8 + 1)))) return rc;
+    g.done = (unsigned*)ctx->done.p;
+    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)(K / 8 + 1), ctx->stream));
     SICP_CUDA(launch_grad(ctx, mode, g));
-    SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
+    if (mode != SICP_NN_GRID)
+        SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
     if ((rc = copy_out(ctx, out_gbar, d_g, sizeof(float) * 6 * K, on_device))) return rc;
     if (out_nn && (rc = copy_out(ctx, out_nn, d_nn, sizeof(int32_t) * (size_t)m * K, on_device))) return rc;
     return sync(ctx);
@@ -547,7 +561,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
         return set_err(ctx, SICP_EINVAL, "non-finite input");
     DeviceScope ds(ctx->device);
-    const int chunks = grad_layout(p.m).chunks;
+    const int chunks = (p.nn_mode == SICP_NN_GRID ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
     const size_t b_th = sizeof(float) * 6 * K;
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
     if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m))) return rc;
@@ -556,6 +570,9 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if ((rc = ensure(ctx, ctx->adam_v, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
+    if ((rc = ensure(ctx, ctx->gbar, b_th))) return rc;
+    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)(K / 8 + 1)))) return rc;
+    const bool grid = p.nn_mode == SICP_NN_GRID;
 
     const void *d_src, *d_th0;
     if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
@@ -567,6 +584,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)(K / 8 + 1), ctx->stream));
 
     const int stride = ctx->prof_stride;
     LoopKey key;
@@ -602,6 +620,8 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     key.ptrs[7] = ctx->grid.sorted;
     key.ptrs[8] = ctx->ref4;
     key.ptrs[9] = stats_ptr(ctx);
+    key.ptrs[10] = ctx->gbar.p;
+    key.ptrs[11] = ctx->done.p;
 
     GraphCache& gc = *ctx->graphs;
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
@@ -616,6 +636,9 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
         g.partial = (float*)ctx->partial.p;
         g.out_nn = nullptr;
         g.stats = stats_ptr(ctx);
+        g.gbar = (float*)ctx->gbar.p;
+        g.done = (unsigned*)ctx->done.p;
+        g.inv_m = 1.f / (float)p.m;
         int np = 0;
         for (int32_t t = 0; t < p.T; ++t) {
             const bool timed = prof && stride > 0 && (t % stride) == 0;
@@ -623,8 +646,11 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
             g.mb = (const int32_t*)ctx->mb.p + (size_t)t * p.m;
             SICP_CUDA(launch_grad(ctx, p.nn_mode, g));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
-            SteinArgs a = stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
-                                     (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
+            // the grid kernel folds its partials into gbar itself; the exhaustive one leaves `chunks` partials
+            SteinArgs a = grid ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
+                                            (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t + 1)
+                               : stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
+                                            (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
             SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;
@@ -679,21 +705,21 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     return sync(ctx);
 }
 
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out4) {
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out6) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     DeviceScope ds(ctx->device);
-    int rc = ensure(ctx, ctx->stats, 4 * sizeof(unsigned long long));
+    int rc = ensure(ctx, ctx->stats, 6 * sizeof(unsigned long long));
     if (rc) return rc;
-    if (out4) {
-        unsigned long long h[4] = {0, 0, 0, 0};
+    if (out6) {
+        unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
         if (ctx->stats_on) {
             SICP_CUDA(cudaMemcpyAsync(h, ctx->stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
             if ((rc = sync(ctx))) return rc;
         }
-        for (int a = 0; a < 4; ++a) out4[a] = (uint64_t)h[a];
+        for (int a = 0; a < 6; ++a) out6[a] = (uint64_t)h[a];
     }
-    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 6 * sizeof(unsigned long long), ctx->stream));
     ctx->stats_on = enable != 0;
     return sync(ctx);
 }

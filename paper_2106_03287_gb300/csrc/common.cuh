@@ -91,33 +91,49 @@ __device__ __forceinline__ bool better(float d2, int idx, float bd, int bi) {
 // Uniform voxel grid over the reference bounding box.  Points are stored
 // sorted by linear cell id (x fastest), so every run of consecutive cells along
 // x is one contiguous range of `sorted`.
-constexpr int kBrick = 8;           // bricks of 8 x 8 x 8 cells carry one representative point
-constexpr int32_t kEmpty = 0x7f7f7f7f;
-
 struct GridView {
     float3 origin;
     float cell, inv_cell, tol;      // tol: absolute slack covering rounding of cell bounds
     int3 dims;                      // cells per axis
-    int3 bdims;                     // bricks per axis
     const float4* sorted;           // M, w = original index bits
     const int32_t* cell_start;      // ncells + 1
     const int2* row_span;           // dims.y * dims.z: first and last non-empty x of the row
-    const int32_t* brick_rep;       // bricks: lowest original index in the brick, kEmpty if none
-    const float4* ref4;             // M, original order
+    const int32_t* seed;            // ncells: position in `sorted` of a point near the cell centre (fine level)
 };
 
 struct Grid {
     GridView v{};
-    int64_t ncells = 0, nbricks = 0;
+    int64_t ncells = 0;
     float4* sorted = nullptr;
     int32_t* cell_start = nullptr;
     int2* row_span = nullptr;
-    int32_t* brick_rep = nullptr;
     int32_t* cell_of = nullptr;     // M: cell id of each reference point (build scratch)
     int32_t* counts = nullptr;      // ncells + 1 (build scratch)
     int32_t* scan_sums = nullptr;   // build scratch
-    size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_bricks = 0, cap_rows = 0,
-           cap_sums = 0;
+    int32_t* seed = nullptr;        // ncells (fine level only)
+    int32_t* seed_tmp = nullptr;    // ncells (build scratch)
+    size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_rows = 0, cap_sums = 0,
+           cap_seed = 0, cap_seed_tmp = 0;
+};
+
+// Row offsets (dy, dz) in cell units, in increasing order of a lower bound on
+// the distance from a query (mirrored into the upper half of its cell) to the
+// row; lb2 holds that bound squared, in cell units squared.
+struct SearchTable {
+    const short2* off;
+    const float* lb2;
+    int n;
+    int upto[8];   // upto[k]: number of entries with lb2 <= (1.5 * 2^k)^2
+};
+
+// Everything an exact grid search reads: a fine and a coarse level over the
+// same points, the row table, and the points in original order for the
+// exhaustive fallback.
+struct GridSearch {
+    GridView fine, coarse;
+    SearchTable tab;
+    const float4* ref4;
+    int M;
 };
 
 struct Buf {
@@ -140,12 +156,15 @@ struct sicp_ctx {
     int64_t M = 0;
     float4* ref4 = nullptr;   // original order, w = index bits
     size_t ref_cap = 0;
-    sicp::Grid grid;
+    sicp::Grid grid, grid2;           // fine and coarse levels
+    sicp::GridSearch search{};
+    short2* tab_off = nullptr;
+    float* tab_lb2 = nullptr;
     float3 ref_lo = {0, 0, 0}, ref_hi = {0, 0, 0};
 
     // per-problem and scratch buffers (grow-only)
     sicp::Buf src4, mb, theta, adam_m, adam_v, partial, moments, flags, tmp_in, tmp_out, tmp_aux;
-    sicp::Buf bbox, stats;
+    sicp::Buf bbox, stats, gbar, done;
     bool stats_on = false;
     int prof_stride = 0;
     double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
@@ -190,12 +209,13 @@ cudaError_t launch_minibatch(uint64_t seed, int64_t t0, int32_t T, int64_t N, in
 cudaError_t launch_nn_brute(const float4* ref, int64_t M, const float* q, int64_t n,
                             int32_t* idx, float* d2, cudaStream_t s);
 
-// The fused gradient kernels split a particle's m minibatch entries over
-// `chunks` CTAs of `chunk_threads` threads (a multiple of 32, at most 256).
+// The fused gradient kernels write one partial sum per (chunk of minibatch
+// entries, particle); `chunks` is how many chunks a launch uses.
 struct GradLayout {
     int chunks, threads;
 };
-GradLayout grad_layout(int32_t m);
+GradLayout grad_layout(int32_t m);            // exhaustive search: threads per CTA, one query each
+GradLayout grad_layout_grid(int32_t m);       // grid search: a lane group per query
 
 struct GradArgs {
     const float4* src;     // N
@@ -205,7 +225,13 @@ struct GradArgs {
     int32_t K;
     float* partial;        // [chunks][K][6] sums of gradient terms (not divided by m)
     int32_t* out_nn;       // K x m or null
-    unsigned long long* stats;  // search work counters (queries, rows, segments, points) or null
+    unsigned long long* stats;  // search work counters or null
+    // grid search only: the last CTA of each particle block folds the block's
+    // chunk partials into gbar = inv_m * sum (fixed chunk order); `done` holds
+    // one arrival counter per particle block, zero between launches.
+    float* gbar;           // K x 6
+    unsigned* done;        // ceil(K / 8)
+    float inv_m;
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
 
@@ -230,8 +256,9 @@ cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStr
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);
-cudaError_t launch_nn_grid(const GridView& g, const float* q, int64_t n, int32_t* idx, float* d2,
+int search_table_init(sicp_ctx* ctx);
+cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32_t* idx, float* d2,
                            unsigned long long* stats, cudaStream_t s);
-cudaError_t launch_grad_grid(const GradArgs& a, const GridView& g, cudaStream_t s);
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch& g, cudaStream_t s);
 
 }  // namespace sicp

@@ -1,35 +1,58 @@
 // Uniform voxel grid for the exact nearest-neighbour step (Eq. correspondences).
 //
-// Build, once per reference cloud:
-//   bounding box -> cell id of every point -> per-cell counts -> exclusive
-//   scan (cell_start) -> scatter into `sorted` (float4, w = original index)
-//   -> per row (y, z) the first and last non-empty x -> per brick of 8^3 cells
-//   the lowest original index it holds.
+// Build, once per reference cloud, for a fine level (cell c) and a coarse
+// level (cell 4c) over the same points:
+//   cell id of every point -> per-cell counts -> exclusive scan (cell_start)
+//   -> scatter into `sorted` (float4, w = original index) -> order each cell
+//   by index -> per row (y, z) the first and last non-empty x.
+// The fine level also gets a seed map: for every cell, a point close to the
+// cell centre, found by jump flooding (each cell repeatedly adopts the
+// closest seed among its neighbours at offsets n/2, n/4, ..., 1, 1).
 // Cells are numbered x fastest, so a run of cells along x is one contiguous
 // range of `sorted`: the search reads whole row segments with float4 loads.
 //
-// Exact search of query q (the same fp32 squared distance and lowest-index
-// tie rule as the exhaustive scan, so both give identical answers):
-//   1. visit every cell within 1.5 cells of q, row segment by row segment,
-//      centre rows first; if a point was found, it is the answer, because all
-//      cells closer than it were visited;
-//   2. otherwise take the best brick representative in the first two
-//      non-empty brick rings as an upper bound, then visit every cell whose box
-//      lies within the current best distance (the bound shrinks as points are
-//      found; empty rows are skipped through the row spans).
+// Exact search of one query by one warp.  A host-built table lists row
+// offsets (dy, dz) in increasing order of a lower bound on the distance from
+// the query to the row (offsets mirrored into the half of the cell the query
+// lies in).  A round gives each lane one row; the lane clips the row to the
+// ball of the current bound (skipping empty or out-of-reach rows) and
+// publishes the row segment; the warp flattens the round's segments and
+// evaluates their points 32 at a time, so all lanes do the same work; a warp
+// minimum (squared distance, then lowest index) closes the round.
+// The seed of the query's cell gives a first point; a round over the
+// 3 x 3 x 3 cells around that point brings the bound close to the true
+// distance; then the table is walked from the start with that bound on the
+// fine level (bound under 6 cells) or the coarse level, until the next row is
+// out of reach.  A query the table cannot settle scans all points.
+// Every search uses the same fp32 squared distance and tie rule as the
+// exhaustive scan, so both give the same answer.
+//
 // Pruning is conservative: cell bounds are widened by `tol` and the squared
 // bound by a relative 5e-7, so rounding can only add visits, never drop one.
 #include <float.h>
 #include <math.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
 namespace sicp {
 namespace {
 
-constexpr int kQueryThreads = 128;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;  // queries in flight per CTA, one warp each
+constexpr int kGradThreads = 64;       // gradient kernel CTA: one warp per particle
+constexpr int kPb = kGradThreads / 32;  // particles per CTA in the gradient kernel
+constexpr int kKc = 4;                 // minibatch entries per warp in the gradient kernel
+constexpr int kFirstRound = 8;         // table entries in the first round of a walk
+constexpr int kCoarseFactor = 4;
+constexpr float kFineReach = 6.f;      // the far phase proves on the fine level below this many cells
+constexpr int kTableRadius = 48;
 constexpr int64_t kMaxCells = 1 << 23;
 constexpr float kSlack = 1.0000005f;
+constexpr int kNone = 0x7fffffff;
+constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ __forceinline__ int cell_coord(float v, float o, float inv, int n) {
     float f = (v - o) * inv;
@@ -50,214 +73,290 @@ __device__ __forceinline__ float slab(float v, float o, float c, int i, float to
     return fmaxf(d - tol, 0.f);
 }
 
-// Per-query work counters: rows examined, row segments read, candidate points.
+// Squared pruning radius: best widened by kSlack, kept finite.
+__device__ __forceinline__ float bound2(float best) { return fminf(best * kSlack, FLT_MAX); }
+
+// Per-lane work counters: rows examined, row segments read, candidate points;
+// lane 0 also counts queries, queries that reached the far phase and queries
+// that reached the exhaustive scan.
 struct Work {
-    unsigned rows = 0, segs = 0, pts = 0;
+    unsigned rows = 0, segs = 0, pts = 0, queries = 0, far = 0, exh = 0;
 };
 
-__device__ __forceinline__ void scan_range(const float4* __restrict__ pts, int b, int e, float3 q, float& best,
-                                           int& bi, float3& bp, Work& w) {
-    w.segs += 1;
-    w.pts += (unsigned)(e - b);
-    for (int p = b; p < e; ++p) {
-        const float4 r = __ldg(pts + p);
-        const float d = dist2(r, q);
-        const int id = __float_as_int(r.w);
-        if (better(d, id, best, bi)) {
-            best = d;
-            bi = id;
-            bp = make_float3(r.x, r.y, r.z);
-        }
+struct Best {
+    float d;
+    int i;
+    float3 p;
+};
+
+__device__ __forceinline__ void take(Best& B, float4 r, float3 q, int id) {
+    const float d = dist2(r, q);
+    if (better(d, id, B.d, B.i)) {
+        B.d = d;
+        B.i = id;
+        B.p = make_float3(r.x, r.y, r.z);
     }
 }
 
-// Squared pruning radius: min(best, cap2) widened by kSlack, kept finite.
-__device__ __forceinline__ float bound2(float best, float cap2) {
-    return fminf(fminf(best, cap2) * kSlack, FLT_MAX);
+// Warp minimum (distance, then lowest index); every lane ends with the result.
+// Distances are non-negative, so their bit patterns order like unsigned ints.
+__device__ __forceinline__ void warp_min(Best& B) {
+    const unsigned db = __float_as_uint(B.d);
+    const unsigned md = __reduce_min_sync(kFull, db);
+    const unsigned mi = __reduce_min_sync(kFull, db == md ? (unsigned)B.i : 0xffffffffu);
+    const unsigned who = __ballot_sync(kFull, db == md && (unsigned)B.i == mi);
+    const int src = __ffs(who) - 1;
+    B.d = __uint_as_float(md);
+    B.i = (int)mi;
+    B.p.x = __shfl_sync(kFull, B.p.x, src);
+    B.p.y = __shfl_sync(kFull, B.p.y, src);
+    B.p.z = __shfl_sync(kFull, B.p.z, src);
 }
 
-// Visit all cells whose box lies within sqrt(min(best, cap2)) of q.
-__device__ void ball_rows(const GridView& g, float3 q, int cy, int cz, float cap2, float& best, int& bi,
-                          float3& bp, Work& w) {
-    for (int oz = 0;; ++oz) {
-        bool live_z = false;
-        for (int sz = 0; sz < 2; ++sz) {
-            if (oz == 0 && sz == 1) break;
-            const int z = sz ? cz - oz : cz + oz;
-            if (z < 0 || z >= g.dims.z) continue;
-            const float dz = slab(q.z, g.origin.z, g.cell, z, g.tol);
-            if (bound2(best, cap2) - dz * dz < 0.f) continue;
-            live_z = true;
-            for (int oy = 0;; ++oy) {
-                bool live_y = false;
-                for (int sy = 0; sy < 2; ++sy) {
-                    if (oy == 0 && sy == 1) break;
-                    const int y = sy ? cy - oy : cy + oy;
-                    if (y < 0 || y >= g.dims.y) continue;
-                    const float dy = slab(q.y, g.origin.y, g.cell, y, g.tol);
-                    const float rem = bound2(best, cap2) - dz * dz - dy * dy;
-                    if (rem < 0.f) continue;
-                    live_y = true;
-                    const int rowi = z * g.dims.y + y;
-                    w.rows += 1;
-                    const int2 span = __ldg(g.row_span + rowi);
-                    if (span.x > span.y) continue;
-                    const float r = sqrtf(rem) + g.tol;
-                    const int x0 = max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), span.x);
-                    const int x1 = min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), span.y);
-                    if (x0 > x1) continue;
+// Every row from table entry e on is farther than the current best.
+__device__ __forceinline__ bool cleared(const GridView& g, const SearchTable& tab, int e, float best) {
+    const float lbd = sqrtf(__ldg(tab.lb2 + e)) * g.cell - g.tol;
+    return lbd > 0.f && lbd * lbd > bound2(best);
+}
+
+// One round: lane l contributes row (y, z) if `has`, limited to cells
+// [xlo, xhi] along x and clipped to the ball of squared radius clip2.
+__device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, int xlo, int xhi, float clip2,
+                           Best& B, Work& w) {
+    const int lane = threadIdx.x & 31;
+    int b = 0, len = 0;
+    if (has && y >= 0 && y < g.dims.y && z >= 0 && z < g.dims.z) {
+        const float dz = slab(q.z, g.origin.z, g.cell, z, g.tol);
+        const float dy = slab(q.y, g.origin.y, g.cell, y, g.tol);
+        const float rem = clip2 - dz * dz - dy * dy;
+        if (rem >= 0.f) {
+            w.rows += 1;
+            const int rowi = z * g.dims.y + y;
+            const int2 span = __ldg(g.row_span + rowi);
+            if (span.x <= span.y) {
+                const float r = sqrtf(rem) + g.tol;
+                const int x0 = max(max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), span.x), xlo);
+                const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), span.y), xhi);
+                if (x0 <= x1) {
                     const int64_t row = (int64_t)rowi * g.dims.x;
-                    scan_range(g.sorted, __ldg(g.cell_start + row + x0), __ldg(g.cell_start + row + x1 + 1), q,
-                               best, bi, bp, w);
-                }
-                if (!live_y) break;
-            }
-        }
-        if (!live_z) break;
-    }
-}
-
-// Upper bound from brick representatives: best over the first non-empty
-// Chebyshev ring of bricks around the query's brick and the ring after it.
-__device__ void brick_seed(const GridView& g, float3 q, int cx, int cy, int cz, float& best, int& bi, float3& bp,
-                           Work& w) {
-    const int bx = cx / kBrick, by = cy / kBrick, bz = cz / kBrick;
-    const int maxr = max(max(g.bdims.x, g.bdims.y), g.bdims.z);
-    int found_at = -1;
-    for (int r = 0; r < maxr; ++r) {
-        for (int dz = -r; dz <= r; ++dz) {
-            const int z = bz + dz;
-            if (z < 0 || z >= g.bdims.z) continue;
-            for (int dy = -r; dy <= r; ++dy) {
-                const int y = by + dy;
-                if (y < 0 || y >= g.bdims.y) continue;
-                const bool face = (dz == -r || dz == r || dy == -r || dy == r);
-                const int step = (face || r == 0) ? 1 : 2 * r;
-                for (int dx = -r; dx <= r; dx += step) {
-                    const int x = bx + dx;
-                    if (x < 0 || x >= g.bdims.x) continue;
-                    const int rep = __ldg(g.brick_rep + ((int64_t)z * g.bdims.y + y) * g.bdims.x + x);
-                    w.rows += 1;
-                    if (rep == kEmpty) continue;
-                    w.pts += 1;
-                    const float4 p = __ldg(g.ref4 + rep);
-                    const float d = dist2(p, q);
-                    if (better(d, rep, best, bi)) {
-                        best = d;
-                        bi = rep;
-                        bp = make_float3(p.x, p.y, p.z);
-                    }
-                    if (found_at < 0) found_at = r;
+                    b = __ldg(g.cell_start + row + x0);
+                    len = __ldg(g.cell_start + row + x1 + 1) - b;
+                    w.segs += len > 0;
                 }
             }
         }
-        if (found_at >= 0 && r >= found_at + 1) break;
     }
-}
-
-__device__ __forceinline__ void grid_search(const GridView& g, float3 q, float& best, int& bi, float3& bp,
-                                            Work& w) {
-    best = FLT_MAX;
-    bi = 0x7fffffff;
-    bp = make_float3(0.f, 0.f, 0.f);
-    const int cx = cell_coord(q.x, g.origin.x, g.inv_cell, g.dims.x);
-    const int cy = cell_coord(q.y, g.origin.y, g.inv_cell, g.dims.y);
-    const int cz = cell_coord(q.z, g.origin.z, g.inv_cell, g.dims.z);
-    const float r0 = 1.5f * g.cell;
-    ball_rows(g, q, cy, cz, r0 * r0, best, bi, bp, w);
-    if (best <= r0 * r0) return;
-    brick_seed(g, q, cx, cy, cz, best, bi, bp, w);
-    ball_rows(g, q, cy, cz, FLT_MAX, best, bi, bp, w);
-}
-
-// Warp-aggregated accumulation of the work counters (stats: queries, rows, segments, points).
-__device__ __forceinline__ void add_stats(unsigned long long* stats, bool active, const Work& w) {
-    unsigned long long v[4] = {active ? 1ull : 0ull, w.rows, w.segs, w.pts};
+    // flatten the round's segments: exclusive offsets and total
+    int incl = len;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], off);
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += v;
     }
-    if ((threadIdx.x & 31) == 0) {
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    const int excl = incl - len;
+    // flattened point t belongs to the last lane whose offset is <= t
+    Best L = B;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        int o = 0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) atomicAdd(stats + a, v[a]);
+        for (int step = 16; step > 0; step >>= 1) {
+            const int ex = __shfl_sync(kFull, excl, o + step);
+            if (ex <= t) o += step;
+        }
+        const int ob = __shfl_sync(kFull, b, o);
+        const int oe = __shfl_sync(kFull, excl, o);
+        if (t < total) {
+            const float4 r = __ldg(g.sorted + ob + (t - oe));
+            take(L, r, q, __float_as_int(r.w));
+        }
     }
+    if (lane == 0) w.pts += (unsigned)total;
+    warp_min(L);
+    B = L;
 }
 
-__global__ void __launch_bounds__(kQueryThreads) k_nn_grid(GridView g, const float* __restrict__ q, int64_t n,
-                                                           int32_t* __restrict__ idx, float* __restrict__ d2,
-                                                           unsigned long long* __restrict__ stats) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    Work w;
-    if (i < n) {
-        const float3 qq = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
-        float best;
-        int bi;
-        float3 bp;
-        grid_search(g, qq, best, bi, bp, w);
-        idx[i] = bi != 0x7fffffff ? bi : -1;
-        if (d2) d2[i] = best;
-    }
-    if (stats) add_stats(stats, i < n, w);
+struct QueryCell {
+    int cy, cz, sy, sz;
+};
+
+__device__ __forceinline__ QueryCell query_cell(const GridView& g, float3 q) {
+    QueryCell c;
+    c.cy = cell_coord(q.y, g.origin.y, g.inv_cell, g.dims.y);
+    c.cz = cell_coord(q.z, g.origin.z, g.inv_cell, g.dims.z);
+    const float fy = fminf(fmaxf((q.y - g.origin.y) * g.inv_cell - (float)c.cy, 0.f), 1.f);
+    const float fz = fminf(fmaxf((q.z - g.origin.z) * g.inv_cell - (float)c.cz, 0.f), 1.f);
+    c.sy = fy >= 0.5f ? 1 : -1;
+    c.sz = fz >= 0.5f ? 1 : -1;
+    return c;
 }
 
-// Deterministic block sum of 6 values per thread (result in thread 0).
-__device__ __forceinline__ void block_sum6(float g[6], float (*red)[6]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Walk table entries [0, n) with rows clipped at min(bound, cap2).  Stops at
+// the first entry out of reach of the best; the answer is exact then if the
+// clipping never cut below the best (best within cap2).
+__device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap2, float3 q, Best& B, Work& w) {
+    const int lane = threadIdx.x & 31;
+    const QueryCell c = query_cell(g, q);
+    for (int base = 0; base < n;) {
+        if (cleared(g, tab, base, B.d)) return bound2(B.d) <= cap2;
+        const int width = base == 0 ? kFirstRound : 32;
+        const int e = base + lane;
+        const bool has = lane < width && e < n;
+        int y = 0, z = 0;
+        if (has) {
+            const short2 o = __ldg(tab.off + e);
+            y = c.cy + c.sy * o.x;
+            z = c.cz + c.sz * o.y;
+        }
+        round_rows(g, q, has, y, z, 0, g.dims.x - 1, fminf(bound2(B.d), cap2), B, w);
+        base += width;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best& B, Work& w) {
+    const int lane = threadIdx.x & 31;
+    const GridView& F = S.fine;
+    B.d = FLT_MAX;
+    B.i = kNone;
+    B.p = make_float3(0.f, 0.f, 0.f);
+    w.queries += lane == 0;
+    // seed of the query's cell, then the 3 x 3 x 3 cells around the seed point
+    {
+        const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
+        const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
+        const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
+        const int s = __ldg(F.seed + ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx);
+        if (s >= 0) {
+            const float4 r = __ldg(F.sorted + s);
+            take(B, r, q, __float_as_int(r.w));
+            const int sx = cell_coord(r.x, F.origin.x, F.inv_cell, F.dims.x);
+            const int sy = cell_coord(r.y, F.origin.y, F.inv_cell, F.dims.y);
+            const int sz = cell_coord(r.z, F.origin.z, F.inv_cell, F.dims.z);
+            round_rows(F, q, lane < 9, sy + lane % 3 - 1, sz + lane / 3 - 1, sx - 1, sx + 1, bound2(B.d), B, w);
+        }
+    }
+    // prove it: walk the table with that bound on the fine level (bound under
+    // kFineReach cells) or the coarse level
+    const float reach = kFineReach * F.cell;
+    const bool fine = B.d <= reach * reach;
+    w.far += (lane == 0 && !fine);
+    const GridView& L = fine ? S.fine : S.coarse;
+    if (walk(L, S.tab, S.tab.n, FLT_MAX, q, B, w)) return;
+    if (cleared(L, S.tab, S.tab.n - 1, B.d)) return;
+    // the table cannot settle it: scan every point
+    w.exh += lane == 0;
+    Best E = B;
+    for (int p = lane; p < S.M; p += 32) take(E, __ldg(S.ref4 + p), q, p);
+    if (lane == 0) {
+        w.segs += 1;
+        w.pts += (unsigned)S.M;
+    }
+    warp_min(E);
+    B = E;
+}
+
+// Warp-aggregated accumulation of the work counters: queries, rows, segments,
+// points, queries that reached the far phase, queries that reached the
+// exhaustive scan.
+__device__ __forceinline__ void add_stats(unsigned long long* stats, const Work& w) {
+    unsigned long long v[6] = {w.queries, w.rows, w.segs, w.pts, w.far, w.exh};
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) g[a] += __shfl_down_sync(0xffffffffu, g[a], off);
+        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_down_sync(kFull, v[a], off);
     }
-    if (lane == 0) {
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int a = 0; a < 6; ++a) red[warp][a] = g[a];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int a = 0; a < 6; ++a) {
-            float s = 0.f;
-            for (int w = 0; w < nw; ++w) s += red[w][a];
-            g[a] = s;
-        }
+        for (int a = 0; a < 6; ++a) atomicAdd(stats + a, v[a]);
     }
 }
 
-// grid (chunks, K); CTA (c, j) handles minibatch entries [c*blockDim, (c+1)*blockDim) of particle j.
-__global__ void __launch_bounds__(256) k_grad_grid(GradArgs a, GridView g) {
-    __shared__ Pose P;
-    __shared__ float red[8][6];
-    const int j = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (threadIdx.x == 0) make_pose(a.theta + 6 * j, P);
-    __syncthreads();
+__global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float* __restrict__ q, int64_t n,
+                                                      int32_t* __restrict__ idx, float* __restrict__ d2,
+                                                      unsigned long long* __restrict__ stats) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    Work w;
+    if (i < n) {
+        const float3 qq = make_float3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
+        Best B;
+        grid_search(S, qq, B, w);
+        if (lane == 0) {
+            idx[i] = B.i != kNone ? B.i : -1;
+            if (d2) d2[i] = B.d;
+        }
+    }
+    if (stats) add_stats(stats, w);
+}
+
+// grid (chunks, particle pairs).  Warp w of CTA (c, b) handles particle
+// b*kPb + w and minibatch entries [c*kKc, (c+1)*kKc), one query at a time.
+// Lane 0 accumulates the particle's gradient terms and writes the chunk's
+// partial sum; the last warp to finish a particle folds its chunk partials
+// into gbar in fixed chunk order.  Warps never wait for each other.
+__global__ void __launch_bounds__(kGradThreads, 16) k_grad_grid(GradArgs a, GridSearch S) {
+    __shared__ Pose P[kPb];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.y * kPb + warp;
+    if (j >= a.K) return;                      // whole warp: no block-wide barrier below
+    if (lane == 0) make_pose(a.theta + 6 * j, P[warp]);
+    __syncwarp();
     float gr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     Work w;
-    if (k < a.m) {
+    for (int kk = 0; kk < kKc; ++kk) {
+        const int k = blockIdx.x * kKc + kk;
+        if (k >= a.m) break;
         const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
         const float3 s = make_float3(s4.x, s4.y, s4.z);
-        const float3 q = apply_pose(P, s);
-        float best;
-        int bi;
-        float3 bp;
-        grid_search(g, q, best, bi, bp, w);
-        const bool found = bi != 0x7fffffff;  // false only for a non-finite distance
-        if (found) grad_terms(P, s, make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z), gr);
-        if (a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? bi : -1;
+        const float3 q = apply_pose(P[warp], s);
+        Best B;
+        grid_search(S, q, B, w);
+        const bool found = B.i != kNone;   // false only for a non-finite distance
+        if (lane == 0) {
+            if (found) {
+                float t[6];
+                grad_terms(P[warp], s, make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z), t);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) gr[c] += t[c];
+            }
+            if (a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
+        }
     }
-    if (a.stats) add_stats(a.stats, k < a.m, w);
-    block_sum6(gr, red);
-    if (threadIdx.x == 0) {
+    if (a.stats) add_stats(a.stats, w);
+    unsigned last = 0;
+    if (lane == 0) {
         float* dst = a.partial + ((int64_t)blockIdx.x * a.K + j) * 6;
+#pragma unroll
         for (int c = 0; c < 6; ++c) dst[c] = gr[c];
+        __threadfence();
+        last = atomicAdd(a.done + j, 1u) == gridDim.x - 1;
+    }
+    if (!__shfl_sync(kFull, last, 0)) return;
+    __threadfence();
+    // lanes 0..29: component lane % 6, chunk subset lane / 6
+    constexpr int kParts = 5;
+    const int c = lane % 6, part = lane / 6;
+    float sum = 0.f;
+    if (part < kParts) {
+#pragma unroll 4
+        for (int ch = part; ch < (int)gridDim.x; ch += kParts) sum += __ldcg(a.partial + ((int64_t)ch * a.K + j) * 6 + c);
+    }
+    float tot = sum;
+#pragma unroll
+    for (int p = 1; p < kParts; ++p) tot += __shfl_sync(kFull, sum, lane + 6 * p < 32 ? lane + 6 * p : lane);
+    if (lane < 6) {
+        a.gbar[j * 6 + c] = tot * a.inv_m;
+        if (lane == 0) a.done[j] = 0u;
     }
 }
 
 // ---------------------------------------------------------------- build kernels
 
 __global__ void k_cell_assign(const float4* __restrict__ ref, int64_t M, GridView g, int32_t* __restrict__ cell_of,
-                              int32_t* __restrict__ counts, int32_t* __restrict__ brick_rep) {
+                              int32_t* __restrict__ counts) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 p = ref[i];
         const int cx = cell_coord(p.x, g.origin.x, g.inv_cell, g.dims.x);
@@ -266,8 +365,6 @@ __global__ void k_cell_assign(const float4* __restrict__ ref, int64_t M, GridVie
         const int32_t cid = (int32_t)(((int64_t)cz * g.dims.y + cy) * g.dims.x + cx);
         cell_of[i] = cid;
         atomicAdd(counts + cid, 1);
-        const int64_t b = ((int64_t)(cz / kBrick) * g.bdims.y + cy / kBrick) * g.bdims.x + cx / kBrick;
-        atomicMin(brick_rep + b, (int32_t)i);
     }
 }
 
@@ -282,18 +379,20 @@ __global__ void k_scatter(const float4* __restrict__ ref, int64_t M, const int32
 }
 
 // Order each cell's points by original index, so the layout is deterministic.
-__global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int64_t ncells, float4* __restrict__ sorted) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+// One warp per cell: rank of each point = number of smaller indices in the cell.
+__global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int64_t ncells, const float4* __restrict__ in,
+                             float4* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = wid; c < ncells; c += nw) {
         const int b = cell_start[c], e = cell_start[c + 1];
-        for (int i = b + 1; i < e; ++i) {
-            const float4 v = sorted[i];
+        for (int i = b + lane; i < e; i += 32) {
+            const float4 v = in[i];
             const int key = __float_as_int(v.w);
-            int j = i - 1;
-            while (j >= b && __float_as_int(sorted[j].w) > key) {
-                sorted[j + 1] = sorted[j];
-                --j;
-            }
-            sorted[j + 1] = v;
+            int rank = 0;
+            for (int k = b; k < e; ++k) rank += __float_as_int(in[k].w) < key;
+            out[b + rank] = v;
         }
     }
 }
@@ -310,6 +409,63 @@ __global__ void k_row_span(const int32_t* __restrict__ cell_start, GridView g, i
             }
         }
         span[r] = make_int2(lo, hi);
+    }
+}
+
+__device__ __forceinline__ float3 cell_centre(const GridView& g, int x, int y, int z) {
+    return make_float3(g.origin.x + ((float)x + 0.5f) * g.cell, g.origin.y + ((float)y + 0.5f) * g.cell,
+                       g.origin.z + ((float)z + 0.5f) * g.cell);
+}
+
+// Seed of a non-empty cell: its point closest to the cell centre; -1 otherwise.
+__global__ void k_seed_init(GridView g, int64_t ncells, int32_t* __restrict__ seed) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int b = g.cell_start[c], e = g.cell_start[c + 1];
+        int best = -1;
+        if (e > b) {
+            const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y), z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
+            const float3 ct = cell_centre(g, x, y, z);
+            float bd = FLT_MAX;
+            for (int p = b; p < e; ++p) {
+                const float d = dist2(g.sorted[p], ct);
+                if (d < bd) {
+                    bd = d;
+                    best = p;
+                }
+            }
+        }
+        seed[c] = best;
+    }
+}
+
+// One jump-flooding step at offset k: adopt the closest seed among the 27 cells at offsets {-k, 0, k}^3.
+__global__ void k_seed_step(GridView g, int64_t ncells, int k, const int32_t* __restrict__ in,
+                            int32_t* __restrict__ out) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y), z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
+        const float3 ct = cell_centre(g, x, y, z);
+        int best = in[c];
+        float bd = best >= 0 ? dist2(g.sorted[best], ct) : FLT_MAX;
+        for (int dz = -k; dz <= k; dz += k) {
+            const int zz = z + dz;
+            if (zz < 0 || zz >= g.dims.z) continue;
+            for (int dy = -k; dy <= k; dy += k) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= g.dims.y) continue;
+                for (int dx = -k; dx <= k; dx += k) {
+                    const int xx = x + dx;
+                    if (xx < 0 || xx >= g.dims.x || (dx == 0 && dy == 0 && dz == 0)) continue;
+                    const int s = in[((int64_t)zz * g.dims.y + yy) * g.dims.x + xx];
+                    if (s < 0 || s == best) continue;
+                    const float d = dist2(g.sorted[s], ct);
+                    if (d < bd || (d == bd && s < best)) {
+                        bd = d;
+                        best = s;
+                    }
+                }
+            }
+        }
+        out[c] = best;
     }
 }
 
@@ -333,10 +489,129 @@ int grow(sicp_ctx* ctx, T*& p, size_t& cap, size_t n) {
     return SICP_OK;
 }
 
+int3 dims_for(const float ext[3], double& c) {
+    int3 d;
+    for (;;) {
+        d.x = (int)fmin(floor(ext[0] / c) + 1.0, 1 << 20);
+        d.y = (int)fmin(floor(ext[1] / c) + 1.0, 1 << 20);
+        d.z = (int)fmin(floor(ext[2] / c) + 1.0, 1 << 20);
+        const double n = (double)d.x * d.y * d.z;
+        if (n <= (double)kMaxCells) return d;
+        c *= cbrt(n / (double)kMaxCells) * 1.01;
+    }
+}
+
+// Build one level with cell edge c over the context's reference points; the
+// seed map only when `seeds`.
+int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], double X, double c, bool seeds) {
+    const int64_t M = ctx->M;
+    cudaStream_t s = ctx->stream;
+    const int3 dims = dims_for(ext, c);
+    const int64_t ncells = (int64_t)dims.x * dims.y * dims.z;
+    const int64_t rows = (int64_t)dims.y * dims.z;
+    int rc;
+    if ((rc = grow(ctx, G.sorted, G.cap_points, (size_t)M))) return rc;
+    if ((rc = grow(ctx, G.cell_of, G.cap_cellof, (size_t)M))) return rc;
+    if ((rc = grow(ctx, G.cell_start, G.cap_cells, (size_t)ncells + 1))) return rc;
+    if ((rc = grow(ctx, G.counts, G.cap_counts, (size_t)ncells + 1))) return rc;
+    if ((rc = grow(ctx, G.row_span, G.cap_rows, (size_t)rows))) return rc;
+    if ((rc = grow(ctx, G.scan_sums, G.cap_sums, scan_sums_size(ncells)))) return rc;
+    if (seeds) {
+        if ((rc = grow(ctx, G.seed, G.cap_seed, (size_t)ncells))) return rc;
+        if ((rc = grow(ctx, G.seed_tmp, G.cap_seed_tmp, (size_t)ncells))) return rc;
+    }
+    // the scatter target doubles as the unsorted staging area of the per-cell sort
+    float4* staging = (float4*)ctx->tmp_aux.p;
+    if ((rc = ensure(ctx, ctx->tmp_aux, sizeof(float4) * (size_t)M))) return rc;
+    staging = (float4*)ctx->tmp_aux.p;
+    GridView& v = G.v;
+    v.origin = make_float3(lo[0], lo[1], lo[2]);
+    v.cell = (float)c;
+    v.inv_cell = (float)(1.0 / c);
+    v.tol = (float)(1e-6 * (X + c));
+    v.dims = dims;
+    v.sorted = G.sorted;
+    v.cell_start = G.cell_start;
+    v.row_span = G.row_span;
+    v.seed = seeds ? G.seed : nullptr;
+    G.ncells = ncells;
+    SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
+    k_cell_assign<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, v, G.cell_of, G.counts);
+    SICP_CUDA(cudaGetLastError());
+    SICP_CUDA(launch_exclusive_scan(G.counts, ncells, G.cell_start, G.scan_sums, s));
+    SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
+    k_scatter<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, G.cell_of, G.cell_start, G.counts, staging);
+    SICP_CUDA(cudaGetLastError());
+    k_sort_cells<<<blocks_for(ncells * 32, 256), 256, 0, s>>>(G.cell_start, ncells, staging, G.sorted);
+    SICP_CUDA(cudaGetLastError());
+    k_row_span<<<blocks_for(rows, 128), 128, 0, s>>>(G.cell_start, v, G.row_span);
+    SICP_CUDA(cudaGetLastError());
+    if (seeds) {
+        int32_t* a = G.seed;
+        int32_t* b = G.seed_tmp;
+        k_seed_init<<<blocks_for(ncells, 256), 256, 0, s>>>(v, ncells, a);
+        SICP_CUDA(cudaGetLastError());
+        int k = 1;
+        while (k * 2 <= std::max(dims.x, std::max(dims.y, dims.z)) / 2) k *= 2;
+        std::vector<int> steps;
+        for (; k >= 1; k /= 2) steps.push_back(k);
+        steps.push_back(1);
+        for (int st : steps) {
+            k_seed_step<<<blocks_for(ncells, 256), 256, 0, s>>>(v, ncells, st, a, b);
+            SICP_CUDA(cudaGetLastError());
+            std::swap(a, b);
+        }
+        if (a != G.seed) SICP_CUDA(cudaMemcpyAsync(G.seed, a, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, s));
+    }
+    return SICP_OK;
+}
+
 }  // namespace
 
+int search_table_init(sicp_ctx* ctx) {
+    struct E {
+        short dy, dz;
+        float lb2;
+    };
+    std::vector<E> es;
+    const int R = kTableRadius;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy) {
+            // lower bound (cell units) on the distance from a query in the upper half of its cell
+            const float lz = dz == 0 ? 0.f : (dz > 0 ? (float)(dz - 1) : (float)(-dz) - 0.5f);
+            const float ly = dy == 0 ? 0.f : (dy > 0 ? (float)(dy - 1) : (float)(-dy) - 0.5f);
+            const float lb2 = lz * lz + ly * ly;
+            if (lb2 <= (float)((R - 1) * (R - 1))) es.push_back({(short)dy, (short)dz, lb2});
+        }
+    std::stable_sort(es.begin(), es.end(), [](const E& a, const E& b) {
+        if (a.lb2 != b.lb2) return a.lb2 < b.lb2;
+        return abs(a.dy) + abs(a.dz) < abs(b.dy) + abs(b.dz);
+    });
+    std::vector<short2> off(es.size());
+    std::vector<float> lb2(es.size());
+    for (size_t i = 0; i < es.size(); ++i) {
+        off[i] = make_short2(es[i].dy, es[i].dz);
+        lb2[i] = es[i].lb2;
+    }
+    if (cudaMalloc(&ctx->tab_off, sizeof(short2) * off.size()) != cudaSuccess ||
+        cudaMalloc(&ctx->tab_lb2, sizeof(float) * lb2.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, SICP_ENOMEM, "search table allocation failed");
+    }
+    SICP_CUDA(cudaMemcpy(ctx->tab_off, off.data(), sizeof(short2) * off.size(), cudaMemcpyHostToDevice));
+    SICP_CUDA(cudaMemcpy(ctx->tab_lb2, lb2.data(), sizeof(float) * lb2.size(), cudaMemcpyHostToDevice));
+    SearchTable& t = ctx->search.tab;
+    t.off = ctx->tab_off;
+    t.lb2 = ctx->tab_lb2;
+    t.n = (int)off.size();
+    for (int k = 0; k < 8; ++k) {
+        const float cap = 1.5f * (float)(1 << k);
+        t.upto[k] = (int)(std::upper_bound(lb2.begin(), lb2.end(), cap * cap) - lb2.begin());
+    }
+    return SICP_OK;
+}
+
 int grid_build(sicp_ctx* ctx, float cell_size) {
-    Grid& G = ctx->grid;
     const int64_t M = ctx->M;
     cudaStream_t s = ctx->stream;
     int rc = ensure(ctx, ctx->bbox, 8 * sizeof(unsigned));
@@ -358,81 +633,46 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
     }
     ctx->ref_lo = make_float3(lo[0], lo[1], lo[2]);
     ctx->ref_hi = make_float3(hi[0], hi[1], hi[2]);
-    double maxext = fmax(ext[0], fmax(ext[1], ext[2]));
+    const double maxext = fmax(ext[0], fmax(ext[1], ext[2]));
     double c = cell_size;
     if (!(c > 0.0)) {
         if (maxext <= 0.0) {
             c = 1.0;
         } else {
-            // half the volumetric spacing of the (degenerate axes padded) box
+            // half the volumetric spacing of the box (degenerate axes padded)
             const double floor_ext = maxext * 1e-3;
             const double V = fmax(ext[0], floor_ext) * fmax(ext[1], floor_ext) * fmax(ext[2], floor_ext);
             c = 0.5 * cbrt(V / (double)M);
         }
     }
-    int3 dims;
-    for (;;) {
-        dims.x = (int)fmin(floor(ext[0] / c) + 1.0, 1 << 20);
-        dims.y = (int)fmin(floor(ext[1] / c) + 1.0, 1 << 20);
-        dims.z = (int)fmin(floor(ext[2] / c) + 1.0, 1 << 20);
-        const double n = (double)dims.x * dims.y * dims.z;
-        if (n <= (double)kMaxCells) break;
-        c *= cbrt(n / (double)kMaxCells) * 1.01;
-    }
-    const int64_t ncells = (int64_t)dims.x * dims.y * dims.z;
-    const int3 bd = make_int3((dims.x + kBrick - 1) / kBrick, (dims.y + kBrick - 1) / kBrick,
-                              (dims.z + kBrick - 1) / kBrick);
-    const int64_t nbricks = (int64_t)bd.x * bd.y * bd.z;
-    const int64_t rows = (int64_t)dims.y * dims.z;
-    if ((rc = grow(ctx, G.sorted, G.cap_points, (size_t)M))) return rc;
-    if ((rc = grow(ctx, G.cell_of, G.cap_cellof, (size_t)M))) return rc;
-    if ((rc = grow(ctx, G.cell_start, G.cap_cells, (size_t)ncells + 1))) return rc;
-    if ((rc = grow(ctx, G.counts, G.cap_counts, (size_t)ncells + 1))) return rc;
-    if ((rc = grow(ctx, G.row_span, G.cap_rows, (size_t)rows))) return rc;
-    if ((rc = grow(ctx, G.brick_rep, G.cap_bricks, (size_t)nbricks))) return rc;
-    if ((rc = grow(ctx, G.scan_sums, G.cap_sums, scan_sums_size(ncells)))) return rc;
-
-    GridView& v = G.v;
-    v.origin = make_float3(lo[0], lo[1], lo[2]);
-    v.cell = (float)c;
-    v.inv_cell = (float)(1.0 / c);
-    v.tol = (float)(1e-6 * (X + c));
-    v.dims = dims;
-    v.bdims = bd;
-    v.sorted = G.sorted;
-    v.cell_start = G.cell_start;
-    v.row_span = G.row_span;
-    v.brick_rep = G.brick_rep;
-    v.ref4 = ctx->ref4;
-    G.ncells = ncells;
-    G.nbricks = nbricks;
-
-    SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
-    SICP_CUDA(cudaMemsetAsync(G.brick_rep, 0x7f, sizeof(int32_t) * nbricks, s));
-    k_cell_assign<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, v, G.cell_of, G.counts, G.brick_rep);
-    SICP_CUDA(cudaGetLastError());
-    SICP_CUDA(launch_exclusive_scan(G.counts, ncells, G.cell_start, G.scan_sums, s));
-    SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
-    k_scatter<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, G.cell_of, G.cell_start, G.counts, G.sorted);
-    SICP_CUDA(cudaGetLastError());
-    k_sort_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(G.cell_start, ncells, G.sorted);
-    SICP_CUDA(cudaGetLastError());
-    k_row_span<<<blocks_for(rows, 128), 128, 0, s>>>(G.cell_start, v, G.row_span);
-    SICP_CUDA(cudaGetLastError());
+    if ((rc = build_level(ctx, ctx->grid, lo, ext, X, c, true))) return rc;
+    const double c2 = (double)ctx->grid.v.cell * kCoarseFactor;
+    if ((rc = build_level(ctx, ctx->grid2, lo, ext, X, c2, false))) return rc;
+    ctx->search.fine = ctx->grid.v;
+    ctx->search.coarse = ctx->grid2.v;
+    ctx->search.ref4 = ctx->ref4;
+    ctx->search.M = (int)M;
     return SICP_OK;
 }
 
-cudaError_t launch_nn_grid(const GridView& g, const float* q, int64_t n, int32_t* idx, float* d2,
+GradLayout grad_layout_grid(int32_t m) {
+    GradLayout L;
+    L.chunks = (m + kKc - 1) / kKc;
+    L.threads = kGradThreads;
+    return L;
+}
+
+cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32_t* idx, float* d2,
                            unsigned long long* stats, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_nn_grid<<<(unsigned)((n + kQueryThreads - 1) / kQueryThreads), kQueryThreads, 0, s>>>(g, q, n, idx, d2, stats);
+    k_nn_grid<<<(unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, s>>>(g, q, n, idx, d2, stats);
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_grid(const GradArgs& a, const GridView& g, cudaStream_t s) {
-    const GradLayout L = grad_layout(a.m);
-    dim3 grid(L.chunks, a.K);
-    k_grad_grid<<<grid, L.threads, 0, s>>>(a, g);
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch& g, cudaStream_t s) {
+    const GradLayout L = grad_layout_grid(a.m);
+    dim3 grid(L.chunks, (a.K + kPb - 1) / kPb);
+    k_grad_grid<<<grid, kGradThreads, 0, s>>>(a, g);
     return cudaGetLastError();
 }
 
