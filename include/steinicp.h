@@ -153,6 +153,36 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
 int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
                  int on_device);
 
+/* ---- allocation-free variant ---- */
+
+/* The mean ICP gradient of sicp_icp_grad with SICP_NN_BRUTE_FP32, for
+ * callers that cannot allocate device memory.  Examples are code that runs
+ * inside a fixed pre-allocated memory budget, a real-time loop where any
+ * cudaMalloc/cudaFree would stall or is forbidden, and a host process whose
+ * allocator belongs to another framework.  There is no counterpart in the
+ * paper: this is a deployment variant of the same computation.
+ *
+ * No context is needed and nothing is allocated.  All array arguments are
+ * device pointers on the current device: reference ref_xyz [M][3], source
+ * src_xyz [N][3], minibatch mb [m] (indices into the source), particles [K][6];
+ * the result goes to out_gbar [K][6].  The work is queued on `cuda_stream`
+ * (NULL: the legacy default stream) and the call returns without waiting.
+ *
+ * Scratch: the kernel's partial sums and arrival counters live in one
+ * file-scope device array of 25,600 bytes that every GPU loading this library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) for that device; make that
+ * first call before any stream capture.  Each call clears the counters itself.
+ * Calls share the array, so calls that overlap on the GPU (on two streams,
+ * or from two threads) race and must be serialised by the caller.
+ *
+ * Limits: K <= 256, m <= 1024, M <= 2^30, N <= 2^31 - 1.  Returns SICP_OK,
+ * SICP_EINVAL (a NULL pointer or a size outside these limits; nothing is
+ * launched), or SICP_ECUDA (no current device, or a failed launch). */
+int sicp_icp_grad_noalloc(const float* ref_xyz, int64_t M, const float* src_xyz, int64_t N,
+                          const int32_t* mb, int32_t m, const float* particles, int32_t K,
+                          float* out_gbar, void* cuda_stream);
+
 /* ---- measurement ---- */
 
 /* Work counters of the grid search (no counterpart in the paper; they state

@@ -39,7 +39,7 @@ _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
-    "sicp_stats", "sicp_profile",
+    "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc",
 )
 
 
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "sicp_moments": (ctypes.c_int, [P, P, I32, P, P, ctypes.c_int]),
             "sicp_stats": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_profile": (ctypes.c_int, [P, ctypes.c_int, P]),
+            "sicp_icp_grad_noalloc": (ctypes.c_int, [P, I64, P, I64, P, I32, P, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -265,3 +266,23 @@ def sicp_profile(ctx, stride: int = 0):
     out = np.zeros(4, np.float64)
     _check(ctx, lib().sicp_profile(ctx, int(stride), out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def sicp_icp_grad_noalloc(ref_xyz, src_xyz, mb, particles, out_gbar=None, stream=None):
+    """Allocation-free mean gradient (exhaustive FP32 search) on torch CUDA
+    tensors; returns out_gbar [K][6].  Raises SicpError on a bad size.  The
+    call only queues work on `stream` (default: torch's current stream)."""
+    import torch
+    for t in (ref_xyz, src_xyz, mb, particles):
+        if not (_is_torch(t) and t.is_cuda):
+            raise ValueError("sicp_icp_grad_noalloc takes CUDA tensors only")
+    K = particles.shape[0]
+    if out_gbar is None:
+        out_gbar = torch.empty((K, 6), dtype=torch.float32, device=particles.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sicp_icp_grad_noalloc(_ptr(ref_xyz, np.float32), ref_xyz.shape[0], _ptr(src_xyz, np.float32),
+                                     src_xyz.shape[0], _ptr(mb, np.int32), mb.shape[0], _ptr(particles, np.float32),
+                                     K, _ptr(out_gbar, np.float32), ctypes.c_void_p(s.cuda_stream))
+    if rc != SICP_OK:
+        raise SicpError(rc, "sicp_icp_grad_noalloc: bad size or pointer (K <= 256, m <= 1024) or CUDA failure")
+    return out_gbar
