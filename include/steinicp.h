@@ -110,6 +110,41 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
                   int32_t K, const sicp_params* p, float* particles_out, double* mean6,
                   double* cov36, int on_device);
 
+/* ---- many problems at once ---- */
+
+/* P independent runs of sicp_register (Sec. IV summary) in one persistent
+ * GPU launch, for serving many registrations at once.  Problem p has
+ * reference points ref_xyz[ref_off[p] .. ref_off[p+1]) [3], source points
+ * src_xyz[src_off[p] .. src_off[p+1]) [3] and particles
+ * particles_in[part_off[p] .. part_off[p+1]) [6]; the offset arrays have
+ * P+1 entries starting at 0 and are always host arrays.  All problems share
+ * the parameters `p` (T, m, lr, Adam constants, prior) except the
+ * minibatch stream: problem p uses seed p->seed + p.  p->nn_mode must be
+ * SICP_NN_GRID.  Outputs: particles_out laid out like particles_in; mean6
+ * [P][6] and cov36 [P][36] (may be NULL).  Each problem needs M >= 1,
+ * N >= m and 1 <= K <= 2048.  Uses the grid cell-size factor and work-item
+ * size set by sicp_autotune_batched (defaults 0.5 and 4).  Errors:
+ * SICP_EINVAL, SICP_ENOMEM, SICP_ECUDA, SICP_ETIMEOUT (a bounded grid
+ * barrier of the persistent kernel gave up). */
+int sicp_register_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, const float* ref_xyz,
+                          const int64_t* src_off, const float* src_xyz, const int32_t* part_off,
+                          const float* particles_in, const sicp_params* p, float* particles_out,
+                          double* mean6, double* cov36, int on_device);
+
+/* Autotuner of the batched path (no counterpart in the paper): times
+ * trial_iters iterations of the persistent kernel for each candidate grid
+ * cell-size factor (0.35, 0.5, 0.7, 1.0 times the volumetric point spacing)
+ * and minibatch entries per work item (2, 4, 8) on the given batch, keeps the
+ * fastest on the context for later sicp_register_batched calls, and returns
+ * it.  With cache_path (may be NULL) the choice is read from / written to a
+ * small JSON file keyed by GPU name, problem count, mean reference size and
+ * m.  Arguments otherwise as sicp_register_batched. */
+int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, const float* ref_xyz,
+                          const int64_t* src_off, const float* src_xyz, const int32_t* part_off,
+                          const float* particles_in, const sicp_params* p, int32_t trial_iters,
+                          const char* cache_path, float* out_cell_factor, int32_t* out_points_per_item,
+                          int on_device);
+
 /* ---- single steps of the iteration, for users who drive the loop ---- */
 
 /* Step 1 (Sec. III-B): the minibatches of iterations t0 .. t0+T-1 of the

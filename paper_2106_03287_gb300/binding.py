@@ -39,7 +39,7 @@ _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
-    "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc",
+    "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
 )
 
 
@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
             "sicp_stats": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_profile": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_icp_grad_noalloc": (ctypes.c_int, [P, I64, P, I64, P, I32, P, I32, P, P]),
+            "sicp_register_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, P, P, P, ctypes.c_int]),
+            "sicp_autotune_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, I32, ctypes.c_char_p, P, P,
+                                                     ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -286,3 +289,65 @@ def sicp_icp_grad_noalloc(ref_xyz, src_xyz, mb, particles, out_gbar=None, stream
     if rc != SICP_OK:
         raise SicpError(rc, "sicp_icp_grad_noalloc: bad size or pointer (K <= 256, m <= 1024) or CUDA failure")
     return out_gbar
+
+
+def _batch_args(problems):
+    """Pack a list of (ref [M][3], src [N][3], particles [K][6]) into CSR arrays."""
+    refs = [_host(p[0], np.float32) for p in problems]
+    srcs = [_host(p[1], np.float32) for p in problems]
+    pars = [_host(p[2], np.float32) for p in problems]
+    dev = _is_torch(refs[0]) and refs[0].is_cuda
+    ref_off = np.zeros(len(problems) + 1, np.int64)
+    src_off = np.zeros(len(problems) + 1, np.int64)
+    part_off = np.zeros(len(problems) + 1, np.int32)
+    ref_off[1:] = np.cumsum([r.shape[0] for r in refs])
+    src_off[1:] = np.cumsum([s.shape[0] for s in srcs])
+    part_off[1:] = np.cumsum([q.shape[0] for q in pars])
+    if dev:
+        import torch
+        cat = lambda xs: torch.cat(xs).contiguous()
+    else:
+        cat = lambda xs: np.ascontiguousarray(np.concatenate(xs))
+    return cat(refs), cat(srcs), cat(pars), ref_off, src_off, part_off, int(dev)
+
+
+def pack_batch(problems):
+    """Pack a list of (ref, src, particles) once, for repeated batched calls."""
+    ref, src, par, ref_off, src_off, part_off, dev = _batch_args(problems)
+    return dict(ref=ref, src=src, par=par, ref_off=ref_off, src_off=src_off, part_off=part_off, dev=dev)
+
+
+def sicp_register_batched(ctx, problems, params: sicp_params):
+    """Run the registrations of `problems` (a list of (ref, src, particles), or
+    the result of pack_batch) in one launch.  Returns (particles list,
+    mean [P][6], cov [P][6][6])."""
+    b = problems if isinstance(problems, dict) else pack_batch(problems)
+    ref, src, par, ref_off, src_off, part_off, dev = (b["ref"], b["src"], b["par"], b["ref_off"], b["src_off"],
+                                                      b["part_off"], b["dev"])
+    P = len(ref_off) - 1
+    out = _empty(par, tuple(par.shape), np.float32)
+    mean = _empty(par, (P, 6), np.float64)
+    cov = _empty(par, (P, 6, 6), np.float64)
+    _check(ctx, lib().sicp_register_batched(ctx, P, ref_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(ref, np.float32), src_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(src, np.float32), part_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(par, np.float32), ctypes.byref(params), _ptr(out, np.float32),
+                                            _ptr(mean, np.float64), _ptr(cov, np.float64), dev))
+    parts = [out[part_off[i]:part_off[i + 1]] for i in range(P)]
+    return parts, mean, cov
+
+
+def sicp_autotune_batched(ctx, problems, params: sicp_params, trial_iters: int = 5, cache_path=None):
+    """Pick and keep the fastest (cell-size factor, minibatch entries per work item)."""
+    b = problems if isinstance(problems, dict) else pack_batch(problems)
+    ref, src, par, ref_off, src_off, part_off, dev = (b["ref"], b["src"], b["par"], b["ref_off"], b["src_off"],
+                                                      b["part_off"], b["dev"])
+    f = ctypes.c_float()
+    k = ctypes.c_int32()
+    _check(ctx, lib().sicp_autotune_batched(ctx, len(ref_off) - 1, ref_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(ref, np.float32), src_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(src, np.float32), part_off.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(par, np.float32), ctypes.byref(params), trial_iters,
+                                            cache_path.encode() if cache_path else None, ctypes.byref(f),
+                                            ctypes.byref(k), dev))
+    return f.value, k.value

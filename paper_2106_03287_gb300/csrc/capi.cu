@@ -298,6 +298,7 @@ void sicp_destroy(sicp_ctx* c) {
     DeviceScope ds(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     delete c->graphs;
+    if (c->batch) batch_destroy(c->batch);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done};
     for (Buf* b : bufs)

@@ -142,6 +142,8 @@ struct Buf {
 };
 
 struct GraphCache;
+struct BatchState;
+void batch_destroy(BatchState* b);
 
 }  // namespace sicp
 
@@ -169,6 +171,7 @@ struct sicp_ctx {
     int prof_stride = 0;
     double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
     sicp::GraphCache* graphs = nullptr;
+    sicp::BatchState* batch = nullptr;   // state of the batched path, created on first use
 };
 
 namespace sicp {

@@ -36,243 +36,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "grid_search.cuh"
 
 namespace sicp {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;  // queries in flight per CTA, one warp each
-constexpr int kGradThreads = 64;       // gradient kernel CTA: one warp per particle
-constexpr int kPb = kGradThreads / 32;  // particles per CTA in the gradient kernel
-constexpr int kKc = 4;                 // minibatch entries per warp in the gradient kernel
-constexpr int kFirstRound = 8;         // table entries in the first round of a walk
-constexpr int kCoarseFactor = 4;
-constexpr float kFineReach = 6.f;      // the far phase proves on the fine level below this many cells
-constexpr int kTableRadius = 48;
-constexpr int64_t kMaxCells = 1 << 23;
-constexpr float kSlack = 1.0000005f;
-constexpr int kNone = 0x7fffffff;
-constexpr unsigned kFull = 0xffffffffu;
+using namespace gs;
 
-__host__ __device__ __forceinline__ int cell_coord(float v, float o, float inv, int n) {
-    float f = (v - o) * inv;
-    f = fminf(fmaxf(f, 0.f), (float)(n - 1));
-    return (int)f;
-}
-
-__device__ __forceinline__ int cell_floor_clamped(float v, float o, float inv, int n) {
-    float f = (v - o) * inv;
-    f = fminf(fmaxf(f, -1.f), (float)n);
-    return (int)floorf(f);
-}
-
-// Distance from coordinate v to the slab of cell i along one axis, minus tol.
-__device__ __forceinline__ float slab(float v, float o, float c, int i, float tol) {
-    const float lo = fmaf((float)i, c, o), hi = lo + c;
-    const float d = fmaxf(fmaxf(lo - v, v - hi), 0.f);
-    return fmaxf(d - tol, 0.f);
-}
-
-// Squared pruning radius: best widened by kSlack, kept finite.
-__device__ __forceinline__ float bound2(float best) { return fminf(best * kSlack, FLT_MAX); }
-
-// Per-lane work counters: rows examined, row segments read, candidate points;
-// lane 0 also counts queries, queries that reached the far phase and queries
-// that reached the exhaustive scan.
-struct Work {
-    unsigned rows = 0, segs = 0, pts = 0, queries = 0, far = 0, exh = 0;
-};
-
-struct Best {
-    float d;
-    int i;
-    float3 p;
-};
-
-__device__ __forceinline__ void take(Best& B, float4 r, float3 q, int id) {
-    const float d = dist2(r, q);
-    if (better(d, id, B.d, B.i)) {
-        B.d = d;
-        B.i = id;
-        B.p = make_float3(r.x, r.y, r.z);
-    }
-}
-
-// Warp minimum (distance, then lowest index); every lane ends with the result.
-// Distances are non-negative, so their bit patterns order like unsigned ints.
-__device__ __forceinline__ void warp_min(Best& B) {
-    const unsigned db = __float_as_uint(B.d);
-    const unsigned md = __reduce_min_sync(kFull, db);
-    const unsigned mi = __reduce_min_sync(kFull, db == md ? (unsigned)B.i : 0xffffffffu);
-    const unsigned who = __ballot_sync(kFull, db == md && (unsigned)B.i == mi);
-    const int src = __ffs(who) - 1;
-    B.d = __uint_as_float(md);
-    B.i = (int)mi;
-    B.p.x = __shfl_sync(kFull, B.p.x, src);
-    B.p.y = __shfl_sync(kFull, B.p.y, src);
-    B.p.z = __shfl_sync(kFull, B.p.z, src);
-}
-
-// Every row from table entry e on is farther than the current best.
-__device__ __forceinline__ bool cleared(const GridView& g, const SearchTable& tab, int e, float best) {
-    const float lbd = sqrtf(__ldg(tab.lb2 + e)) * g.cell - g.tol;
-    return lbd > 0.f && lbd * lbd > bound2(best);
-}
-
-// One round: lane l contributes row (y, z) if `has`, limited to cells
-// [xlo, xhi] along x and clipped to the ball of squared radius clip2.
-__device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, int xlo, int xhi, float clip2,
-                           Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
-    int b = 0, len = 0;
-    if (has && y >= 0 && y < g.dims.y && z >= 0 && z < g.dims.z) {
-        const float dz = slab(q.z, g.origin.z, g.cell, z, g.tol);
-        const float dy = slab(q.y, g.origin.y, g.cell, y, g.tol);
-        const float rem = clip2 - dz * dz - dy * dy;
-        if (rem >= 0.f) {
-            w.rows += 1;
-            const int rowi = z * g.dims.y + y;
-            const int2 span = __ldg(g.row_span + rowi);
-            if (span.x <= span.y) {
-                const float r = sqrtf(rem) + g.tol;
-                const int x0 = max(max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), span.x), xlo);
-                const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), span.y), xhi);
-                if (x0 <= x1) {
-                    const int64_t row = (int64_t)rowi * g.dims.x;
-                    b = __ldg(g.cell_start + row + x0);
-                    len = __ldg(g.cell_start + row + x1 + 1) - b;
-                    w.segs += len > 0;
-                }
-            }
-        }
-    }
-    // flatten the round's segments: exclusive offsets and total
-    int incl = len;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += v;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
-    const int excl = incl - len;
-    // flattened point t belongs to the last lane whose offset is <= t
-    Best L = B;
-    for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        int o = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int ex = __shfl_sync(kFull, excl, o + step);
-            if (ex <= t) o += step;
-        }
-        const int ob = __shfl_sync(kFull, b, o);
-        const int oe = __shfl_sync(kFull, excl, o);
-        if (t < total) {
-            const float4 r = __ldg(g.sorted + ob + (t - oe));
-            take(L, r, q, __float_as_int(r.w));
-        }
-    }
-    if (lane == 0) w.pts += (unsigned)total;
-    warp_min(L);
-    B = L;
-}
-
-struct QueryCell {
-    int cy, cz, sy, sz;
-};
-
-__device__ __forceinline__ QueryCell query_cell(const GridView& g, float3 q) {
-    QueryCell c;
-    c.cy = cell_coord(q.y, g.origin.y, g.inv_cell, g.dims.y);
-    c.cz = cell_coord(q.z, g.origin.z, g.inv_cell, g.dims.z);
-    const float fy = fminf(fmaxf((q.y - g.origin.y) * g.inv_cell - (float)c.cy, 0.f), 1.f);
-    const float fz = fminf(fmaxf((q.z - g.origin.z) * g.inv_cell - (float)c.cz, 0.f), 1.f);
-    c.sy = fy >= 0.5f ? 1 : -1;
-    c.sz = fz >= 0.5f ? 1 : -1;
-    return c;
-}
-
-// Walk table entries [0, n) with rows clipped at min(bound, cap2).  Stops at
-// the first entry out of reach of the best; the answer is exact then if the
-// clipping never cut below the best (best within cap2).
-__device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap2, float3 q, Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
-    const QueryCell c = query_cell(g, q);
-    for (int base = 0; base < n;) {
-        if (cleared(g, tab, base, B.d)) return bound2(B.d) <= cap2;
-        const int width = base == 0 ? kFirstRound : 32;
-        const int e = base + lane;
-        const bool has = lane < width && e < n;
-        int y = 0, z = 0;
-        if (has) {
-            const short2 o = __ldg(tab.off + e);
-            y = c.cy + c.sy * o.x;
-            z = c.cz + c.sz * o.y;
-        }
-        round_rows(g, q, has, y, z, 0, g.dims.x - 1, fminf(bound2(B.d), cap2), B, w);
-        base += width;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
-    const GridView& F = S.fine;
-    B.d = FLT_MAX;
-    B.i = kNone;
-    B.p = make_float3(0.f, 0.f, 0.f);
-    w.queries += lane == 0;
-    // seed of the query's cell, then the 3 x 3 x 3 cells around the seed point
-    {
-        const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
-        const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
-        const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
-        const int s = __ldg(F.seed + ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx);
-        if (s >= 0) {
-            const float4 r = __ldg(F.sorted + s);
-            take(B, r, q, __float_as_int(r.w));
-            const int sx = cell_coord(r.x, F.origin.x, F.inv_cell, F.dims.x);
-            const int sy = cell_coord(r.y, F.origin.y, F.inv_cell, F.dims.y);
-            const int sz = cell_coord(r.z, F.origin.z, F.inv_cell, F.dims.z);
-            round_rows(F, q, lane < 9, sy + lane % 3 - 1, sz + lane / 3 - 1, sx - 1, sx + 1, bound2(B.d), B, w);
-        }
-    }
-    // prove it: walk the table with that bound on the fine level (bound under
-    // kFineReach cells) or the coarse level
-    const float reach = kFineReach * F.cell;
-    const bool fine = B.d <= reach * reach;
-    w.far += (lane == 0 && !fine);
-    const GridView& L = fine ? S.fine : S.coarse;
-    if (walk(L, S.tab, S.tab.n, FLT_MAX, q, B, w)) return;
-    if (cleared(L, S.tab, S.tab.n - 1, B.d)) return;
-    // the table cannot settle it: scan every point
-    w.exh += lane == 0;
-    Best E = B;
-    for (int p = lane; p < S.M; p += 32) take(E, __ldg(S.ref4 + p), q, p);
-    if (lane == 0) {
-        w.segs += 1;
-        w.pts += (unsigned)S.M;
-    }
-    warp_min(E);
-    B = E;
-}
-
-// Warp-aggregated accumulation of the work counters: queries, rows, segments,
-// points, queries that reached the far phase, queries that reached the
-// exhaustive scan.
-__device__ __forceinline__ void add_stats(unsigned long long* stats, const Work& w) {
-    unsigned long long v[6] = {w.queries, w.rows, w.segs, w.pts, w.far, w.exh};
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_down_sync(kFull, v[a], off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int a = 0; a < 6; ++a) atomicAdd(stats + a, v[a]);
-    }
-}
 
 __global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float* __restrict__ q, int64_t n,
                                                       int32_t* __restrict__ idx, float* __restrict__ d2,

@@ -14,8 +14,9 @@ namespace {
 
 constexpr int kThreads = 1024;
 
-__global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t0, int64_t N,
-                                                        int32_t m, int32_t* __restrict__ out) {
+// The minibatch of iteration t into row[0..m) by the whole CTA (kThreads threads).
+__device__ __forceinline__ void minibatch_row(uint64_t seed, int64_t t, int64_t N, int32_t m,
+                                              int32_t* __restrict__ row) {
     __shared__ unsigned hist[256];
     __shared__ uint64_t s_prefix;
     __shared__ unsigned s_rem;
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const uint64_t base = sm64_at(seed, (uint64_t)(t0 + blockIdx.x) + 1);
+    const uint64_t base = sm64_at(seed, (uint64_t)t + 1);
 
     uint64_t prefix = 0, mask = 0;
     unsigned rem = (unsigned)m;       // rank (1-based) still wanted among keys matching prefix
@@ -71,7 +72,6 @@ __global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t
     }
 
     // selected: (key & mask) <= prefix, compacted in ascending index order
-    int32_t* row = out + (int64_t)blockIdx.x * m;
     unsigned written = 0;
     for (int64_t i0 = 0; i0 < N; i0 += kThreads) {
         const int64_t i = i0 + tid;
@@ -100,7 +100,27 @@ __global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t0, int64_t N, int32_t m,
+                                                        int32_t* __restrict__ out) {
+    minibatch_row(seed, t0 + blockIdx.x, N, m, out + (int64_t)blockIdx.x * m);
+}
+
+// grid (T, P): problem p uses seed + p, its own source size and row [p][t].
+__global__ void __launch_bounds__(kThreads) k_minibatch_batched(uint64_t seed, int32_t T, int32_t m,
+                                                                const int64_t* __restrict__ src_off,
+                                                                int32_t* __restrict__ out) {
+    const int p = blockIdx.y, t = blockIdx.x;
+    minibatch_row(seed + (uint64_t)p, t, src_off[p + 1] - src_off[p], m, out + ((int64_t)p * T + t) * m);
+}
+
 }  // namespace
+
+cudaError_t launch_minibatch_batched(uint64_t seed, int32_t T, int32_t m, int32_t P, const int64_t* src_off,
+                                     int32_t* out, cudaStream_t s) {
+    if (T <= 0 || P <= 0) return cudaSuccess;
+    k_minibatch_batched<<<dim3(T, P), kThreads, 0, s>>>(seed, T, m, src_off, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_minibatch(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
                              int32_t* out, cudaStream_t s) {

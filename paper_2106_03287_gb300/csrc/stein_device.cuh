@@ -1,0 +1,303 @@
+// Stein + Adam device code shared by the single-problem kernel and the
+// batched persistent kernel.  See k_stein.cu for the description.
+#pragma once
+
+#include <float.h>
+
+#include "common.cuh"
+
+namespace sicp {
+namespace sd {
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr float kTwoPiHi = 6.28318548202514648f;      // float nearest 2 pi
+constexpr float kTwoPiLo = -1.74845553146951576e-7f;  // 2 pi - kTwoPiHi
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+__device__ __forceinline__ float wrapf(float x) {
+    const float r = rintf(x * kInvTwoPi);
+    return fmaf(-r, kTwoPiLo, fmaf(-r, kTwoPiHi, x));
+}
+
+__device__ __forceinline__ float pair_d2(const float* th, int j, int l, int block) {
+    const float* a = th + 6 * j + 3 * block;
+    const float* b = th + 6 * l + 3 * block;
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float d = a[c] - b[c];
+        if (block) d = wrapf(d);
+        s = fmaf(d, d, s);
+    }
+    return s;
+}
+
+constexpr int kCacheFloats = 40000;   // pair distances of both blocks kept in shared memory (K <= 200)
+
+// A team is a contiguous range of threads of the CTA with its own named barrier.
+struct Team {
+    int t0, n, bar;
+};
+__device__ __forceinline__ void team_sync(const Team& T) {
+    asm volatile("bar.sync %0, %1;" ::"r"(T.bar), "r"(T.n) : "memory");
+}
+
+// Visit the K(K-1)/2 distances of unique pairs j < l of one block, team-uniformly:
+// every thread of the team calls f(valid, value) the same number of times.
+template <class F>
+__device__ __forceinline__ void for_each_pair(const Team& T, const float* D, bool cached, const float* th, int K,
+                                              int block, F f) {
+    const int lt = threadIdx.x - T.t0;
+    if (cached) {
+        const int n = K * (K - 1) / 2;
+        for (int base = 0; base < n; base += T.n) {
+            const int p = base + lt;
+            const bool v = p < n;
+            f(v, v ? D[p] : 0.f);
+        }
+    } else {
+        const int n = K * K;
+        for (int base = 0; base < n; base += T.n) {
+            const int p = base + lt;
+            const int j = p / K, l = p % K;
+            const bool v = p < n && j < l;
+            f(v, v ? pair_d2(th, j, l, block) : 0.f);
+        }
+    }
+}
+
+// Exact value of rank `rank` (0-based) among the unique pair distances: radix
+// select over their bit patterns with 11-, 11- and 10-bit digits, counting
+// with one shared atomic per distinct bin per warp.
+__device__ unsigned select_rank(const Team& T, const float* D, bool cached, const float* th, int K, int block,
+                                unsigned rank, unsigned* hist, unsigned* s_u, unsigned* wsum) {
+    const int lane = threadIdx.x & 31, lt = threadIdx.x - T.t0, lw = lt >> 5;
+    unsigned prefix = 0, mask = 0, rem = rank + 1;
+    const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = shifts[pass], nb = 1 << widths[pass];
+        for (int i = lt; i < nb; i += T.n) hist[i] = 0;
+        team_sync(T);
+        for_each_pair(T, D, cached, th, K, block, [&](bool v, float x) {
+            const unsigned b = __float_as_uint(x);
+            const bool m = v && (b & mask) == prefix;
+            const unsigned bin = m ? (b >> shift) & (unsigned)(nb - 1) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (m && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+        });
+        team_sync(T);
+        {
+            // team-wide scan of the histogram: thread lt owns bins [lt*per, lt*per + per)
+            const int per = nb / T.n;
+            unsigned tot = 0;
+            for (int q = 0; q < per; ++q) tot += hist[lt * per + q];
+            unsigned incl = tot;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            if (lane == 31) wsum[lw] = incl;
+            team_sync(T);
+            if (lw == 0) {
+                const unsigned v = lane < (T.n >> 5) ? wsum[lane] : 0u;
+                unsigned vi = v;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned u = __shfl_up_sync(0xffffffffu, vi, off);
+                    if (lane >= off) vi += u;
+                }
+                if (lane < (T.n >> 5)) wsum[lane] = vi - v;
+            }
+            team_sync(T);
+            incl += wsum[lw];
+            unsigned acc = incl - tot;
+            if (acc < rem && rem <= incl) {
+                for (int q = 0; q < per; ++q) {
+                    const unsigned c = hist[lt * per + q];
+                    if (rem <= acc + c) {
+                        s_u[0] = prefix | ((unsigned)(lt * per + q) << shift);
+                        s_u[1] = rem - acc;
+                        break;
+                    }
+                    acc += c;
+                }
+            }
+        }
+        team_sync(T);
+        prefix = s_u[0];
+        rem = s_u[1];
+        mask |= (unsigned)(nb - 1) << shift;
+        team_sync(T);
+    }
+    return prefix;
+}
+
+// Median heuristic: median of all K*K squared distances of the block (the K
+// zeros of the diagonal plus every unique pair twice; the mean of the two
+// middle values for an even count) divided by ln(K+1); 1 if the median is 0.
+__device__ float bandwidth(const Team& T, const float* th, int K, int block, float* D, bool cached,
+                           unsigned* hist, unsigned* s_u, unsigned* wsum) {
+    if (K < 2) return 1.f;
+    const int lt = threadIdx.x - T.t0;
+    if (cached) {
+        const int n = K * K;
+        for (int p = lt; p < n; p += T.n) {
+            const int j = p / K, l = p % K;
+            if (j < l) D[j * K - j * (j + 1) / 2 + (l - j - 1)] = pair_d2(th, j, l, block);
+        }
+        team_sync(T);
+    }
+    const unsigned n = (unsigned)K * (unsigned)K;
+    const unsigned r_lo = (n - 1) / 2, r_hi = n / 2, uK = (unsigned)K;
+    // full-multiset rank r maps to 0 for r < K, else to unique rank (r - K) / 2
+    unsigned v_lo = 0;
+    if (r_lo >= uK) v_lo = select_rank(T, D, cached, th, K, block, (r_lo - uK) / 2, hist, s_u, wsum);
+    float med = __uint_as_float(v_lo);
+    if (r_hi != r_lo) {
+        // the next order statistic: v_lo again if enough values are <= v_lo, else the smallest value above it
+        if (lt == 0) {
+            s_u[2] = 0;
+            s_u[3] = 0x7f800000u;
+        }
+        team_sync(T);
+        unsigned cnt = 0, mn = 0x7f800000u;
+        for_each_pair(T, D, cached, th, K, block, [&](bool v, float x) {
+            if (!v) return;
+            const unsigned b = __float_as_uint(x);
+            if (b <= v_lo) ++cnt;
+            else mn = min(mn, b);
+        });
+        atomicAdd(&s_u[2], cnt);
+        atomicMin(&s_u[3], mn);
+        team_sync(T);
+        const unsigned below = uK + 2 * s_u[2];   // full count of values <= v_lo
+        const float v_hi = (below > r_hi) ? med : __uint_as_float(s_u[3]);
+        med = 0.5f * (med + v_hi);
+        team_sync(T);
+    }
+    return med > 0.f ? med / logf((float)K + 1.f) : 1.f;
+}
+
+// One Stein + Adam update of K particles by the whole CTA (1024 threads), with
+// its shared memory laid out as described at the top of k_stein.cu.
+__device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
+    extern __shared__ float sm[];
+    float* th = sm;               // K x 6
+    float* G = sm + 6 * a.K;      // K x 6
+    float* Ph = sm + 12 * a.K;    // K x 6: the Stein direction
+    float* D = sm + 18 * a.K;     // unique pair distances of both blocks when they fit
+    __shared__ unsigned hist[2][2048];
+    __shared__ unsigned s_u[2][4];
+    __shared__ unsigned wsum[2][32];
+    __shared__ float s_h[2];
+    const int K = a.K, tid = threadIdx.x;
+    const int pairs = K * (K - 1) / 2;
+    const bool cached = 2 * pairs <= kCacheFloats;
+
+    // G = -N gbar + grad log prior, gbar = inv_m * (sum of the chunk partials)
+    if (a.chunks == 1) {
+        for (int idx = tid; idx < 6 * K; idx += blockDim.x) {
+            const float x = a.theta[idx], gb = a.partial[idx];
+            const int c = idx % 6;
+            th[idx] = x;
+            float pr = 0.f;
+            if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
+            G[idx] = fmaf(-a.N, gb * a.inv_m, pr);
+        }
+    } else {
+        // one warp per component, lanes over chunks, fixed butterfly order
+        const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+        for (int idx = warp; idx < 6 * K; idx += nwarps) {
+            const int j = idx / 6, c = idx % 6;
+            float s = 0.f;
+            for (int ch = lane; ch < a.chunks; ch += 32) s += a.partial[((int64_t)ch * K + j) * 6 + c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) {
+                const float x = a.theta[idx];
+                th[idx] = x;
+                float pr = 0.f;
+                if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
+                G[idx] = fmaf(-a.N, s * a.inv_m, pr);
+            }
+        }
+    }
+    __syncthreads();
+
+    // the two halves of the CTA take the translation and rotation medians at the same time
+    {
+        const int half = tid >= (int)blockDim.x / 2;
+        const Team T = {half * (int)blockDim.x / 2, (int)blockDim.x / 2, 1 + half};
+        const float h = bandwidth(T, th, K, half, D + (cached ? half * pairs : 0), cached, hist[half], s_u[half],
+                                  wsum[half]);
+        if (tid == T.t0) s_h[half] = h;
+    }
+    __syncthreads();
+    const float h_t = s_h[0], h_r = s_h[1];
+    const float inv_ht = 1.f / h_t, inv_hr = 1.f / h_r;
+    const float two_ht = 2.f / h_t, two_hr = 2.f / h_r;
+    if (tid == 0 && a.out_h) { a.out_h[0] = h_t; a.out_h[1] = h_r; }
+
+    // S lanes per particle (power of two <= 32), each summing over j = lane (mod S)
+    int S = 32;
+    while (S > 1 && K * S > (int)blockDim.x) S >>= 1;
+    const int groups = blockDim.x / S;
+    const int g_id = tid / S, g_lane = tid % S;
+    const int rounds = (K + groups - 1) / groups;
+    const float invK = 1.f / (float)K;
+    const float omb1 = 1.f - a.beta1, omb2 = 1.f - a.beta2;   // exact for beta in [0.5, 1]
+    const float c1 = -expm1f((float)a.t * log1pf(-omb1));    // 1 - beta1^t
+    const float c2 = -expm1f((float)a.t * log1pf(-omb2));    // 1 - beta2^t
+    for (int r = 0; r < rounds; ++r) {
+        const int i = r * groups + g_id;
+        const bool valid = i < K;
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            const float* ti = th + 6 * i;
+            for (int j = g_lane; j < K; j += S) {
+                const float* tj = th + 6 * j;
+                const float* Gj = G + 6 * j;
+                float dt[3], dr[3], Dt = 0.f, Dr = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dt[c] = ti[c] - tj[c];
+                    Dt = fmaf(dt[c], dt[c], Dt);
+                    dr[c] = wrapf(ti[3 + c] - tj[3 + c]);
+                    Dr = fmaf(dr[c], dr[c], Dr);
+                }
+                const float kt = expf(-Dt * inv_ht), kr = expf(-Dr * inv_hr);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    acc[c] += kt * fmaf(two_ht, dt[c], Gj[c]);
+                    acc[3 + c] += kr * fmaf(two_hr, dr[c], Gj[3 + c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            for (int off = S >> 1; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, S);
+        if (valid && g_lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Ph[6 * i + c] = acc[c] * invK;
+        }
+    }
+    __syncthreads();
+    // Adam on g = -phi, all components in parallel
+    for (int idx = tid; idx < 6 * K; idx += blockDim.x) {
+        const float phi = Ph[idx];
+        if (a.out_phi) a.out_phi[idx] = phi;
+        const float g = -phi;
+        const float mo = fmaf(a.beta1, a.adam_m[idx], omb1 * g);
+        const float ve = fmaf(a.beta2, a.adam_v[idx], omb2 * g * g);
+        a.adam_m[idx] = mo;
+        a.adam_v[idx] = ve;
+        const float mh = mo / c1, vh = ve / c2;
+        a.theta[idx] = th[idx] - a.lr * mh / (sqrtf(vh) + a.eps);
+    }
+}
+
+}  // namespace
+}  // namespace sd
+}  // namespace sicp
