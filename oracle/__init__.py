@@ -83,6 +83,11 @@ def _setup(L):
         "or_step": (None, [_p, _i64, _p, _i64, _p, _p, _p, _i32, _p, _i64, _p, _p, _p, _p]),
         "or_register": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _p, _p, _p, _p]),
         "or_num_threads": (ctypes.c_int, []),
+        "or_mlp_nparam": (ctypes.c_int, []),
+        "or_bf16": (_f64, [_f64]),
+        "or_mlp_features": (None, [_p, _p]),
+        "or_mlp_forward": (None, [_p, _p, _i64, ctypes.c_int, _p]),
+        "or_mlp_loss_grad": (_f64, [_p, _p, _p, _i64, _f64, _f64, ctypes.c_int, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -277,3 +282,51 @@ def register(ref, src, theta0, params: Params):
     if rc != 0:
         raise ValueError(f"or_register rc={rc}")
     return th, mean, cov.reshape(6, 6)
+
+
+# ---------------------------------------------------------------- learned closest-point field
+
+MLP_D_IN, MLP_H, MLP_D_OUT = 112, 128, 16
+
+
+def mlp_nparam() -> int:
+    return _L().or_mlp_nparam()
+
+
+def bf16(x: float) -> float:
+    return float(_L().or_bf16(float(x)))
+
+
+def mlp_features(qn):
+    qn = _f64a(qn).reshape(3)
+    x = np.empty(MLP_D_IN)
+    _L().or_mlp_features(_ptr(qn), _ptr(x))
+    return x
+
+
+def mlp_forward(params, qn, bf16ops=False):
+    params, qn = _f64a(params), _f64a(qn).reshape(-1, 3)
+    out = np.empty((qn.shape[0], MLP_D_OUT))
+    _L().or_mlp_forward(_ptr(params), _ptr(qn), qn.shape[0], int(bf16ops), _ptr(out))
+    return out
+
+
+def mlp_loss_grad(params, qn, dstar, lam=0.1, delta=0.02, bf16ops=False, cstar=None):
+    params, qn, dstar = _f64a(params), _f64a(qn).reshape(-1, 3), _f64a(dstar).reshape(-1, 3)
+    grad = np.empty(mlp_nparam())
+    cs = None if cstar is None else _f64a(cstar)
+    loss = _L().or_mlp_loss_grad(_ptr(params), _ptr(qn), _ptr(dstar), qn.shape[0], lam, delta, int(bf16ops),
+                                 None if cs is None else _ptr(cs), _ptr(grad))
+    return float(loss), grad
+
+
+def mlp_split(params):
+    """Views W1, b1, W2, b2, W3, b3 of a flat parameter vector."""
+    p = np.asarray(params)
+    sizes = [(MLP_H, MLP_D_IN), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_D_OUT, MLP_H), (MLP_D_OUT,)]
+    out, o = [], 0
+    for sh in sizes:
+        n = int(np.prod(sh))
+        out.append(p[o:o + n].reshape(sh))
+        o += n
+    return out

@@ -456,3 +456,165 @@ OR_EXPORT int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned closest-point field (the surrogate of the correspondence search)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * An MLP maps a normalised query q~ = (q - c) / s to the displacement d~ to
+ * its nearest reference point (in the same normalised units) and a
+ * confidence logit z.  Features: q~ (3 values), then sin and cos of
+ * w_f q~_a for frequencies w_f = pi 2^(8 f / 15), f = 0..15, a = 0..2
+ * (96 values, index 3 + 6 f + 2 a), then zeros up to 112.
+ * Layers: 112 -> 128 (ReLU) -> 128 (ReLU) -> 16, of which outputs 0..2 are
+ * d~ and output 3 is z.  Parameters, flat: W1[128][112], b1[128],
+ * W2[128][128], b2[128], W3[16][128], b3[16] (33,040 values).
+ * Loss over n samples with targets d~*:
+ *   (1/n) sum_b [ |d~ - d~*|^2 + lam * (softplus(z) - c* z) ],
+ *   c* = exp(-|d~ - d~*|^2 / delta^2), held constant (not differentiated).
+ * bf16ops = 1 rounds the operands of every product to bfloat16 (round to
+ * nearest even) the way the tensor-core kernels store them: the features,
+ * the weights, the hidden activations, and the back-propagated deltas fed to
+ * the next product; accumulation stays in double.
+ */
+#define OR_D_IN 112
+#define OR_H 128
+#define OR_D_OUT 16
+#define OR_NPARAM (OR_H * OR_D_IN + OR_H + OR_H * OR_H + OR_H + OR_D_OUT * OR_H + OR_D_OUT)
+
+OR_EXPORT int or_mlp_nparam(void) { return OR_NPARAM; }
+
+/* Round a double to the nearest bfloat16 value (ties to even), via float. */
+OR_EXPORT double or_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;       /* inf / nan */
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double or_q(double x, int bf) { return bf ? or_bf16(x) : x; }
+
+OR_EXPORT void or_mlp_features(const double qn[3], double x[OR_D_IN]) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < OR_D_IN; ++i) x[i] = 0.0;
+    for (int a = 0; a < 3; ++a) x[a] = qn[a];
+    for (int f = 0; f < 16; ++f) {
+        double w = pi * pow(2.0, 8.0 * f / 15.0);
+        for (int a = 0; a < 3; ++a) {
+            x[3 + 6 * f + 2 * a] = sin(w * qn[a]);
+            x[3 + 6 * f + 2 * a + 1] = cos(w * qn[a]);
+        }
+    }
+}
+
+typedef struct {
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+} or_mlp;
+
+static or_mlp or_mlp_view(const double* p) {
+    or_mlp m;
+    m.W1 = p;
+    m.b1 = m.W1 + OR_H * OR_D_IN;
+    m.W2 = m.b1 + OR_H;
+    m.b2 = m.W2 + OR_H * OR_H;
+    m.W3 = m.b2 + OR_H;
+    m.b3 = m.W3 + OR_D_OUT * OR_H;
+    return m;
+}
+
+/* Forward pass of one sample: the (possibly rounded) features x, hidden
+ * activations h1, h2 as fed to the next product, and the 16 outputs. */
+static void or_mlp_fwd1(const or_mlp* m, const double xin[OR_D_IN], int bf, double x[OR_D_IN], double h1[OR_H],
+                        double h2[OR_H], double out[OR_D_OUT]) {
+    for (int i = 0; i < OR_D_IN; ++i) x[i] = or_q(xin[i], bf);
+    for (int j = 0; j < OR_H; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < OR_D_IN; ++i) s += or_q(m->W1[j * OR_D_IN + i], bf) * x[i];
+        s += m->b1[j];
+        h1[j] = or_q(s > 0.0 ? s : 0.0, bf);
+    }
+    for (int j = 0; j < OR_H; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < OR_H; ++i) s += or_q(m->W2[j * OR_H + i], bf) * h1[i];
+        s += m->b2[j];
+        h2[j] = or_q(s > 0.0 ? s : 0.0, bf);
+    }
+    for (int o = 0; o < OR_D_OUT; ++o) {
+        double s = 0.0;
+        for (int i = 0; i < OR_H; ++i) s += or_q(m->W3[o * OR_H + i], bf) * h2[i];
+        out[o] = s + m->b3[o];
+    }
+}
+
+/* Outputs (n x 16) for normalised queries qn (n x 3). */
+OR_EXPORT void or_mlp_forward(const double* params, const double* qn, int64_t n, int bf16ops, double* out) {
+    or_mlp m = or_mlp_view(params);
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < n; ++b) {
+        double xin[OR_D_IN], x[OR_D_IN], h1[OR_H], h2[OR_H];
+        or_mlp_features(qn + 3 * b, xin);
+        or_mlp_fwd1(&m, xin, bf16ops, x, h1, h2, out + OR_D_OUT * b);
+    }
+}
+
+/* Loss and its gradient with respect to all parameters (grad: OR_NPARAM).
+ * cstar_fixed (n, may be NULL) overrides the confidence targets. */
+OR_EXPORT double or_mlp_loss_grad(const double* params, const double* qn, const double* dstar, int64_t n,
+                                  double lam, double delta, int bf16ops, const double* cstar_fixed, double* grad) {
+    or_mlp m = or_mlp_view(params);
+    for (int i = 0; i < OR_NPARAM; ++i) grad[i] = 0.0;
+    double* gW1 = grad;
+    double* gb1 = gW1 + OR_H * OR_D_IN;
+    double* gW2 = gb1 + OR_H;
+    double* gb2 = gW2 + OR_H * OR_H;
+    double* gW3 = gb2 + OR_H;
+    double* gb3 = gW3 + OR_D_OUT * OR_H;
+    const int bf = bf16ops;
+    double loss = 0.0;
+    for (int64_t b = 0; b < n; ++b) {
+        double xin[OR_D_IN], x[OR_D_IN], h1[OR_H], h2[OR_H], out[OR_D_OUT];
+        or_mlp_features(qn + 3 * b, xin);
+        or_mlp_fwd1(&m, xin, bf, x, h1, h2, out);
+        const double* t = dstar + 3 * b;
+        double e2 = 0.0;
+        for (int a = 0; a < 3; ++a) e2 += (out[a] - t[a]) * (out[a] - t[a]);
+        const double cs = cstar_fixed ? cstar_fixed[b] : exp(-e2 / (delta * delta));
+        const double z = out[3];
+        const double sp = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
+        loss += e2 + lam * (sp - cs * z);
+        /* delta of the outputs (per sample; the 1/n is applied at the end) */
+        double d3[OR_D_OUT];
+        for (int o = 0; o < OR_D_OUT; ++o) d3[o] = 0.0;
+        for (int a = 0; a < 3; ++a) d3[a] = 2.0 * (out[a] - t[a]);
+        d3[3] = lam * (1.0 / (1.0 + exp(-z)) - cs);
+        for (int o = 0; o < OR_D_OUT; ++o) {
+            gb3[o] += d3[o];
+            for (int i = 0; i < OR_H; ++i) gW3[o * OR_H + i] += d3[o] * h2[i];
+        }
+        double d3q[OR_D_OUT], d2[OR_H], d1[OR_H];
+        for (int o = 0; o < OR_D_OUT; ++o) d3q[o] = or_q(d3[o], bf);
+        for (int i = 0; i < OR_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < OR_D_OUT; ++o) s += or_q(m.W3[o * OR_H + i], bf) * d3q[o];
+            d2[i] = or_q(h2[i] > 0.0 ? s : 0.0, bf);
+        }
+        for (int j = 0; j < OR_H; ++j) {
+            gb2[j] += d2[j];
+            for (int i = 0; i < OR_H; ++i) gW2[j * OR_H + i] += d2[j] * h1[i];
+        }
+        for (int i = 0; i < OR_H; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < OR_H; ++j) s += or_q(m.W2[j * OR_H + i], bf) * d2[j];
+            d1[i] = or_q(h1[i] > 0.0 ? s : 0.0, bf);
+        }
+        for (int j = 0; j < OR_H; ++j) {
+            gb1[j] += d1[j];
+            for (int i = 0; i < OR_D_IN; ++i) gW1[j * OR_D_IN + i] += d1[j] * x[i];
+        }
+    }
+    for (int i = 0; i < OR_NPARAM; ++i) grad[i] /= (double)n;
+    return loss / (double)n;
+}
