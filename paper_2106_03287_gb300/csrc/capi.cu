@@ -476,9 +476,9 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.stats = stats_ptr(ctx);
     g.gbar = d_g;
     g.inv_m = 1.f / (float)m;
-    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)(K / 8 + 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     g.done = (unsigned*)ctx->done.p;
-    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)(K / 8 + 1), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
     SICP_CUDA(launch_grad(ctx, mode, g));
     if (mode != SICP_NN_GRID)
         SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
@@ -572,7 +572,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
     if ((rc = ensure(ctx, ctx->gbar, b_th))) return rc;
-    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)(K / 8 + 1)))) return rc;
+    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     const bool grid = p.nn_mode == SICP_NN_GRID;
 
     const void *d_src, *d_th0;
@@ -585,7 +585,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
-    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)(K / 8 + 1), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
 
     const int stride = ctx->prof_stride;
     LoopKey key;

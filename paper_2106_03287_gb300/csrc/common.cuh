@@ -229,11 +229,11 @@ struct GradArgs {
     float* partial;        // [chunks][K][6] sums of gradient terms (not divided by m)
     int32_t* out_nn;       // K x m or null
     unsigned long long* stats;  // search work counters or null
-    // grid search only: the last CTA of each particle block folds the block's
-    // chunk partials into gbar = inv_m * sum (fixed chunk order); `done` holds
-    // one arrival counter per particle block, zero between launches.
+    // grid search only: the last warp to finish a particle folds that
+    // particle's chunk partials into gbar = inv_m * sum (fixed chunk order);
+    // `done` holds one arrival counter per particle, zero between launches.
     float* gbar;           // K x 6
-    unsigned* done;        // ceil(K / 8)
+    unsigned* done;        // K
     float inv_m;
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
