@@ -159,9 +159,10 @@ _CYL_R = 0.07
 _CYL_H = 0.25
 
 
-def _render_kinect(st: Stream, R_cam, t_cam, width=640, height=480, f=525.0):
+def _render_kinect(st: Stream, R_cam, t_cam, width=640, height=480, f=525.0, return_depth=False):
     """Depth-render the scene from a camera at (R_cam, t_cam) in the reference
-    camera frame. Returns valid points in the rendering camera's frame."""
+    camera frame. Returns valid points in the rendering camera's frame (and,
+    with return_depth, the noisy depth image, inf where a ray hits nothing)."""
     scale = width / 640.0
     fx = fy = f * scale
     cx, cy = (width - 1) / 2.0, (height - 1) / 2.0
@@ -205,19 +206,46 @@ def _render_kinect(st: Stream, R_cam, t_cam, width=640, height=480, f=525.0):
     valid = np.isfinite(best)
     depth = best[valid]                      # rays have camera z = 1: t is depth
     depth = depth + st.normal(depth.size, 0.001 * depth ** 2)
-    return dc[valid] * depth[:, None]
+    pts = dc[valid] * depth[:, None]
+    if not return_depth:
+        return pts
+    image = np.full(width * height, np.inf)
+    image[valid] = depth
+    return pts, image.reshape(height, width)
+
+
+def _seen_by(image, p, f=525.0):
+    """Which points p [n][3] (camera frame of the view that rendered `image`)
+    that view also sees: they project inside the image onto a pixel whose
+    depth agrees within 2 cm + 1 %."""
+    height, width = image.shape
+    fx = fy = f * width / 640.0
+    cx, cy = (width - 1) / 2.0, (height - 1) / 2.0
+    z = p[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = np.rint(fx * p[:, 0] / z + cx)
+        v = np.rint(fy * p[:, 1] / z + cy)
+    inside = (z > 0) & (u >= 0) & (u < width) & (v >= 0) & (v < height)
+    ok = np.zeros(p.shape[0], bool)
+    ui, vi = u[inside].astype(np.int64), v[inside].astype(np.int64)
+    ok[inside] = np.abs(image[vi, ui] - z[inside]) <= 0.02 + 0.01 * z[inside]
+    return ok
 
 
 def make_kinect_problem(seed: int, M=50_000, N=10_000, K=100, t_max=0.1,
                         ang_max_deg=20.0, init_t=0.15, init_ang_deg=20.0,
                         width=640, height=480):
     """Reference: M points of a render from the identity view. Source: N points
-    of a render from a view offset by a seeded pose."""
+    of a render from a view offset by a seeded pose, drawn from the part of
+    that render the reference view also sees (without this overlap crop the
+    point-to-point cost of a 20-degree offset is lowest far from the true pose,
+    pulled by source points that have no counterpart in the reference)."""
     st = Stream(seed, 2)
-    ref_all = _render_kinect(st, np.eye(3), np.zeros(3), width, height)
+    ref_all, ref_depth = _render_kinect(st, np.eye(3), np.zeros(3), width, height, return_depth=True)
     ref = ref_all[st.permutation(ref_all.shape[0])[:M]]
     R_gt, t_gt = random_pose(st, t_max, ang_max_deg)
     src_all = _render_kinect(st, R_gt, t_gt, width, height)
+    src_all = src_all[_seen_by(ref_depth, src_all @ R_gt.T + t_gt)]
     src = src_all[st.permutation(src_all.shape[0])[:N]]
     # a source point s (camera frame of the moved view) is R_gt s + t_gt in the reference frame
     theta_true = np.concatenate([t_gt, euler_of(R_gt)])
@@ -250,15 +278,8 @@ def _lidar_scene(st: Stream, n_boxes=40, n_poles=20, half=50.0, keep_out=3.0,
     return np.array(boxes), np.array(poles)
 
 
-def _scan_lidar(st: Stream, boxes, poles, sensor_xyz, yaw, beams=64,
-                el_lo=-25.0, el_hi=3.0, az_step=0.2, max_range=120.0, noise=0.02):
-    el = np.deg2rad(np.linspace(el_lo, el_hi, beams))
-    az = np.deg2rad(np.arange(0.0, 360.0, az_step))
-    E, A = np.meshgrid(el, az, indexing="ij")
-    dl = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
-    Rz = rotation(0.0, 0.0, yaw)
-    d = dl @ Rz.T
-    o = np.asarray(sensor_xyz, dtype=np.float64)
+def _cast_scene(boxes, poles, o, d):
+    """Distance along unit rays d [n][3] from o to the first surface (inf: none)."""
     best = np.full(d.shape[0], np.inf)
     with np.errstate(divide="ignore", invalid="ignore"):
         t = -o[2] / d[:, 2]
@@ -281,24 +302,55 @@ def _scan_lidar(st: Stream, boxes, poles, sensor_xyz, yaw, beams=64,
             hz = o[2] + t * d[:, 2]
             hit = (disc > 0) & (t > 0) & (hz >= 0) & (hz <= h)
             best = np.where(hit & (t < best), t, best)
+    return best
+
+
+def _scan_lidar(st: Stream, boxes, poles, sensor_xyz, yaw, beams=64,
+                el_lo=-25.0, el_hi=3.0, az_step=0.2, max_range=120.0, noise=0.02):
+    el = np.deg2rad(np.linspace(el_lo, el_hi, beams))
+    az = np.deg2rad(np.arange(0.0, 360.0, az_step))
+    E, A = np.meshgrid(el, az, indexing="ij")
+    dl = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    Rz = rotation(0.0, 0.0, yaw)
+    o = np.asarray(sensor_xyz, dtype=np.float64)
+    best = _cast_scene(boxes, poles, o, dl @ Rz.T)
     valid = best <= max_range
     rng_ = best[valid] + st.normal(int(valid.sum()), noise)
     return dl[valid] * rng_[:, None]          # sensor frame (yawed with the sensor)
 
 
+def _lidar_seen_by(boxes, poles, o, p, max_range, el_lo=-25.0, el_hi=3.0):
+    """Which world points p [n][3] a scanner at o sees: inside its range and
+    elevation span, and the first surface along the ray is p itself."""
+    v = p - o
+    r = np.linalg.norm(v, axis=1)
+    d = v / np.maximum(r, 1e-12)[:, None]
+    el = np.degrees(np.arcsin(np.clip(d[:, 2], -1.0, 1.0)))
+    ok = (r <= max_range) & (el >= el_lo - 0.2) & (el <= el_hi + 0.2)
+    hit = _cast_scene(boxes, poles, o, d[ok])
+    ok[ok] = np.abs(hit - r[ok]) <= 0.1 + 0.002 * r[ok]
+    return ok
+
+
 def make_lidar_problem(seed: int, K=200, t_max_xy=2.0, yaw_max_deg=10.0,
                        init_t=1.5, init_ang_deg=15.0, sensor_height=1.73,
-                       az_step=0.2):
+                       az_step=0.2, max_range=120.0):
     """Reference: scan from the origin. Source: scan from a pose offset by up to
-    t_max_xy in the ground plane and yaw_max_deg in yaw."""
+    t_max_xy in the ground plane and yaw_max_deg in yaw, keeping the points the
+    reference scanner also sees (the overlap)."""
     st = Stream(seed, 3)
     ang = st.uniform(1, 0, 2 * np.pi)[0]
     rad = st.uniform(1, 0, t_max_xy)[0]
     t_gt = np.array([rad * np.cos(ang), rad * np.sin(ang), 0.0])
     yaw = np.deg2rad(st.uniform(1, -yaw_max_deg, yaw_max_deg)[0])
     boxes, poles = _lidar_scene(st, sensors=((0.0, 0.0), (t_gt[0], t_gt[1])))
-    ref = _scan_lidar(st, boxes, poles, (0, 0, sensor_height), 0.0, az_step=az_step)
-    src = _scan_lidar(st, boxes, poles, (t_gt[0], t_gt[1], sensor_height), yaw, az_step=az_step)
+    ref = _scan_lidar(st, boxes, poles, (0, 0, sensor_height), 0.0, az_step=az_step, max_range=max_range)
+    src = _scan_lidar(st, boxes, poles, (t_gt[0], t_gt[1], sensor_height), yaw, az_step=az_step,
+                      max_range=max_range)
+    # a source point s (sensor frame, yawed) is Rz(yaw) s + t_gt in the reference frame
+    o_ref = np.array([0.0, 0.0, sensor_height])
+    world = src @ rotation(0.0, 0.0, yaw).T + t_gt + o_ref
+    src = src[_lidar_seen_by(boxes, poles, o_ref, world, max_range)]
     theta_true = np.array([t_gt[0], t_gt[1], 0.0, 0.0, 0.0, yaw])
     particles = init_particles(st, K, init_t, init_ang_deg)
     return dict(ref=ref.astype(np.float32), src=src.astype(np.float32),
@@ -340,8 +392,8 @@ def make_batched_problems(seed: int, P=256, M_lo=5_000, M_hi=80_000, src_frac=0.
 # parameters of each workload's run (iterations T, minibatch m, Adam step)
 WORKLOADS = {
     "box": dict(T=100, m=100, lr=0.01),
-    "kinect": dict(T=150, m=300, lr=0.01),
+    "kinect": dict(T=150, m=300, lr=0.03),
     "lidar": dict(T=200, m=500, lr=0.01),
     "batched": dict(T=100, m=300, lr=0.01),
-    "surrogate": dict(T=200, m=300, lr=0.01, surrogate_iters=150),
+    "surrogate": dict(T=200, m=300, lr=0.03, surrogate_iters=150),
 }
