@@ -73,10 +73,12 @@ typedef struct sicp_params {
     float prior_mu[6];         /* prior means (Eqs. trans_prior, rot_prior) */
     float prior_sigma[3];      /* translation prior divisor, printed as a variance */
     float prior_kappa[3];      /* von Mises concentrations */
+    float surrogate_min_conf;  /* SICP_NN_SURROGATE: queries whose confidence is below this use the exact search */
 } sicp_params;
 
 /* Fill `p` with the defaults: T 100, m 100, lr 0.01, Adam (0.9, 0.999, 1e-8),
- * seed 0, SICP_NN_GRID, uniform prior. */
+ * seed 0, SICP_NN_GRID, surrogate_iters 0, surrogate_min_conf 0.5, uniform
+ * prior. */
 void sicp_default_params(sicp_params* p);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -102,10 +104,15 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
  * particles_out [K][6] after T iterations; mean6 [6] and cov36 [6][6]
  * (row-major, divisor K-1, zero for K = 1) of the final particles, both
  * float64 (may be NULL).  T = 0 returns the input particles and their
- * moments.  1 <= K <= 2048.  Errors: SICP_EINVAL (N < 1, K outside [1, 2048],
- * m outside [1, N], T < 0,
- * bad mode, non-finite input), SICP_ENOREF, SICP_ENOSURROGATE, SICP_ENOMEM,
- * SICP_ECUDA. */
+ * moments.  1 <= K <= 2048.  With SICP_NN_SURROGATE the first
+ * min(surrogate_iters, T) iterations take their correspondences from the
+ * trained surrogate (sicp_surrogate_train), each query falling back to the
+ * exact grid search where the surrogate's confidence is below
+ * surrogate_min_conf or the query lies outside the cube it was trained on;
+ * the remaining iterations use the exact grid search.  Errors: SICP_EINVAL
+ * (N < 1, K outside [1, 2048], m outside [1, N], T < 0, surrogate_iters < 0,
+ * surrogate_min_conf outside [0, 1], bad mode, non-finite input),
+ * SICP_ENOREF, SICP_ENOSURROGATE, SICP_ENOMEM, SICP_ECUDA, SICP_ETIMEOUT. */
 int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in,
                   int32_t K, const sicp_params* p, float* particles_out, double* mean6,
                   double* cov36, int on_device);
@@ -167,7 +174,13 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
 /* Steps 2-4 (Eqs. trans_gradient, rotation_gradient): for K particles
  * [K][6] and one minibatch mb [m] of indices into src_xyz [N][3], the mean
  * gradient of L/2 per particle, out_gbar [K][6] float32, and optionally the
- * correspondences out_nn [K][m] int32 (may be NULL).  Errors as sicp_nn. */
+ * correspondences out_nn [K][m] int32 (may be NULL).  `mode` is
+ * SICP_NN_BRUTE_FP32, SICP_NN_GRID or SICP_NN_SURROGATE; the last takes each
+ * correspondence from the trained surrogate (predicted nearest point
+ * q + d) where its confidence is at least 0.5 and the query lies in the
+ * trained cube, from the exact grid search otherwise, and needs
+ * out_nn = NULL and K * m <= 2^24.  Errors as sicp_nn, plus
+ * SICP_ENOSURROGATE and SICP_ETIMEOUT in surrogate mode. */
 int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t* mb, int32_t m,
                   const float* particles, int32_t K, int32_t mode, float* out_gbar,
                   int32_t* out_nn, int on_device);
@@ -218,17 +231,78 @@ int sicp_icp_grad_noalloc(const float* ref_xyz, int64_t M, const float* src_xyz,
                           const int32_t* mb, int32_t m, const float* particles, int32_t K,
                           float* out_gbar, void* cuda_stream);
 
+/* ---- learned closest-point field (no counterpart in the paper) ----
+ *
+ * A small network that stands in for step 3 during the early iterations:
+ * for a query q it predicts the displacement d from q to its nearest
+ * reference point and a confidence c in (0, 1).  With c = (cx, cy, cz) the
+ * centre of the reference bounding box and s = 0.6 x its largest extent,
+ * q~ = (q - c) / s; the input features (112) are q~, then sin and cos of
+ * w_f q~_a for w_f = pi 2^(8f/15), f = 0..15, a = x, y, z (feature
+ * 3 + 6f + 2a is the sine, the next one the cosine), then zeros.  Layers:
+ * x -> h1 = relu(W1 x + b1) (128) -> h2 = relu(W2 h1 + b2) (128) ->
+ * o = W3 h2 + b3 (16); d = s (o0, o1, o2), c = sigmoid(o3); outputs 4..15
+ * are unused.  Parameters are float32, flat, in the order W1 [128][112],
+ * b1 [128], W2 [128][128], b2 [128], W3 [16][128], b3 [16]: 33,040 values.
+ * The GPU computes with bf16 weights, features and activations and float32
+ * accumulation (fifth-generation tensor cores).
+ *
+ * Training loss per sample (normalised units, targets d~* = (r - q) / s of
+ * the exact nearest reference point r):
+ *   |d~ - d~*|^2 + lam (softplus(o3) - c* o3),  c* = exp(-|d~ - d~*|^2 / delta^2)
+ * with c* held constant in the gradient; lam = 0.1 and delta = 0.01 in
+ * sicp_surrogate_train. */
+
+/* Train the surrogate of the context's reference cloud.  Draws n_queries
+ * (rounded down to a multiple of batch) queries from the counter-based stream
+ * `seed`: even ones are reference points plus normal offsets whose standard
+ * deviation per axis is log-uniform in [0.002 s, 0.1 s], odd ones uniform in
+ * the cube |q~| <= 1; labels them with the exact
+ * grid search; initialises the weights (He-normal from the same seed) and
+ * runs `epochs` passes of Adam (lr, 0.9, 0.999, 1e-8) over batches of `batch`
+ * samples in a fixed order.  out_loss (may be NULL): mean batch loss of the
+ * last epoch.  The surrogate stays valid until the next sicp_set_reference.
+ * Errors: SICP_EINVAL (n_queries outside [128, 2^26], epochs outside
+ * [1, 1e5], batch not a multiple of 128 in [128, 65536], lr <= 0),
+ * SICP_ENOREF, SICP_ENOMEM, SICP_ECUDA, SICP_ETIMEOUT. */
+int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
+                         float lr, float* out_loss);
+
+/* Read (set = 0) or replace (set = 1) the surrogate's parameters: params
+ * [33040] float32 in the layout above, norm4 = (cx, cy, cz, s); host arrays.
+ * Setting marks the surrogate trained.  Errors: SICP_EINVAL (NULL,
+ * non-finite value, s <= 0), SICP_ENOSURROGATE (reading before any
+ * surrogate exists), SICP_ENOMEM, SICP_ECUDA. */
+int sicp_surrogate_params(sicp_ctx* ctx, int set, float* params, float* norm4);
+
+/* The training kernels' loss and gradient for given parameters [33040] on
+ * n normalised queries qn [n][3] with targets dstar [n][3] (host arrays):
+ * out_loss (may be NULL) the mean loss, out_grad [33040] its gradient with
+ * respect to the parameters.  The context's own surrogate is left unchanged.
+ * n a multiple of 128 in [128, 65536].  Errors: SICP_EINVAL, SICP_ENOMEM,
+ * SICP_ECUDA, SICP_ETIMEOUT. */
+int sicp_surrogate_loss_grad(sicp_ctx* ctx, const float* params, const float* qn, const float* dstar,
+                             int64_t n, float lam, float delta, float* out_loss, float* out_grad);
+
+/* Surrogate inference: for queries q [n][3] (metres) the predicted
+ * displacement out_disp [n][3] (metres; the predicted nearest point is
+ * q + d) and confidence out_conf [n].  n = 0 is a no-op.  Errors:
+ * SICP_EINVAL, SICP_ENOSURROGATE, SICP_ECUDA, SICP_ETIMEOUT. */
+int sicp_surrogate_infer(sicp_ctx* ctx, const float* q, int64_t n, float* out_disp, float* out_conf,
+                         int on_device);
+
 /* ---- measurement ---- */
 
 /* Work counters of the grid search (no counterpart in the paper; they state
  * the algorithmic bytes a search moved).  Copies the counters accumulated
- * since the previous call into out6 (may be NULL): queries, rows examined
+ * since the previous call into out8 (may be NULL): queries, rows examined
  * (one row span each), row segments read (two cell offsets each), candidate
  * points read (16 bytes each), queries that went on to the coarse level,
- * queries that went on to the exhaustive scan; then zeroes them and turns
+ * queries that went on to the exhaustive scan, queries put to the surrogate,
+ * surrogate queries sent on to the exact search; then zeroes them and turns
  * counting on (enable = 1) or off.  Counting adds six warp-aggregated atomics
  * per 32 lanes. */
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out6);
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8);
 
 /* Kernel timing inside sicp_register (no counterpart in the paper).  With
  * stride s > 0 the captured loop records CUDA events around the gradient and

@@ -7,4 +7,5 @@ from .binding import (  # noqa: F401
     LIB_PATH, lib, sicp_create, sicp_default_params, sicp_destroy, sicp_icp_grad, sicp_last_error,
     sicp_minibatch, sicp_moments, sicp_nn, sicp_params, sicp_profile, sicp_register, sicp_set_reference,
     sicp_stats, sicp_stein_adam, sicp_icp_grad_noalloc, sicp_register_batched, sicp_autotune_batched, pack_batch,
+    SURROGATE_NPARAM, sicp_surrogate_train, sicp_surrogate_params, sicp_surrogate_loss_grad, sicp_surrogate_infer,
 )

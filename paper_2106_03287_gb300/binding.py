@@ -40,7 +40,10 @@ EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
     "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
+    "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
 )
+
+SURROGATE_NPARAM = 33040
 
 
 class SicpError(RuntimeError):
@@ -56,6 +59,7 @@ class sicp_params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("nn_mode", ctypes.c_int32), ("surrogate_iters", ctypes.c_int32), ("prior", ctypes.c_int32),
         ("prior_mu", ctypes.c_float * 6), ("prior_sigma", ctypes.c_float * 3), ("prior_kappa", ctypes.c_float * 3),
+        ("surrogate_min_conf", ctypes.c_float),
     ]
 
 
@@ -89,6 +93,10 @@ def lib() -> ctypes.CDLL:
             "sicp_register_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, P, P, P, ctypes.c_int]),
             "sicp_autotune_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, I32, ctypes.c_char_p, P, P,
                                                      ctypes.c_int]),
+            "sicp_surrogate_train": (ctypes.c_int, [P, I64, U64, I32, I32, F32, P]),
+            "sicp_surrogate_params": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+            "sicp_surrogate_loss_grad": (ctypes.c_int, [P, P, P, P, I64, F32, F32, P, P]),
+            "sicp_surrogate_infer": (ctypes.c_int, [P, P, I64, P, P, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -255,10 +263,11 @@ def sicp_moments(ctx, particles):
 
 
 def sicp_stats(ctx, enable: bool = True):
-    """Grid-search counters since the last call (queries, rows, segments,
-    points, coarse-level queries, exhaustive-scan queries) as a uint64 array;
-    then resets them and sets counting on/off."""
-    out = np.zeros(6, np.uint64)
+    """Search counters since the last call (queries, rows, segments, points,
+    coarse-level queries, exhaustive-scan queries, surrogate queries,
+    surrogate queries sent to the exact search) as a uint64 array; then
+    resets them and sets counting on/off."""
+    out = np.zeros(8, np.uint64)
     _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
@@ -269,6 +278,57 @@ def sicp_profile(ctx, stride: int = 0):
     out = np.zeros(4, np.float64)
     _check(ctx, lib().sicp_profile(ctx, int(stride), out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def sicp_surrogate_train(ctx, n_queries: int, seed: int = 0, epochs: int = 10, batch: int = 4096,
+                         lr: float = 1e-3) -> float:
+    """Train the context's learned closest-point field; returns the mean batch loss of the last epoch."""
+    loss = ctypes.c_float(0.0)
+    _check(ctx, lib().sicp_surrogate_train(ctx, int(n_queries), seed & ((1 << 64) - 1), int(epochs), int(batch),
+                                           float(lr), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def sicp_surrogate_params(ctx, params=None, norm4=None):
+    """With params/norm4 None: returns (params [33040] float32, norm4 [4] float32).
+    Otherwise sets them (host arrays) and returns None."""
+    if params is None:
+        p = np.empty(SURROGATE_NPARAM, np.float32)
+        n = np.empty(4, np.float32)
+        _check(ctx, lib().sicp_surrogate_params(ctx, 0, _ptr(p, np.float32), _ptr(n, np.float32)))
+        return p, n
+    p = np.ascontiguousarray(params, np.float32)
+    n = np.ascontiguousarray(norm4, np.float32)
+    if p.shape != (SURROGATE_NPARAM,) or n.shape != (4,):
+        raise ValueError("params must have 33040 values and norm4 four")
+    _check(ctx, lib().sicp_surrogate_params(ctx, 1, _ptr(p, np.float32), _ptr(n, np.float32)))
+    return None
+
+
+def sicp_surrogate_loss_grad(ctx, params, qn, dstar, lam: float = 0.1, delta: float = 0.02):
+    """Loss and gradient [33040] of the training kernels (host arrays)."""
+    p = np.ascontiguousarray(params, np.float32)
+    qn = np.ascontiguousarray(qn, np.float32)
+    dstar = np.ascontiguousarray(dstar, np.float32)
+    if p.shape != (SURROGATE_NPARAM,) or qn.shape != dstar.shape or qn.ndim != 2 or qn.shape[1] != 3:
+        raise ValueError("params [33040], qn and dstar [n][3]")
+    g = np.empty(SURROGATE_NPARAM, np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(ctx, lib().sicp_surrogate_loss_grad(ctx, _ptr(p, np.float32), _ptr(qn, np.float32),
+                                               _ptr(dstar, np.float32), qn.shape[0], float(lam), float(delta),
+                                               ctypes.byref(loss), _ptr(g, np.float32)))
+    return float(loss.value), g
+
+
+def sicp_surrogate_infer(ctx, q):
+    """Predicted displacement [n][3] (metres) and confidence [n] per query [n][3]."""
+    q = _host(q, np.float32)
+    n = q.shape[0]
+    d = _empty(q, (n, 3), np.float32)
+    c = _empty(q, (n,), np.float32)
+    _check(ctx, lib().sicp_surrogate_infer(ctx, _ptr(q, np.float32), n, _ptr(d, np.float32), _ptr(c, np.float32),
+                                           _on_device(q)))
+    return d, c
 
 
 def sicp_icp_grad_noalloc(ref_xyz, src_xyz, mb, particles, out_gbar=None, stream=None):

@@ -55,6 +55,9 @@ struct LoopKey {
     int32_t K, T, m, mode, chunks, stride, pad;
     int32_t pi[4];          // T, m, nn_mode, prior
     float pf[16];           // lr, betas, eps, prior mu/sigma/kappa
+    int32_t surr_iters;
+    float min_conf;
+    uint64_t surr_gen;      // surrogate weights / normalisation version
     uint64_t seed;
     const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
@@ -145,8 +148,10 @@ int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
     if (mode == SICP_NN_BRUTE_FP32 || mode == SICP_NN_GRID) return SICP_OK;
     if (mode == SICP_NN_BRUTE_BF16)
         return set_err(ctx, SICP_EINVAL, "nn_mode %d (BF16 tensor-core search) is not available in this build", mode);
-    if (mode == SICP_NN_SURROGATE && allow_surrogate)
+    if (mode == SICP_NN_SURROGATE && allow_surrogate) {
+        if (surrogate_ready(ctx)) return SICP_OK;
         return set_err(ctx, SICP_ENOSURROGATE, "no trained surrogate on this context");
+    }
     return set_err(ctx, SICP_EINVAL, "unknown nn_mode %d", mode);
 }
 
@@ -159,6 +164,7 @@ void fill_defaults(sicp_params* p) {
     p->beta2 = 0.999f;
     p->eps = 1e-8f;
     p->nn_mode = SICP_NN_GRID;
+    p->surrogate_min_conf = 0.5f;
     for (int a = 0; a < 3; ++a) {
         p->prior_sigma[a] = 1.f;
         p->prior_kappa[a] = 1.f;
@@ -180,6 +186,9 @@ int check_params(sicp_ctx* ctx, const sicp_params& p) {
     if (!(p.eps > 0.f) || !isfinite(p.lr) || !(p.lr >= 0.f))
         return set_err(ctx, SICP_EINVAL, "lr must be finite and >= 0, eps > 0");
     if (p.prior != 0 && p.prior != 1) return set_err(ctx, SICP_EINVAL, "prior must be 0 or 1");
+    if (p.surrogate_iters < 0) return set_err(ctx, SICP_EINVAL, "surrogate_iters must be >= 0");
+    if (!(p.surrogate_min_conf >= 0.f && p.surrogate_min_conf <= 1.f))
+        return set_err(ctx, SICP_EINVAL, "surrogate_min_conf must lie in [0, 1]");
     if (p.prior == 1) {
         for (int a = 0; a < 3; ++a)
             if (!(p.prior_sigma[a] > 0.f) || !(p.prior_kappa[a] >= 0.f))
@@ -243,6 +252,7 @@ cudaError_t launch_grad(sicp_ctx* ctx, int32_t mode, const GradArgs& g) {
 }
 
 constexpr int32_t kMaxK = 2048;
+constexpr float kSurrogateIcpGradConf = 0.5f;   // confidence threshold of sicp_icp_grad's surrogate mode
 constexpr int64_t kMaxN = 0x7fffffff;
 constexpr int64_t kMaxM = (int64_t)1 << 30;
 
@@ -276,7 +286,7 @@ int sicp_create(sicp_ctx** out, int device, void* cuda_stream) {
         c->own_stream = true;
     }
     c->graphs = new GraphCache();
-    if (kernel_attrs_init() != cudaSuccess) {
+    if (kernel_attrs_init() != cudaSuccess || surrogate_kernel_attrs() != cudaSuccess) {
         cudaGetLastError();
         sicp_destroy(c);
         return SICP_ECUDA;
@@ -299,6 +309,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     delete c->graphs;
     if (c->batch) batch_destroy(c->batch);
+    if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done};
     for (Buf* b : bufs)
@@ -339,6 +350,7 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
         ctx->ref_cap = M;
     }
     ctx->M = 0;
+    surrogate_invalidate(ctx);   // a surrogate belongs to the reference it was trained on
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_xyz, M, ctx->ref4, (int*)ctx->flags.p, ctx->stream));
     int flags[4];
@@ -425,7 +437,10 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     if (!src_xyz || !mb || !particles || !out_gbar) return set_err(ctx, SICP_EINVAL, "null pointer");
     if (N < 1 || N > kMaxN || m < 1 || K < 1 || K > 65535)
         return set_err(ctx, SICP_EINVAL, "icp_grad needs N >= 1, m >= 1, 1 <= K <= 65535");
-    int rc = check_mode(ctx, mode, false);
+    const bool surr = mode == SICP_NN_SURROGATE;
+    if (surr && (out_nn || (int64_t)K * m > ((int64_t)1 << 24)))
+        return set_err(ctx, SICP_EINVAL, "surrogate mode needs out_nn = NULL and K * m <= 2^24");
+    int rc = check_mode(ctx, mode, true);
     if (rc) return rc;
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     if (!on_device) {
@@ -451,9 +466,10 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
         d_mb = aux + b_src;
         d_th = aux + b_src + b_mb;
     }
-    const int chunks = (mode == SICP_NN_GRID ? grad_layout_grid(m) : grad_layout(m)).chunks;
+    const int chunks = (mode == SICP_NN_BRUTE_FP32 ? grad_layout(m) : grad_layout_grid(m)).chunks;
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
-    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
+    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)(surr && m > chunks ? m : chunks) * K))) return rc;
+    if (surr && (rc = surrogate_prepare(ctx, (int64_t)K * m))) return rc;
     if ((rc = ensure(ctx, ctx->tmp_out, (sizeof(float) * 6 + sizeof(int32_t) * (size_t)m) * K))) return rc;
     float* d_g = (float*)ctx->tmp_out.p;
     int32_t* d_nn = (int32_t*)((char*)ctx->tmp_out.p + sizeof(float) * 6 * K);
@@ -479,11 +495,20 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     g.done = (unsigned*)ctx->done.p;
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
-    SICP_CUDA(launch_grad(ctx, mode, g));
-    if (mode != SICP_NN_GRID)
-        SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
+    if (surr) {
+        SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, m, g.theta, K, kSurrogateIcpGradConf, (float*)ctx->partial.p,
+                                        d_g, g.stats, (int*)ctx->flags.p + 3));
+    } else {
+        SICP_CUDA(launch_grad(ctx, mode, g));
+        if (mode != SICP_NN_GRID)
+            SICP_CUDA(launch_partial_to_gbar((const float*)ctx->partial.p, chunks, K, 1.f / (float)m, d_g, ctx->stream));
+    }
     if ((rc = copy_out(ctx, out_gbar, d_g, sizeof(float) * 6 * K, on_device))) return rc;
     if (out_nn && (rc = copy_out(ctx, out_nn, d_nn, sizeof(int32_t) * (size_t)m * K, on_device))) return rc;
+    if (surr) {
+        if ((rc = read_flags(ctx, flags))) return rc;
+        if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a tensor-core wait of the surrogate gave up");
+    }
     return sync(ctx);
 }
 
@@ -562,18 +587,26 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
         return set_err(ctx, SICP_EINVAL, "non-finite input");
     DeviceScope ds(ctx->device);
-    const int chunks = (p.nn_mode == SICP_NN_GRID ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
+    const bool surr = p.nn_mode == SICP_NN_SURROGATE;
+    if (surr && (int64_t)K * p.m > ((int64_t)1 << 24))
+        return set_err(ctx, SICP_EINVAL, "surrogate mode needs K * m <= 2^24 queries per iteration");
+    const bool grid = p.nn_mode == SICP_NN_GRID || surr;   // the surrogate's exact iterations use the grid
+    const int32_t exact_mode = surr ? SICP_NN_GRID : p.nn_mode;
+    const int chunks = (grid ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
+    const int32_t surr_T = surr ? (p.surrogate_iters < p.T ? p.surrogate_iters : p.T) : 0;
     const size_t b_th = sizeof(float) * 6 * K;
+    // partial sums of the exhaustive kernel, or the surrogate's per-query terms
+    const size_t partial_floats = 6 * (size_t)K * (size_t)(surr_T > 0 && p.m > chunks ? p.m : chunks);
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
     if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m))) return rc;
     if ((rc = ensure(ctx, ctx->theta, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->adam_m, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->adam_v, b_th))) return rc;
-    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)chunks * K))) return rc;
+    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * partial_floats))) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
     if ((rc = ensure(ctx, ctx->gbar, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
-    const bool grid = p.nn_mode == SICP_NN_GRID;
+    if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
 
     const void *d_src, *d_th0;
     if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
@@ -610,6 +643,9 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
         key.pf[10 + a] = p.prior_sigma[a];
         key.pf[13 + a] = p.prior_kappa[a];
     }
+    key.surr_iters = surr_T;
+    key.min_conf = surr ? p.surrogate_min_conf : 0.f;
+    key.surr_gen = surr ? ctx->surr_gen : 0;
     key.seed = p.seed;
     key.ptrs[0] = ctx->src4.p;
     key.ptrs[1] = ctx->mb.p;
@@ -645,9 +681,14 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
             const bool timed = prof && stride > 0 && (t % stride) == 0;
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np], ctx->stream, cudaEventRecordExternal));
             g.mb = (const int32_t*)ctx->mb.p + (size_t)t * p.m;
-            SICP_CUDA(launch_grad(ctx, p.nn_mode, g));
+            if (t < surr_T)
+                SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, p.m, theta, K, p.surrogate_min_conf,
+                                                (float*)ctx->partial.p, (float*)ctx->gbar.p, g.stats,
+                                                (int*)ctx->flags.p + 3));
+            else
+                SICP_CUDA(launch_grad(ctx, exact_mode, g));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
-            // the grid kernel folds its partials into gbar itself; the exhaustive one leaves `chunks` partials
+            // the grid kernel and the surrogate path leave gbar; the exhaustive kernel leaves `chunks` partials
             SteinArgs a = grid ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
                                             (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t + 1)
                                : stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
@@ -700,27 +741,28 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     int flags[4];
     if ((rc = read_flags(ctx, flags))) return rc;
     if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
+    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a tensor-core wait of the surrogate gave up");
     if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
     if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
     if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;
     return sync(ctx);
 }
 
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out6) {
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     DeviceScope ds(ctx->device);
-    int rc = ensure(ctx, ctx->stats, 6 * sizeof(unsigned long long));
+    int rc = ensure(ctx, ctx->stats, 8 * sizeof(unsigned long long));
     if (rc) return rc;
-    if (out6) {
-        unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+    if (out8) {
+        unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (ctx->stats_on) {
             SICP_CUDA(cudaMemcpyAsync(h, ctx->stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
             if ((rc = sync(ctx))) return rc;
         }
-        for (int a = 0; a < 6; ++a) out6[a] = (uint64_t)h[a];
+        for (int a = 0; a < 8; ++a) out8[a] = (uint64_t)h[a];
     }
-    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 6 * sizeof(unsigned long long), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), ctx->stream));
     ctx->stats_on = enable != 0;
     return sync(ctx);
 }

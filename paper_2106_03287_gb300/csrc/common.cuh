@@ -144,6 +144,8 @@ struct Buf {
 struct GraphCache;
 struct BatchState;
 void batch_destroy(BatchState* b);
+struct Surrogate;
+void surrogate_destroy(Surrogate* s);
 
 }  // namespace sicp
 
@@ -172,6 +174,8 @@ struct sicp_ctx {
     double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
     sicp::GraphCache* graphs = nullptr;
     sicp::BatchState* batch = nullptr;   // state of the batched path, created on first use
+    sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
+    uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
 };
 
 namespace sicp {
@@ -256,6 +260,24 @@ struct SteinArgs {
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);
+
+// Learned closest-point field (k_mlp.cu)
+cudaError_t surrogate_kernel_attrs();
+bool surrogate_ready(const sicp_ctx* ctx);
+void surrogate_invalidate(sicp_ctx* ctx);
+// One iteration's gradient with the surrogate: per-query terms into qterms
+// [K][m][6] (the exact grid search, in a second kernel, for queries whose
+// confidence is below min_conf or that leave the trained cube), then gbar
+// [K][6] = their mean per particle.
+// stats (8 counters or null): slots 0..5 as the grid search, 6 surrogate
+// tiles' queries, 7 queries sent to the exact search.  err: set on a
+// tensor-core wait that gave up.
+// Size the surrogate path's fallback list for `queries` per iteration and
+// clear its count (before capturing a loop that calls surrogate_launch_grad).
+int surrogate_prepare(sicp_ctx* ctx, int64_t queries);
+cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta,
+                                  int K, float min_conf, float* qterms, float* gbar, unsigned long long* stats,
+                                  int* err);
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);

@@ -33,6 +33,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_binding_params_layout_matches_defaults():
     p = S.sicp_default_params()
-    assert (p.T, p.m, p.nn_mode, p.prior) == (100, 100, S.SICP_NN_GRID, 0)
+    assert (p.T, p.m, p.nn_mode, p.prior, p.surrogate_iters) == (100, 100, S.SICP_NN_GRID, 0, 0)
+    assert p.surrogate_min_conf == 0.5
     assert abs(p.lr - 0.01) < 1e-9 and abs(p.beta2 - 0.999) < 1e-7
     assert ctypes.sizeof(S.sicp_params) == 96
