@@ -54,7 +54,8 @@ extern "C" {
 
 /* Nearest-neighbour search used for step 3. */
 #define SICP_NN_BRUTE_FP32 0    /* exhaustive FP32 scan of the whole reference */
-#define SICP_NN_BRUTE_BF16 1    /* exhaustive BF16 tensor-core distance tiles + exact FP32 refine */
+#define SICP_NN_BRUTE_BF16 1    /* exhaustive, BF16 tensor-core distance tiles + exact FP32 re-check;
+                                   same results as SICP_NN_BRUTE_FP32 */
 #define SICP_NN_GRID 2          /* uniform voxel grid, exact */
 #define SICP_NN_SURROGATE 3     /* learned closest-point field, then exact grid */
 
@@ -166,8 +167,12 @@ int sicp_minibatch(sicp_ctx* ctx, uint64_t seed, int64_t t0, int32_t T, int64_t 
 /* Step 3 (Eq. correspondences): nearest reference point of each query
  * q [n][3] (float32) by search `mode` (SICP_NN_BRUTE_FP32, _BRUTE_BF16 or
  * _GRID).  out_idx [n] int32 reference indices (ties: lowest index), out_d2
- * [n] float32 squared distances (may be NULL).  n = 0 is a no-op.
- * Errors: SICP_EINVAL, SICP_ENOREF, SICP_ECUDA. */
+ * [n] float32 squared distances (may be NULL).  All three modes return the
+ * minimiser of the same float32 squared distance |q - r|^2.  SICP_NN_BRUTE_BF16
+ * computes every query-point distance bound on the tensor cores from bf16
+ * splits of the coordinates (about 16 significant bits) and re-checks in
+ * float32 the points it cannot rule out.  n = 0 is a no-op.
+ * Errors: SICP_EINVAL, SICP_ENOREF, SICP_ECUDA, SICP_ETIMEOUT. */
 int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out_idx,
             float* out_d2, int on_device);
 
@@ -175,7 +180,8 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
  * [K][6] and one minibatch mb [m] of indices into src_xyz [N][3], the mean
  * gradient of L/2 per particle, out_gbar [K][6] float32, and optionally the
  * correspondences out_nn [K][m] int32 (may be NULL).  `mode` is
- * SICP_NN_BRUTE_FP32, SICP_NN_GRID or SICP_NN_SURROGATE; the last takes each
+ * SICP_NN_BRUTE_FP32, SICP_NN_BRUTE_BF16 (K * m <= 2^26), SICP_NN_GRID or
+ * SICP_NN_SURROGATE; the last takes each
  * correspondence from the trained surrogate (predicted nearest point
  * q + d) where its confidence is at least 0.5 and the query lies in the
  * trained cube, from the exact grid search otherwise, and needs

@@ -145,9 +145,7 @@ int read_flags(sicp_ctx* ctx, int* flags_host) {
 }
 
 int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
-    if (mode == SICP_NN_BRUTE_FP32 || mode == SICP_NN_GRID) return SICP_OK;
-    if (mode == SICP_NN_BRUTE_BF16)
-        return set_err(ctx, SICP_EINVAL, "nn_mode %d (BF16 tensor-core search) is not available in this build", mode);
+    if (mode == SICP_NN_BRUTE_FP32 || mode == SICP_NN_GRID || mode == SICP_NN_BRUTE_BF16) return SICP_OK;
     if (mode == SICP_NN_SURROGATE && allow_surrogate) {
         if (surrogate_ready(ctx)) return SICP_OK;
         return set_err(ctx, SICP_ENOSURROGATE, "no trained surrogate on this context");
@@ -286,7 +284,8 @@ int sicp_create(sicp_ctx** out, int device, void* cuda_stream) {
         c->own_stream = true;
     }
     c->graphs = new GraphCache();
-    if (kernel_attrs_init() != cudaSuccess || surrogate_kernel_attrs() != cudaSuccess) {
+    if (kernel_attrs_init() != cudaSuccess || surrogate_kernel_attrs() != cudaSuccess ||
+        bf16_kernel_attrs() != cudaSuccess) {
         cudaGetLastError();
         sicp_destroy(c);
         return SICP_ECUDA;
@@ -311,7 +310,8 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->batch) batch_destroy(c->batch);
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
-                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done};
+                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done,
+                   &c->bf16_tiles};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -351,6 +351,7 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
     }
     ctx->M = 0;
     surrogate_invalidate(ctx);   // a surrogate belongs to the reference it was trained on
+    ctx->bf16_ready = false;
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_xyz, M, ctx->ref4, (int*)ctx->flags.p, ctx->stream));
     int flags[4];
@@ -414,14 +415,19 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
     }
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     if (on_device) SICP_CUDA(launch_check_finite((const float*)d_q, 3 * n, (int*)ctx->flags.p, ctx->stream));
-    if (mode == SICP_NN_GRID)
+    if (mode == SICP_NN_GRID) {
         SICP_CUDA(launch_nn_grid(ctx->search, (const float*)d_q, n, d_idx, d_d2, stats_ptr(ctx), ctx->stream));
-    else
+    } else if (mode == SICP_NN_BRUTE_BF16) {
+        if ((rc = bf16_prepare(ctx))) return rc;
+        SICP_CUDA(launch_nn_bf16(ctx, (const float*)d_q, n, d_idx, d_d2, (int*)ctx->flags.p + 3));
+    } else {
         SICP_CUDA(launch_nn_brute(ctx->ref4, ctx->M, (const float*)d_q, n, d_idx, d_d2, ctx->stream));
+    }
     int flags[4];
     rc = read_flags(ctx, flags);
     if (rc) return rc;
     if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite query");
+    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded wait of the tensor-core search gave up");
     if (!on_device) {
         if ((rc = copy_out(ctx, out_idx, d_idx, sizeof(int32_t) * n, 0))) return rc;
         if (out_d2 && (rc = copy_out(ctx, out_d2, d_d2, sizeof(float) * n, 0))) return rc;
@@ -466,10 +472,15 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
         d_mb = aux + b_src;
         d_th = aux + b_src + b_mb;
     }
+    const bool bf = mode == SICP_NN_BRUTE_BF16;
+    if (bf && (int64_t)K * m > ((int64_t)1 << 26))
+        return set_err(ctx, SICP_EINVAL, "the tensor-core search needs K * m <= 2^26");
     const int chunks = (mode == SICP_NN_BRUTE_FP32 ? grad_layout(m) : grad_layout_grid(m)).chunks;
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
-    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)(surr && m > chunks ? m : chunks) * K))) return rc;
+    if ((rc = ensure(ctx, ctx->partial, sizeof(float) * 6 * (size_t)((surr || bf) && m > chunks ? m : chunks) * K)))
+        return rc;
     if (surr && (rc = surrogate_prepare(ctx, (int64_t)K * m))) return rc;
+    if (bf && (rc = bf16_prepare(ctx))) return rc;
     if ((rc = ensure(ctx, ctx->tmp_out, (sizeof(float) * 6 + sizeof(int32_t) * (size_t)m) * K))) return rc;
     float* d_g = (float*)ctx->tmp_out.p;
     int32_t* d_nn = (int32_t*)((char*)ctx->tmp_out.p + sizeof(float) * 6 * K);
@@ -498,6 +509,9 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     if (surr) {
         SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, m, g.theta, K, kSurrogateIcpGradConf, (float*)ctx->partial.p,
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
+    } else if (bf) {
+        SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, m, g.theta, K, (float*)ctx->partial.p, d_g, out_nn ? d_nn : nullptr,
+                                   (int*)ctx->flags.p + 3));
     } else {
         SICP_CUDA(launch_grad(ctx, mode, g));
         if (mode != SICP_NN_GRID)
@@ -505,9 +519,9 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     }
     if ((rc = copy_out(ctx, out_gbar, d_g, sizeof(float) * 6 * K, on_device))) return rc;
     if (out_nn && (rc = copy_out(ctx, out_nn, d_nn, sizeof(int32_t) * (size_t)m * K, on_device))) return rc;
-    if (surr) {
+    if (surr || bf) {
         if ((rc = read_flags(ctx, flags))) return rc;
-        if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a tensor-core wait of the surrogate gave up");
+        if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded tensor-core wait gave up");
     }
     return sync(ctx);
 }
@@ -590,13 +604,16 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     const bool surr = p.nn_mode == SICP_NN_SURROGATE;
     if (surr && (int64_t)K * p.m > ((int64_t)1 << 24))
         return set_err(ctx, SICP_EINVAL, "surrogate mode needs K * m <= 2^24 queries per iteration");
+    const bool bf = p.nn_mode == SICP_NN_BRUTE_BF16;
+    if (bf && (int64_t)K * p.m > ((int64_t)1 << 26))
+        return set_err(ctx, SICP_EINVAL, "the tensor-core search needs K * m <= 2^26");
     const bool grid = p.nn_mode == SICP_NN_GRID || surr;   // the surrogate's exact iterations use the grid
     const int32_t exact_mode = surr ? SICP_NN_GRID : p.nn_mode;
     const int chunks = (grid ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
     const int32_t surr_T = surr ? (p.surrogate_iters < p.T ? p.surrogate_iters : p.T) : 0;
     const size_t b_th = sizeof(float) * 6 * K;
     // partial sums of the exhaustive kernel, or the surrogate's per-query terms
-    const size_t partial_floats = 6 * (size_t)K * (size_t)(surr_T > 0 && p.m > chunks ? p.m : chunks);
+    const size_t partial_floats = 6 * (size_t)K * (size_t)((surr_T > 0 || bf) && p.m > chunks ? p.m : chunks);
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
     if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m))) return rc;
     if ((rc = ensure(ctx, ctx->theta, b_th))) return rc;
@@ -607,6 +624,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if ((rc = ensure(ctx, ctx->gbar, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
+    if (bf && (rc = bf16_prepare(ctx))) return rc;
 
     const void *d_src, *d_th0;
     if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
@@ -685,11 +703,14 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
                 SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, p.m, theta, K, p.surrogate_min_conf,
                                                 (float*)ctx->partial.p, (float*)ctx->gbar.p, g.stats,
                                                 (int*)ctx->flags.p + 3));
+            else if (bf)
+                SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, p.m, theta, K, (float*)ctx->partial.p, (float*)ctx->gbar.p,
+                                           nullptr, (int*)ctx->flags.p + 3));
             else
                 SICP_CUDA(launch_grad(ctx, exact_mode, g));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
             // the grid kernel and the surrogate path leave gbar; the exhaustive kernel leaves `chunks` partials
-            SteinArgs a = grid ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
+            SteinArgs a = (grid || bf) ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
                                             (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t + 1)
                                : stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
                                             (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
@@ -741,7 +762,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     int flags[4];
     if ((rc = read_flags(ctx, flags))) return rc;
     if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
-    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a tensor-core wait of the surrogate gave up");
+    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded tensor-core wait gave up");
     if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
     if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
     if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;

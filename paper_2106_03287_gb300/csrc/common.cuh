@@ -174,6 +174,10 @@ struct sicp_ctx {
     double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
     sicp::GraphCache* graphs = nullptr;
     sicp::BatchState* batch = nullptr;   // state of the batched path, created on first use
+    sicp::Buf bf16_tiles;                // reference tiles of the tensor-core exhaustive search
+    bool bf16_ready = false;             // bf16_tiles hold the current reference
+    float3 bf16_centre = {0, 0, 0};
+    int bf16_R = 0;                      // reference tiles of 256 points
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
 };
@@ -200,6 +204,10 @@ cudaError_t launch_check_index(const int32_t* idx, int64_t n, int64_t N, int* fl
 // gbar[j][c] = inv_m * sum over chunks of partial[chunk][j][c]
 cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, float inv_m, float* gbar,
                                    cudaStream_t s);
+// gbar[j][c] = inv_m * sum over k of qterms[j][k][c] ([K][m][6], fixed order); also zeroes
+// *fb_count when it is not null
+cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
+                                  cudaStream_t s);
 // ordered-uint bounding box of float4 points into lohi[6] (min xyz, max xyz), pre-initialised
 cudaError_t launch_bbox(const float4* p, int64_t n, unsigned* lohi, cudaStream_t s);
 float ordered_to_float(unsigned u);
@@ -278,6 +286,16 @@ int surrogate_prepare(sicp_ctx* ctx, int64_t queries);
 cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta,
                                   int K, float min_conf, float* qterms, float* gbar, unsigned long long* stats,
                                   int* err);
+
+// Exhaustive search with tensor-core distance tiles and an exact fp32 re-check
+// (k_nn_bf16.cu); same results as launch_nn_brute / the fp32 gradient.
+cudaError_t bf16_kernel_attrs();
+int bf16_prepare(sicp_ctx* ctx);   // reference tiles of the current reference (needs the grid)
+// err: set when a bounded wait gave up
+cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* idx, float* d2, int* err);
+// per-query gradient terms into qterms [K][m][6], then gbar [K][6]; out_nn [K][m] or null
+cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
+                             float* qterms, float* gbar, int32_t* out_nn, int* err);
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);

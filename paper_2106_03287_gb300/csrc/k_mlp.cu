@@ -746,30 +746,6 @@ __global__ void __launch_bounds__(128, 8) k_grad_fallback(FallbackArgs a) {
     if (a.stats) add_stats(a.stats, w);
 }
 
-// gbar[j] = inv_m * (sum over k of qterms[j][k]) in a fixed order: one warp per
-// particle, lanes over the minibatch, then a fixed butterfly.  Clears the
-// fallback count for the next iteration.
-__global__ void k_qterms_to_gbar(const float* __restrict__ qterms, int K, int m, float inv_m, float* __restrict__ gbar,
-                                 int* fb_count) {
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && fb_count) *fb_count = 0;
-    if (j >= K) return;
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float* row = qterms + (int64_t)j * m * 6;
-    for (int k = lane; k < m; k += 32)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += __ldg(row + 6 * k + c);
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-        for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-    if (lane < 6) {
-        float v = acc[0];
-#pragma unroll
-        for (int c = 1; c < 6; ++c) v = lane == c ? acc[c] : v;
-        gbar[6 * j + lane] = v * inv_m;
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -938,8 +914,7 @@ cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_
     f.stats = stats;
     k_grad_fallback<<<(unsigned)(ctx->num_sms * 8), 128, 0, ctx->stream>>>(f);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_qterms_to_gbar<<<(K + 7) / 8, 256, 0, ctx->stream>>>(qterms, K, m, 1.f / (float)m, gbar, fb_count);
-    return cudaGetLastError();
+    return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, fb_count, ctx->stream);
 }
 
 }  // namespace sicp

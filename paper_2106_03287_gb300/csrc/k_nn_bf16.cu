@@ -1,0 +1,488 @@
+// Exhaustive nearest-neighbour search with the distance tiles on the
+// fifth-generation tensor cores (bf16 operands, fp32 accumulation in tensor
+// memory) and an exact fp32 re-check of the few candidates they cannot rule
+// out.  The result is the same (index, squared distance) as the fp32
+// exhaustive search: the lowest-index minimiser of the fp32 squared distance.
+//
+// Distances.  With c the centre of the reference bounding box, q' = q - c and
+// r' = r - c, the squared distance is |q'|^2 + d~(q, r) with
+//   d~(q, r) = |r'|^2 - 2 q'.r'.
+// |q'|^2 does not depend on r, so the nearest r minimises d~.  Each fp32
+// coordinate is split into two bf16 parts, x = x_h + x_l + O(2^-16 |x|); the
+// product q'.r' is taken as q_h.r_h + q_l.r_h + q_h.r_l (the dropped q_l.r_l
+// is O(2^-16)).  The 9 products and the two bf16 parts of |r'|^2 fill 11 of
+// the 16 K slots of one MMA, so one M = 128 x N = 256 x K = 16 MMA gives, for
+// 128 queries and 256 reference points, v ~ d~(q, r) with
+//   |v - d~(q, r)| <= E(q, t) = a |q'| N_t + b N_t^2 + e |q'|^2,
+// N_t the largest |r'| of reference tile t.  E bounds, with a factor of two to
+// spare, every rounding between the bf16 products and the exact fp32 squared
+// distance that the fp32 search compares: the splits (2^-16 per product), the
+// fp32 accumulation, and the fp32 evaluation of |q - r|^2.
+//
+// Search (one sweep).  Per query, u = the smallest upper bound v + E seen so
+// far bounds the minimum of d~ from above at every moment, so a point whose
+// lower bound v - E exceeds the current u cannot be the fp32 minimiser (nor
+// tie with it); every other point is a candidate and gets its exact fp32
+// squared distance; the best candidate under the (distance, index) order is
+// the answer.  Per element of a tile the work is one min; the candidates
+// (points within a few bound widths of the best so far) are rare once u has
+// come down.
+//
+// Pipeline per CTA (one 128-query tile at a time, persistent over tiles, one
+// CTA per SM; the sweep starts at the reference tile holding the grid cell of
+// the tile's first query and wraps around): the 16 warps copy each reference tile (8 KB, precomputed per
+// reference cloud in the spatially sorted order of the voxel grid) and its 256
+// fp32 points into a shared-memory ring with asynchronous 16-byte copies,
+// three tiles ahead; thread 0 issues a landed tile's MMA into one of two
+// 256-column tensor-memory buffers while the warps read the other (four warps
+// per 32 rows, one per column quarter).  The only wait, on MMA completion, is
+// bounded.
+#include <cuda_bf16.h>
+#include <float.h>
+
+#include "common.cuh"
+#include "grid_search.cuh"
+#include "tc.cuh"
+
+namespace sicp {
+namespace {
+
+using gs::cell_coord;
+
+constexpr int kQRows = 128;
+constexpr int kRCols = 256;
+constexpr int kKDim = 16;
+constexpr int kTileBytes = kRCols * kKDim * 2;        // one reference tile
+constexpr int kSlotBytes = kTileBytes + kRCols * 16;  // a tile and its 256 fp32 points
+constexpr int kSlots = 5;                             // tile t in slot t % kSlots
+constexpr int kAhead = 3;                             // tiles whose copies are in flight ahead of the MMA
+constexpr int kWarps = 16;                            // 4 row groups x 4 column quarters
+constexpr int kQuarter = kRCols / 4;
+constexpr int kBfThreads = kWarps * 32;
+constexpr long long kPolls = 1ll << 24;
+// error-bound coefficients (see the header comment): a, b, e
+constexpr float kEpsQR = 2.2e-4f, kEpsRR = 3.6e-5f, kEpsQQ = 1.2e-6f;
+constexpr float kPadW = 1e30f;                        // |r'|^2 of the padding columns of the last tile
+constexpr unsigned kNoIdx = 0x7fffffffu;
+
+constexpr int sA = 0;                                 // 128 x 16 bf16, K-major
+constexpr int sRing = sA + kQRows * kKDim * 2;        // kSlots x kSlotBytes
+constexpr int sQ = sRing + kSlots * kSlotBytes;       // float4 per row
+constexpr int sXD = sQ + kQRows * 16;                 // quarters 1..3: best distance, index, point
+constexpr int sXI = sXD + 3 * kQRows * 4;
+constexpr int sXP = sXI + 3 * kQRows * 4;
+constexpr int kBfSmemUsed = sXP + 3 * kQRows * 16;
+// Launched with more shared memory than it uses so that no two CTAs share an
+// SM: each holds all 512 tensor-memory columns for its whole life.
+constexpr int kBfSmem = 120 * 1024;
+static_assert(kBfSmemUsed <= kBfSmem, "layout exceeds the launch size");
+static_assert(kTileBytes == 16 * kBfThreads && kRCols <= kBfThreads, "one 16-byte copy per thread and tile");
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void store_row16(unsigned char* tile, int row, const __nv_bfloat16 v[16]) {
+    uint4 lo, hi;
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(v);
+    lo.x = p[0]; lo.y = p[1]; lo.z = p[2]; lo.w = p[3];
+    hi.x = p[4]; hi.y = p[5]; hi.z = p[6]; hi.w = p[7];
+    *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(row, 0, kKDim)) = lo;
+    *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(row, 8, kKDim)) = hi;
+}
+
+// The B operand of every reference tile (tile t at out + t * kTileBytes) from
+// the grid's sorted points, and N_t = the largest |r'| of each tile (nmax,
+// zeroed beforehand; non-negative floats order like their bit patterns).
+__global__ void k_bf16_btiles(const float4* __restrict__ sorted, int M, float3 c, int R,
+                              unsigned char* __restrict__ out, unsigned* __restrict__ nmax) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)R * kRCols) return;
+    const int tile = (int)(i / kRCols), row = (int)(i % kRCols);
+    __nv_bfloat16 v[16];
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int k = 0; k < 16; ++k) v[k] = z;
+    if (i < M) {
+        const float4 r = sorted[i];
+        const float p[3] = {r.x - c.x, r.y - c.y, r.z - c.z};
+        const float n2 = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
+        for (int a = 0; a < 3; ++a) {
+            __nv_bfloat16 h, l;
+            split_bf16(p[a], h, l);
+            v[a] = h;
+            v[3 + a] = h;
+            v[6 + a] = l;
+        }
+        split_bf16(n2, v[9], v[10]);
+        atomicMax(nmax + tile, __float_as_uint(sqrtf(n2)));
+    } else {
+        v[9] = __float2bfloat16_rn(kPadW);
+    }
+    store_row16(out + (size_t)tile * kTileBytes, row, v);
+}
+
+struct BfArgs {
+    int grad;                  // 0: queries given; 1: queries R_j s_k + u_j of a registration iteration
+    const float* q;            // grad = 0: [n][3]
+    int64_t n;
+    const float4* src;         // grad = 1
+    const int32_t* mb;
+    int m;
+    const float* theta;
+    int K;
+    float3 c;
+    const unsigned char* btiles;
+    const float* nmax;         // [R]
+    const float4* sorted;
+    GridView grid;             // the fine grid: where each cell's points start in `sorted`
+    int M, R;
+    int32_t* out_idx;          // grad = 0: [n]; grad = 1: [K][m] or null
+    float* out_d2;             // grad = 0
+    float* qterms;             // grad = 1: [K][m][6]
+    int* err;
+};
+
+// Wait for phase `parity` of the mbarrier; false (and the error flag set)
+// after kPolls polls.
+__device__ __forceinline__ bool bwait(uint64_t* mb, uint32_t parity, int* err) {
+    if (tc::mbar_wait(mb, parity, kPolls)) return true;
+    atomicOr(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t r[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Minimum of 64 accumulator values (a tree, for instruction-level parallelism).
+__device__ __forceinline__ float min64(const uint32_t r[64]) {
+    float t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        t[i] = fminf(fminf(__uint_as_float(r[i]), __uint_as_float(r[i + 16])),
+                     fminf(__uint_as_float(r[i + 32]), __uint_as_float(r[i + 48])));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; ++i) t[i] = fminf(t[i], t[i + w]);
+    return t[0];
+}
+
+// Reference tile swept at step t (all R tiles, from `rot` on).
+__device__ __forceinline__ int ref_tile(int t, int R, int rot) {
+    const int r = t + rot;
+    return r >= R ? r - R : r;
+}
+
+__device__ __forceinline__ bool better_u(float d, unsigned i, float bd, unsigned bi) {
+    return d < bd || (d == bd && i < bi);
+}
+
+__global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t tfull[2];
+    __shared__ uint32_t tbase;
+    __shared__ int s_fail, s_rot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int64_t Q = a.grad ? (int64_t)a.K * a.m : a.n;
+    const int64_t ntiles = (Q + kQRows - 1) / kQRows;
+    const int T = a.R;
+    float4* qrow = reinterpret_cast<float4*>(sm + sQ);
+    float* xd = reinterpret_cast<float*>(sm + sXD);
+    unsigned* xi = reinterpret_cast<unsigned*>(sm + sXI);
+    float4* xp = reinterpret_cast<float4*>(sm + sXP);
+
+    if (warp == 0) tc::tmem_alloc(&tbase, 512);
+    if (tid == 0) {
+        tc::mbar_init(&tfull[0], 1);
+        tc::mbar_init(&tfull[1], 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = tc::idesc_bf16(kQRows, kRCols);
+    const uint64_t adesc = tc::smem_desc(tc::smem_u32(sm + sA), 128, kKDim * 16, false);
+    int rot = 0;
+    const int qtr = warp >> 2, rq = warp & 3, row = 32 * rq + lane;
+    int64_t N0 = 0;   // MMAs issued by this CTA before the current query tile
+
+    // asynchronous copy (no registers) of this thread's 16 bytes of tile t
+    // and of its points; one commit group per tile
+    auto fetch = [&](int t) {
+        if (t < T) {
+            const int rt = ref_tile(t, a.R, rot);
+            unsigned char* slot = sm + sRing + (t % kSlots) * kSlotBytes;
+            cp_async16(slot + 16 * tid, a.btiles + (size_t)rt * kTileBytes + 16 * tid);
+            if (tid < kRCols && rt * kRCols + tid < a.M)
+                cp_async16(slot + kTileBytes + 16 * tid, a.sorted + (size_t)rt * kRCols + tid);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // publish tile t's slot and, from thread 0, issue its MMA
+    auto issue_mma = [&](int t) {
+        tc::fence_async_shared();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0 && !s_fail) {
+            const int64_t N = N0 + t;
+            const uint64_t bdesc =
+                tc::smem_desc(tc::smem_u32(sm + sRing + (t % kSlots) * kSlotBytes), 128, kKDim * 16, false);
+            tc::mma_bf16(tmem + (uint32_t)((N & 1) * kRCols), adesc, bdesc, idesc, false);
+            tc::mma_commit(&tfull[N & 1]);
+        }
+    };
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // ---- A operand and the fp32 queries of this tile.  In a registration
+        // iteration the rows go minibatch-major (the K particles' images of one
+        // source point are neighbours), which keeps a tile's queries close.
+        if (tid < kQRows) {
+            const int64_t g = tile * kQRows + tid;
+            float3 q = make_float3(0.f, 0.f, 0.f);
+            if (g < Q) {
+                if (a.grad) {
+                    const int k = (int)(g / a.K), j = (int)(g % a.K);
+                    Pose P;
+                    make_pose(a.theta + 6 * j, P);
+                    const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+                    q = apply_pose(P, make_float3(s4.x, s4.y, s4.z));
+                } else {
+                    q = make_float3(a.q[3 * g], a.q[3 * g + 1], a.q[3 * g + 2]);
+                }
+            }
+            const float p[3] = {q.x - a.c.x, q.y - a.c.y, q.z - a.c.z};
+            const float n2 = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
+            qrow[tid] = make_float4(q.x, q.y, q.z, sqrtf(n2));
+            __nv_bfloat16 v[16];
+            const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+            for (int k = 0; k < 16; ++k) v[k] = z;
+            for (int d = 0; d < 3; ++d) {
+                __nv_bfloat16 h, l;
+                split_bf16(-2.f * p[d], h, l);     // exact scaling by -2
+                v[d] = h;
+                v[3 + d] = l;
+                v[6 + d] = h;
+            }
+            v[9] = v[10] = __float2bfloat16_rn(1.f);
+            store_row16(sm + sA, tid, v);
+            if (tid == 0) {
+                // the sweep starts at the reference tile that holds the grid cell of the
+                // tile's first query (the points around it come early and bring u down)
+                const GridView& G = a.grid;
+                const int cx = cell_coord(q.x, G.origin.x, G.inv_cell, G.dims.x);
+                const int cy = cell_coord(q.y, G.origin.y, G.inv_cell, G.dims.y);
+                const int cz = cell_coord(q.z, G.origin.z, G.inv_cell, G.dims.z);
+                const int32_t start = __ldg(G.cell_start + ((int64_t)cz * G.dims.y + cy) * G.dims.x + cx);
+                s_rot = min(start / kRCols, a.R - 1);
+            }
+        }
+        __syncthreads();
+        rot = s_rot;
+        // ---- prologue: tiles 0 .. kAhead in flight, tile 0 landed and its MMA issued
+        for (int t = 0; t <= kAhead; ++t) fetch(t);
+        asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
+        issue_mma(0);
+        const float4 q4 = qrow[row];
+        const float3 q = make_float3(q4.x, q4.y, q4.z);
+        const float qn = q4.w;
+        // the per-row part of the bound: E = aq N + b N^2 + eq
+        const float aq = kEpsQR * qn, eq = kEpsQQ * qn * qn;
+        float u = FLT_MAX, bd = FLT_MAX;
+        unsigned bi = kNoIdx;
+        float4 bp = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        for (int t = 0; t < T; ++t) {
+            // tile t + 1 has landed (the kAhead - 1 newer groups may still be in
+            // flight); its slot is published and its MMA issued
+            if (t + 1 < T) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory");
+                issue_mma(t + 1);
+            }
+            // the slot of tile t + 1 + kAhead last held tile t + 1 + kAhead - kSlots = t - 1,
+            // consumed before the barrier above
+            fetch(t + 1 + kAhead);
+
+            // ---- accumulators of tile t: warp w reads rows 32 (w % 4) .. + 31, columns of quarter w / 4
+            const int64_t N = N0 + t;
+            const int b = (int)(N & 1);
+            int ok = 1;
+            if (lane == 0) ok = s_fail ? 0 : bwait(&tfull[b], (uint32_t)((N >> 1) & 1), a.err);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            tc::fence_after_sync();
+            if (!ok) {
+                if (lane == 0) s_fail = 1;
+                continue;
+            }
+            const uint32_t tb = tmem + (uint32_t)(b * kRCols + qtr * kQuarter) + ((uint32_t)(32 * rq) << 16);
+            uint32_t r[64];
+            tmem_ld16_nw(tb, r);
+            tmem_ld16_nw(tb + 16, r + 16);
+            tmem_ld16_nw(tb + 32, r + 32);
+            tmem_ld16_nw(tb + 48, r + 48);
+            tmem_wait_ld();
+            const int rt = ref_tile(t, a.R, rot);
+            const float nt = __ldg(a.nmax + rt);
+            const float E = fmaf(aq, nt, fmaf(kEpsRR * nt, nt, eq));
+            const float cm = min64(r);
+            u = fminf(u, cm + E);
+            const float thr = u + E;   // lower bound v - E <= u
+            if (cm <= thr) {
+                const int col0 = qtr * kQuarter;
+                const float4* pts =
+                    reinterpret_cast<const float4*>(sm + sRing + (t % kSlots) * kSlotBytes + kTileBytes);
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    if (__uint_as_float(r[j]) <= thr && rt * kRCols + col0 + j < a.M) {
+                        const float4 r4 = pts[col0 + j];
+                        const float d = dist2(r4, q);
+                        const unsigned id = __float_as_uint(r4.w);
+                        if (better_u(d, id, bd, bi)) {
+                            bd = d;
+                            bi = id;
+                            bp = r4;
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+
+        // the four column quarters of each row: the best answer wins
+        if (qtr > 0) {
+            xd[(qtr - 1) * kQRows + row] = bd;
+            xi[(qtr - 1) * kQRows + row] = bi;
+            xp[(qtr - 1) * kQRows + row] = bp;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (qtr == 0) {
+            for (int o = 0; o < 3; ++o) {
+                if (better_u(xd[o * kQRows + row], xi[o * kQRows + row], bd, bi)) {
+                    bd = xd[o * kQRows + row];
+                    bi = xi[o * kQRows + row];
+                    bp = xp[o * kQRows + row];
+                }
+            }
+            const int64_t g = tile * kQRows + row;
+            const bool found = !s_fail && bi != kNoIdx;
+            if (g < Q) {
+                if (a.grad) {
+                    const int k = (int)(g / a.K), j = (int)(g % a.K);
+                    const int64_t o = (int64_t)j * a.m + k;      // [K][m] layout of the outputs
+                    float t6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (found) {
+                        Pose P;
+                        make_pose(a.theta + 6 * j, P);
+                        const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+                        grad_terms(P, make_float3(s4.x, s4.y, s4.z), make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z),
+                                   t6);
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < 6; ++cc) a.qterms[o * 6 + cc] = t6[cc];
+                    if (a.out_idx) a.out_idx[o] = found ? (int32_t)bi : -1;
+                } else {
+                    a.out_idx[g] = found ? (int32_t)bi : -1;
+                    if (a.out_d2) a.out_d2[g] = found ? bd : FLT_MAX;
+                }
+            }
+        }
+        N0 += T;
+        __syncthreads();
+        if (s_fail) break;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+cudaError_t bf16_kernel_attrs() {
+    return cudaFuncSetAttribute(k_nn_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kBfSmem);
+}
+
+// The reference tiles of the current reference cloud (built on first use):
+// R tiles of kTileBytes, then the R tile radii N_t.
+int bf16_prepare(sicp_ctx* ctx) {
+    if (ctx->bf16_ready) return SICP_OK;
+    const int R = (int)((ctx->M + kRCols - 1) / kRCols);
+    const size_t tiles_bytes = (size_t)R * kTileBytes;
+    int rc = ensure(ctx, ctx->bf16_tiles, tiles_bytes + sizeof(float) * (size_t)R);
+    if (rc) return rc;
+    const float3 c = make_float3(0.5f * (ctx->ref_lo.x + ctx->ref_hi.x), 0.5f * (ctx->ref_lo.y + ctx->ref_hi.y),
+                                 0.5f * (ctx->ref_lo.z + ctx->ref_hi.z));
+    unsigned* nmax = (unsigned*)((char*)ctx->bf16_tiles.p + tiles_bytes);
+    SICP_CUDA(cudaMemsetAsync(nmax, 0, sizeof(float) * (size_t)R, ctx->stream));
+    const int64_t rows = (int64_t)R * kRCols;
+    k_bf16_btiles<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->grid.v.sorted, (int)ctx->M, c, R, (unsigned char*)ctx->bf16_tiles.p, nmax);
+    SICP_CUDA(cudaGetLastError());
+    ctx->bf16_centre = c;
+    ctx->bf16_R = R;
+    ctx->bf16_ready = true;
+    return SICP_OK;
+}
+
+static BfArgs bf_args(sicp_ctx* ctx, int* err) {
+    BfArgs a{};
+    a.c = ctx->bf16_centre;
+    a.btiles = (const unsigned char*)ctx->bf16_tiles.p;
+    a.nmax = (const float*)((const char*)ctx->bf16_tiles.p + (size_t)ctx->bf16_R * kTileBytes);
+    a.sorted = ctx->grid.v.sorted;
+    a.grid = ctx->grid.v;
+    a.M = (int)ctx->M;
+    a.R = ctx->bf16_R;
+    a.err = err;
+    return a;
+}
+
+static unsigned bf_grid(sicp_ctx* ctx, int64_t Q) {
+    const int64_t tiles = (Q + kQRows - 1) / kQRows;
+    return (unsigned)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
+}
+
+cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* idx, float* d2, int* err) {
+    BfArgs a = bf_args(ctx, err);
+    a.grad = 0;
+    a.q = q;
+    a.n = n;
+    a.out_idx = idx;
+    a.out_d2 = d2;
+    k_nn_bf16<<<bf_grid(ctx, n), kBfThreads, kBfSmem, ctx->stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
+                             float* qterms, float* gbar, int32_t* out_nn, int* err) {
+    BfArgs a = bf_args(ctx, err);
+    a.grad = 1;
+    a.src = src;
+    a.mb = mb;
+    a.m = m;
+    a.theta = theta;
+    a.K = K;
+    a.qterms = qterms;
+    a.out_idx = out_nn;
+    k_nn_bf16<<<bf_grid(ctx, (int64_t)K * m), kBfThreads, kBfSmem, ctx->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, nullptr, ctx->stream);
+}
+
+}  // namespace sicp

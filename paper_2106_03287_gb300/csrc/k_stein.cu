@@ -1,5 +1,7 @@
-// Stein update + Adam, fused in one CTA (Eq. stein_icp_phi, the RBF kernels
-// that follow it, and Sec. V), plus the FP64 particle moments.
+// Stein update + Adam (Eq. stein_icp_phi, the RBF kernels that follow it, and
+// Sec. V), plus the FP64 particle moments.  The translation and rotation
+// blocks are independent (own kernel, bandwidth, gradient and Adam
+// components), so the update runs as two CTAs of 1024 threads, one per block.
 //
 // Per iteration, for K particles theta_j with mean ICP gradients gbar_j:
 //   G_j   = -N gbar_j + grad log prior(theta_j)          (Eq. posterior)
@@ -24,7 +26,8 @@ namespace {
 
 using namespace sd;
 
-__global__ void __launch_bounds__(kThreads) k_stein_adam(SteinArgs a) { stein_adam_block(a); }
+// CTA b updates block b (translation, rotation) of every particle.
+__global__ void __launch_bounds__(kThreads) k_stein_adam(SteinArgs a) { stein_adam_one_block(a, blockIdx.x); }
 
 __global__ void k_moments(const float* __restrict__ th, int K, double* __restrict__ out) {
     __shared__ double mean[6];
@@ -52,8 +55,8 @@ cudaError_t kernel_attrs_init() {
 
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s) {
     const size_t pairs = (size_t)a.K * (a.K - 1) / 2;
-    const size_t smem = sizeof(float) * (18 * (size_t)a.K + (2 * pairs <= (size_t)kCacheFloats ? 2 * pairs : 0));
-    k_stein_adam<<<1, kThreads, smem, s>>>(a);
+    const size_t smem = sizeof(float) * (18 * (size_t)a.K + (pairs <= (size_t)kCacheFloats ? pairs : 0));
+    k_stein_adam<<<2, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -152,6 +152,30 @@ unsigned grid_1d(int64_t n, int threads, int cap = 4096) {
     return (unsigned)b;
 }
 
+// gbar[j] = inv_m * (sum over k of qterms[j][k]) in a fixed order: one warp per
+// particle, lanes over the minibatch, then a fixed butterfly.  Clears the
+// fallback count for the next iteration.
+__global__ void k_qterms_to_gbar(const float* __restrict__ qterms, int K, int m, float inv_m, float* __restrict__ gbar,
+                                 int* fb_count) {
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && fb_count) *fb_count = 0;
+    if (j >= K) return;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float* row = qterms + (int64_t)j * m * 6;
+    for (int k = lane; k < m; k += 32)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += __ldg(row + 6 * k + c);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (lane < 6) {
+        float v = acc[0];
+#pragma unroll
+        for (int c = 1; c < 6; ++c) v = lane == c ? acc[c] : v;
+        gbar[6 * j + lane] = v * inv_m;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* flags, cudaStream_t s) {
@@ -172,6 +196,12 @@ cudaError_t launch_check_index(const int32_t* idx, int64_t n, int64_t N, int* fl
 cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, float inv_m, float* gbar,
                                    cudaStream_t s) {
     k_partial_to_gbar<<<(6 * K + 255) / 256, 256, 0, s>>>(partial, chunks, K, inv_m, gbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
+                                  cudaStream_t s) {
+    k_qterms_to_gbar<<<(K + 7) / 8, 256, 0, s>>>(qterms, K, m, inv_m, gbar, fb_count);
     return cudaGetLastError();
 }
 

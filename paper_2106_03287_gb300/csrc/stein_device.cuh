@@ -298,6 +298,109 @@ __device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
     }
 }
 
+// The same update for one block only (b = 0: translation x, y, z; b = 1:
+// rotation), by the whole CTA: the two blocks share nothing (each has its own
+// kernel, bandwidth, gradient components and Adam components), so two CTAs
+// can take them on two SMs.  Same arithmetic and summation order as
+// stein_adam_block, so the results are bit-identical.
+__device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) {
+    extern __shared__ float sm[];
+    float* th = sm;               // K x 6 (all components: pair_d2 indexes the full rows)
+    float* G = sm + 6 * a.K;      // K x 6, columns 3b..3b+2 used
+    float* Ph = sm + 12 * a.K;    // K x 6, columns 3b..3b+2 used
+    float* D = sm + 18 * a.K;     // unique pair distances of block b when they fit
+    __shared__ unsigned hist[2048];
+    __shared__ unsigned s_u[4];
+    __shared__ unsigned wsum[32];
+    const int K = a.K, tid = threadIdx.x;
+    const int pairs = K * (K - 1) / 2;
+    const bool cached = pairs <= kCacheFloats;
+    const int c0 = 3 * b;
+
+    for (int idx = tid; idx < 6 * K; idx += blockDim.x) th[idx] = a.theta[idx];
+    if (a.chunks == 1) {
+        for (int e = tid; e < 3 * K; e += blockDim.x) {
+            const int j = e / 3, c = c0 + e % 3, idx = 6 * j + c;
+            const float x = a.theta[idx], gb = a.partial[idx];
+            float pr = 0.f;
+            if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
+            G[idx] = fmaf(-a.N, gb * a.inv_m, pr);
+        }
+    } else {
+        const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+        for (int e = warp; e < 3 * K; e += nwarps) {
+            const int j = e / 3, c = c0 + e % 3, idx = 6 * j + c;
+            float s = 0.f;
+            for (int ch = lane; ch < a.chunks; ch += 32) s += a.partial[((int64_t)ch * K + j) * 6 + c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) {
+                const float x = a.theta[idx];
+                float pr = 0.f;
+                if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
+                G[idx] = fmaf(-a.N, s * a.inv_m, pr);
+            }
+        }
+    }
+    __syncthreads();
+
+    const Team T = {0, (int)blockDim.x, 1};
+    const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum);
+    if (tid == 0 && a.out_h) a.out_h[b] = h;
+    const float inv_h = 1.f / h, two_h = 2.f / h;
+
+    int S = 32;
+    while (S > 1 && K * S > (int)blockDim.x) S >>= 1;
+    const int groups = blockDim.x / S;
+    const int g_id = tid / S, g_lane = tid % S;
+    const int rounds = (K + groups - 1) / groups;
+    const float invK = 1.f / (float)K;
+    const float omb1 = 1.f - a.beta1, omb2 = 1.f - a.beta2;
+    const float c1 = -expm1f((float)a.t * log1pf(-omb1));
+    const float c2 = -expm1f((float)a.t * log1pf(-omb2));
+    for (int r = 0; r < rounds; ++r) {
+        const int i = r * groups + g_id;
+        const bool valid = i < K;
+        float acc[3] = {0.f, 0.f, 0.f};
+        if (valid) {
+            const float* ti = th + 6 * i + c0;
+            for (int j = g_lane; j < K; j += S) {
+                const float* tj = th + 6 * j + c0;
+                const float* Gj = G + 6 * j + c0;
+                float d[3], Dd = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    d[c] = b ? wrapf(ti[c] - tj[c]) : ti[c] - tj[c];
+                    Dd = fmaf(d[c], d[c], Dd);
+                }
+                const float k = expf(-Dd * inv_h);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] += k * fmaf(two_h, d[c], Gj[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (int off = S >> 1; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off, S);
+        if (valid && g_lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ph[6 * i + c0 + c] = acc[c] * invK;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 3 * K; e += blockDim.x) {
+        const int idx = 6 * (e / 3) + c0 + e % 3;
+        const float phi = Ph[idx];
+        if (a.out_phi) a.out_phi[idx] = phi;
+        const float g = -phi;
+        const float mo = fmaf(a.beta1, a.adam_m[idx], omb1 * g);
+        const float ve = fmaf(a.beta2, a.adam_v[idx], omb2 * g * g);
+        a.adam_m[idx] = mo;
+        a.adam_v[idx] = ve;
+        const float mh = mo / c1, vh = ve / c2;
+        a.theta[idx] = th[idx] - a.lr * mh / (sqrtf(vh) + a.eps);
+    }
+}
+
 }  // namespace
 }  // namespace sd
 }  // namespace sicp
