@@ -219,6 +219,7 @@ SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, c
     }
     a.out_phi = nullptr;
     a.out_h = nullptr;
+    a.med_state = nullptr;
     return a;
 }
 
@@ -621,7 +622,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if ((rc = ensure(ctx, ctx->adam_v, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->partial, sizeof(float) * partial_floats))) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
-    if ((rc = ensure(ctx, ctx->gbar, b_th))) return rc;
+    if ((rc = ensure(ctx, ctx->gbar, b_th + 4 * sizeof(float)))) return rc;   // + the two blocks' medians
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
@@ -637,6 +638,8 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
+    float* med_state = (float*)ctx->gbar.p + 6 * (size_t)K;
+    SICP_CUDA(cudaMemsetAsync(med_state, 0, 2 * sizeof(float), ctx->stream));
 
     const int stride = ctx->prof_stride;
     LoopKey key;
@@ -714,6 +717,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
                                             (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t + 1)
                                : stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
                                             (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
+            a.med_state = med_state;
             SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;

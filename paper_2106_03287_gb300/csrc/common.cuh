@@ -265,6 +265,9 @@ struct SteinArgs {
     float mu[6], sigma[3], kappa[3];
     float* out_phi;        // K x 6 or null
     float* out_h;          // 2 or null
+    // the two blocks' medians of the previous iteration (in/out; 0: none) or
+    // null: starts the median selection next to the previous median
+    float* med_state;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);

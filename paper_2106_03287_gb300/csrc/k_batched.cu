@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
             }
             a.out_phi = nullptr;
             a.out_h = nullptr;
+            a.med_state = nullptr;
             sd::stein_adam_block(a);
             __syncthreads();
         }

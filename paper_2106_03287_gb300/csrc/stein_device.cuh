@@ -134,11 +134,68 @@ __device__ unsigned select_rank(const Team& T, const float* D, bool cached, cons
     return prefix;
 }
 
+constexpr int kBracketMax = 1024;   // values the warm start selects among
+
+// Warm start of the selection: the unique-pair distances of unique ranks
+// u[0], u[1] (cached in D, n of them) are looked for among the values within
+// 1/32 relative of m_prev, the previous iteration's median.  True, with the
+// two values in v[], when both ranks fall inside that bracket and it holds at
+// most kBracketMax values; the caller takes the full selection otherwise.
+// Exact either way: the values found are the same order statistics.
+__device__ bool bracket_select(const Team& T, const float* D, int n, const unsigned u[2], float m_prev, float* C,
+                               unsigned* s_u, float v[2]) {
+    const int lane = threadIdx.x & 31, lt = threadIdx.x - T.t0;
+    const float lo = m_prev * (1.f - 1.f / 32.f), hi = m_prev * (1.f + 1.f / 32.f);
+    if (lt == 0) {
+        s_u[0] = 0;   // values below the bracket
+        s_u[1] = 0;   // values inside it
+    }
+    team_sync(T);
+    for (int base = 0; base < n; base += T.n) {
+        const int p = base + lt;
+        const float x = p < n ? D[p] : FLT_MAX;
+        const unsigned below = __ballot_sync(0xffffffffu, p < n && x < lo);
+        const bool in = p < n && x >= lo && x <= hi;
+        const unsigned inm = __ballot_sync(0xffffffffu, in);
+        unsigned at = 0;
+        if (lane == 0) {
+            if (below) atomicAdd(&s_u[0], (unsigned)__popc(below));
+            if (inm) at = atomicAdd(&s_u[1], (unsigned)__popc(inm));
+        }
+        at = __shfl_sync(0xffffffffu, at, 0) + __popc(inm & ((1u << lane) - 1u));
+        if (in && at < (unsigned)kBracketMax) C[at] = x;
+    }
+    team_sync(T);
+    const unsigned c_lt = s_u[0], nc = s_u[1];
+    const bool ok = nc <= (unsigned)kBracketMax && u[0] >= c_lt && u[1] < c_lt + nc;
+    team_sync(T);
+    if (!ok) return false;
+    // rank of each bracketed value (ties by position: a permutation of 0 .. nc-1)
+    for (int i = lt; i < (int)nc; i += T.n) {
+        const float x = C[i];
+        unsigned r = c_lt;
+        for (int j = 0; j < (int)nc; ++j) {
+            const float y = C[j];
+            r += (y < x) || (y == x && j < i);
+        }
+        if (r == u[0]) s_u[2] = __float_as_uint(x);
+        if (r == u[1]) s_u[3] = __float_as_uint(x);
+    }
+    team_sync(T);
+    v[0] = __uint_as_float(s_u[2]);
+    v[1] = __uint_as_float(s_u[3]);
+    team_sync(T);
+    return true;
+}
+
 // Median heuristic: median of all K*K squared distances of the block (the K
 // zeros of the diagonal plus every unique pair twice; the mean of the two
 // middle values for an even count) divided by ln(K+1); 1 if the median is 0.
+// With m_prev > 0 and the distances cached, a warm start around the previous
+// median is tried first; *med_out (if not null) receives the median itself.
 __device__ float bandwidth(const Team& T, const float* th, int K, int block, float* D, bool cached,
-                           unsigned* hist, unsigned* s_u, unsigned* wsum) {
+                           unsigned* hist, unsigned* s_u, unsigned* wsum, float m_prev = 0.f, float* C = nullptr,
+                           float* med_out = nullptr) {
     if (K < 2) return 1.f;
     const int lt = threadIdx.x - T.t0;
     if (cached) {
@@ -151,6 +208,16 @@ __device__ float bandwidth(const Team& T, const float* th, int K, int block, flo
     }
     const unsigned n = (unsigned)K * (unsigned)K;
     const unsigned r_lo = (n - 1) / 2, r_hi = n / 2, uK = (unsigned)K;
+    if (cached && C && m_prev > 0.f && r_lo >= uK) {
+        // full-multiset rank r >= K is unique rank (r - K) / 2
+        const unsigned u[2] = {(r_lo - uK) / 2, (r_hi - uK) / 2};
+        float v[2];
+        if (bracket_select(T, D, K * (K - 1) / 2, u, m_prev, C, s_u, v)) {
+            const float med = r_hi != r_lo ? 0.5f * (v[0] + v[1]) : v[0];
+            if (med_out) *med_out = med;
+            return med > 0.f ? med / logf((float)K + 1.f) : 1.f;
+        }
+    }
     // full-multiset rank r maps to 0 for r < K, else to unique rank (r - K) / 2
     unsigned v_lo = 0;
     if (r_lo >= uK) v_lo = select_rank(T, D, cached, th, K, block, (r_lo - uK) / 2, hist, s_u, wsum);
@@ -177,6 +244,7 @@ __device__ float bandwidth(const Team& T, const float* th, int K, int block, flo
         med = 0.5f * (med + v_hi);
         team_sync(T);
     }
+    if (med_out) *med_out = med;
     return med > 0.f ? med / logf((float)K + 1.f) : 1.f;
 }
 
@@ -312,6 +380,7 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) 
     __shared__ unsigned hist[2048];
     __shared__ unsigned s_u[4];
     __shared__ unsigned wsum[32];
+    __shared__ float bracket[kBracketMax];
     const int K = a.K, tid = threadIdx.x;
     const int pairs = K * (K - 1) / 2;
     const bool cached = pairs <= kCacheFloats;
@@ -345,8 +414,11 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) 
     __syncthreads();
 
     const Team T = {0, (int)blockDim.x, 1};
-    const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum);
+    const float m_prev = a.med_state ? a.med_state[b] : 0.f;
+    float med = 0.f;
+    const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum, m_prev, bracket, &med);
     if (tid == 0 && a.out_h) a.out_h[b] = h;
+    if (tid == 0 && a.med_state) a.med_state[b] = med;
     const float inv_h = 1.f / h, two_h = 2.f / h;
 
     int S = 32;
