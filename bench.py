@@ -40,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+SURR_QUERIES, SURR_EPOCHS = 1 << 21, 10
 
 
 def parse():
@@ -48,7 +49,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="kinect", choices=["kinect", "box", "lidar", "batched"])
+    ap.add_argument("--workload", default="kinect", choices=["kinect", "box", "lidar", "batched", "surrogate"])
+    ap.add_argument("--nn", default=None, choices=["grid", "bf16", "fp32", "surrogate"],
+                    help="search of the registration loop (default: per workload)")
     ap.add_argument("--profile-stride", type=int, default=5,
                     help="time the gradient and Stein kernels of every s-th iteration with CUDA events")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,11 +66,32 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank registers its own problem: the workload generator's seed for `rank`."""
+    return 1000 + rank
+
+
+def slowest_rank_ms(ms: float, world: int, device: str) -> float:
+    """The step time of the slowest rank (the job's time): a MAX all-reduce
+    over the process group (nccl on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(evals_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * evals_per_rank / (ms_max / 1e3)
+
+
 def make_problem(workload: str, seed: int):
     from paper_2106_03287_gb300 import synth
     if workload == "batched":
         return synth.make_batched_problems(seed), dict(synth.WORKLOADS["batched"])
-    if workload == "kinect":
+    if workload in ("kinect", "surrogate"):
         d = synth.make_kinect_problem(seed)
     elif workload == "box":
         d = synth.make_box_problem(seed)
@@ -82,12 +106,20 @@ def workload_config(workload, d, cfg, nn_mode_name):
             "minibatch": cfg["m"], "iterations": cfg["T"], "adam_lr": cfg["lr"], "nn": nn_mode_name}
 
 
-def measured_peak():
+FALLBACK_BF16_TFLOPS = 1900.0
+# fp32 FMA lanes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (nominal unit counts and clock)
+ALU_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peak(key="hbm_gbs"):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
-    return FALLBACK_HBM_GBS, "fallback"
+            return float(json.load(f)[key]), "measured"
+    return (FALLBACK_HBM_GBS if key == "hbm_gbs" else FALLBACK_BF16_TFLOPS), "fallback"
+
+
+DEFAULT_NN = {"kinect": "grid", "box": "bf16", "lidar": "bf16", "surrogate": "surrogate"}
 
 
 class ClockSampler:
@@ -236,22 +268,38 @@ def run_ours(args):
     from paper_2106_03287_gb300 import build
     if not os.path.exists(S.LIB_PATH):
         build.build()
-    d, cfg = make_problem(args.workload, 1000 + rank)
+    d, cfg = make_problem(args.workload, rank_seed(rank))
     K = int(d["particles"].shape[0])
     M, N = int(d["ref"].shape[0]), int(d["src"].shape[0])
-    nn_mode = S.SICP_NN_GRID if args.workload != "box" else S.SICP_NN_BRUTE_FP32
-    mode_name = {S.SICP_NN_GRID: "voxel grid (exact)", S.SICP_NN_BRUTE_FP32: "exhaustive fp32"}[nn_mode]
+    nn = args.nn or DEFAULT_NN[args.workload]
+    modes = {"grid": S.SICP_NN_GRID, "bf16": S.SICP_NN_BRUTE_BF16, "fp32": S.SICP_NN_BRUTE_FP32,
+             "surrogate": S.SICP_NN_SURROGATE}
+    names = {"grid": "voxel grid (exact)", "bf16": "exhaustive, bf16 tensor-core tiles + exact fp32 re-check",
+             "fp32": "exhaustive fp32",
+             "surrogate": "learned closest-point field for the first iterations, exact voxel grid after and as fallback"}
+    nn_mode, mode_name = modes[nn], names[nn]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = S.sicp_create(local, stream)
-    p = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, nn_mode=nn_mode)
+    p = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, nn_mode=nn_mode,
+                              surrogate_iters=cfg.get("surrogate_iters", 0))
     ref_d = torch.from_numpy(d["ref"]).cuda()
     src_d = torch.from_numpy(d["src"]).cuda()
     par_d = torch.from_numpy(d["particles"]).cuda()
     torch.cuda.synchronize()
+    training = None
+    if nn == "surrogate":
+        # the learned field belongs to the reference: trained once, timed apart from the loop
+        S.sicp_set_reference(ctx, ref_d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = S.sicp_surrogate_train(ctx, SURR_QUERIES, seed=3, epochs=SURR_EPOCHS, batch=4096, lr=1e-3)
+        training = {"queries": SURR_QUERIES, "epochs": SURR_EPOCHS, "batch": 4096, "seconds": time.perf_counter() - t0,
+                    "final_loss": loss}
 
     def step():
-        S.sicp_set_reference(ctx, ref_d)
+        if nn != "surrogate":
+            S.sicp_set_reference(ctx, ref_d)
         return S.sicp_register(ctx, src_d, par_d, p)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -291,53 +339,87 @@ def run_ours(args):
     prof = S.sicp_profile(ctx, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = slowest_rank_ms(ms, world, "cuda")
     evals = K * cfg["m"] * cfg["T"]
-    value = world * evals / (ms_max / 1e3)
+    value = job_value(evals, world, ms_max)
 
     grad_ms = prof[0] / prof[1] if prof[1] else None
-    peak, peak_kind = measured_peak()
     queries_per_launch = K * cfg["m"]
-    alg_bytes = bytes_per_query * queries_per_launch
-    achieved = alg_bytes / (grad_ms * 1e-3) / 1e9 if grad_ms else None
-    tpq = ncu_traffic_per_query()
-    roofline = {"kernel": "k_grad_grid (transform + grid NN + gradient, one iteration)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} copy bandwidth",
-                "frac": achieved / peak if achieved else None,
-                "traffic": tpq * queries_per_launch if tpq else None,
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
-                "launches_timed": int(prof[1]),
-                "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
-                              "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
-                "stein_adam_avg_launch_us": 1e3 * prof[2] / prof[3] if prof[3] else None}
+    stein_us = 1e3 * prof[2] / prof[3] if prof[3] else None
+    if nn == "grid":
+        peak, peak_kind = measured_peak()
+        alg_bytes = bytes_per_query * queries_per_launch
+        achieved = alg_bytes / (grad_ms * 1e-3) / 1e9 if grad_ms else None
+        tpq = ncu_traffic_per_query()
+        roofline = {"kernel": "k_grad_grid (transform + grid NN + gradient, one iteration)", "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} copy bandwidth",
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": tpq * queries_per_launch if tpq else None,
+                    "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
+                    "launches_timed": int(prof[1]),
+                    "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
+                                  "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
+                    "stein_adam_avg_launch_us": stein_us}
+    elif nn == "bf16":
+        peak, peak_kind = measured_peak("bf16_tflops")
+        cols = 256 * ((M + 255) // 256)
+        mma_flops = 2.0 * 16 * queries_per_launch * cols    # executed: K = 16 slots, padded columns
+        achieved = mma_flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None
+        roofline = {"kernel": "k_nn_bf16 (transform + tensor-core distance tiles + fp32 re-check + gradient terms) "
+                              "and the per-particle reduction, one iteration", "bound": "tensor",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_kind": f"{peak_kind} dense bf16 (burst)",
+                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "mma_flops_per_launch": mma_flops,
+                    "algorithmic_flops_per_launch": 2.0 * 4 * queries_per_launch * M,
+                    "avg_launch_us": grad_ms * 1e3 if grad_ms else None, "launches_timed": int(prof[1]),
+                    "stein_adam_avg_launch_us": stein_us}
+    elif nn == "fp32":
+        achieved = 8.0 * queries_per_launch * M / (grad_ms * 1e-3) / 1e12 if grad_ms else None
+        roofline = {"kernel": "k_grad_brute (transform + fp32 exhaustive search + gradient, one iteration)",
+                    "bound": "alu", "achieved": achieved, "peak": ALU_FP32_TFLOPS, "unit": "TFLOP/s",
+                    "peak_kind": "nominal fp32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                    "frac": achieved / ALU_FP32_TFLOPS if achieved else None, "traffic": None,
+                    "flops_per_pair": 8, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
+                    "launches_timed": int(prof[1]), "stein_adam_avg_launch_us": stein_us}
+    else:
+        roofline = surrogate_roofline(S, ctx, p, src_d, par_d, queries_per_launch, cfg)
+        roofline["stein_adam_avg_launch_us"] = stein_us
 
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
         ref_h, src_h, par_h = pin(d["ref"]), pin(d["src"]), pin(d["particles"])
+        with_ref = nn != "surrogate"   # the learned field stays with the reference it was trained on
         for _ in range(2):
-            S.sicp_set_reference(ctx, ref_h)
+            if with_ref:
+                S.sicp_set_reference(ctx, ref_h)
             S.sicp_register(ctx, src_h, par_h, p)
         wall = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            S.sicp_set_reference(ctx, ref_h)
+            if with_ref:
+                S.sicp_set_reference(ctx, ref_h)
             out = S.sicp_register(ctx, src_h, par_h, p)
             wall.append(time.perf_counter() - t0)
         e2e = {"value": world * evals / statistics.mean(wall), "unit": "particle_point_evals/s",
-               "h2d_bytes_per_step": 12 * M + 12 * N + 24 * K, "d2h_bytes_per_step": 24 * K + 8 * 42,
-               "ms_per_step": 1e3 * statistics.mean(wall)}
+               "h2d_bytes_per_step": (12 * M if with_ref else 0) + 12 * N + 24 * K,
+               "d2h_bytes_per_step": 24 * K + 8 * 42, "ms_per_step": 1e3 * statistics.mean(wall)}
 
+    comparison = None
+    if nn in ("bf16", "surrogate"):
+        comparison = compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, cfg)
     S.sicp_destroy(ctx)
-    launches_per_step = 9 + 4 + 2 * cfg["T"]
+    per_iter = {"grid": 2, "fp32": 2, "bf16": 3}.get(nn)
+    if per_iter is not None:
+        launches_per_step = 9 + 4 + per_iter * cfg["T"]
+    else:   # surrogate, fallback, reduction and Stein for the surrogate iterations; grid and Stein after
+        si = min(cfg.get("surrogate_iters", 0), cfg["T"])
+        launches_per_step = 4 + 4 * si + 2 * (cfg["T"] - si)
     if rank == 0:
         line = {"metric": "particle_point_evals_per_sec", "value": value, "unit": "particle_point_evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -350,10 +432,86 @@ def run_ours(args):
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu}
+        if training:
+            line["surrogate_training"] = training
+        if comparison:
+            line["comparison"] = comparison
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def timed_runs(fn, flush, stream, steps):
+    import torch
+    fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, steps):
+    """bf16: the same run with the fp32 exhaustive search (the precision
+    comparison).  surrogate: the all-exact run (the ablation) and the final
+    pose mean / spread of the surrogate run against it."""
+    import ctypes
+    q = S.sicp_params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+    if nn == "bf16":
+        q.nn_mode = S.SICP_NN_BRUTE_FP32
+        run = lambda: (S.sicp_set_reference(ctx, ref_d), S.sicp_register(ctx, src_d, par_d, q))[1]
+        name = "exhaustive fp32 search"
+    else:
+        q.nn_mode = S.SICP_NN_GRID
+        run = lambda: S.sicp_register(ctx, src_d, par_d, q)
+        name = "all-exact run (voxel grid every iteration)"
+    ms = timed_runs(run, flush, stream, steps)
+    th_o, mean_o, cov_o = [np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in run()]
+    if nn != "surrogate":
+        S.sicp_set_reference(ctx, ref_d)
+    th_s, mean_s, cov_s = [np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in S.sicp_register(ctx, src_d, par_d, p)]
+    sd_o, sd_s = np.sqrt(np.diag(cov_o)), np.sqrt(np.diag(cov_s))
+    return {"other": name, "other_value": K * cfg["m"] * cfg["T"] / (ms / 1e3),
+            "other_iters_per_sec": cfg["T"] / (ms / 1e3), "other_ms_per_step": ms,
+            "particles_max_abs_diff": float(np.abs(th_s - th_o).max()),
+            "mean_diff_mm": (1e3 * np.abs(mean_s[:3] - mean_o[:3])).tolist(),
+            "mean_diff_deg": np.degrees(np.abs(mean_s[3:] - mean_o[3:])).tolist(),
+            "sd_diff_mm": (1e3 * np.abs(sd_s[:3] - sd_o[:3])).tolist(),
+            "sd_diff_deg": np.degrees(np.abs(sd_s[3:] - sd_o[3:])).tolist(),
+            "gate_1mm_0.05deg": bool(np.all(1e3 * np.abs(mean_s[:3] - mean_o[:3]) <= 1.0) and
+                                     np.all(np.degrees(np.abs(mean_s[3:] - mean_o[3:])) <= 0.05) and
+                                     np.all(1e3 * np.abs(sd_s[:3] - sd_o[:3]) <= 1.0) and
+                                     np.all(np.degrees(np.abs(sd_s[3:] - sd_o[3:])) <= 0.05))}
+
+
+def surrogate_roofline(S, ctx, p, src_d, par_d, queries, cfg):
+    """The surrogate's gradient kernels timed on a run that uses the surrogate in
+    every iteration (untimed for the metric), against the dense bf16 peak:
+    three layers, 2 (112 x 128 + 128 x 128 + 128 x 16) flops per query."""
+    import ctypes
+    q = S.sicp_params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+    q.surrogate_iters = q.T
+    S.sicp_profile(ctx, 1)
+    S.sicp_register(ctx, src_d, par_d, q)
+    S.sicp_stats(ctx, True)
+    S.sicp_register(ctx, src_d, par_d, q)
+    st = S.sicp_stats(ctx, False)
+    prof = S.sicp_profile(ctx, 0)
+    grad_ms = prof[0] / prof[1] if prof[1] else None
+    flops = 2.0 * (112 * 128 + 128 * 128 + 128 * 16) * queries
+    peak, peak_kind = measured_peak("bf16_tflops")
+    achieved = flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None
+    return {"kernel": "k_grad_surrogate + exact fallback + reduction (one surrogate iteration)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_kind": f"{peak_kind} dense bf16 (burst)",
+            "frac": achieved / peak if achieved else None, "traffic": None, "flops_per_launch": flops,
+            "avg_launch_us": grad_ms * 1e3 if grad_ms else None, "launches_timed": int(prof[1]),
+            "fallback_fraction": float(st[7] / st[6]) if st[6] else None}
 
 
 def run_ours_batched(args):
@@ -368,7 +526,7 @@ def run_ours_batched(args):
     from paper_2106_03287_gb300 import build
     if not os.path.exists(S.LIB_PATH):
         build.build()
-    raw, cfg = make_problem("batched", 1000 + rank)
+    raw, cfg = make_problem("batched", rank_seed(rank))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = S.sicp_create(local, stream)
@@ -397,10 +555,7 @@ def run_ours_batched(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = slowest_rank_ms(ms, world, "cuda")
     host = S.pack_batch([(d["ref"], d["src"], d["particles"]) for d in raw])
     for key in ("ref", "src", "par"):
         host[key] = torch.from_numpy(host[key]).pin_memory().numpy()   # pinned staging of the packed inputs

@@ -118,6 +118,17 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
                   int32_t K, const sicp_params* p, float* particles_out, double* mean6,
                   double* cov36, int on_device);
 
+/* Checkpoint / resume: T = p->T more iterations of a run that has done t0
+ * iterations.  state [3][K][6] float32 (in/out) holds the particles, then the
+ * Adam first and second moments; a new run starts from its initial particles
+ * and zero moments with t0 = 0.  Iteration t of a run draws minibatch t of
+ * p->seed and takes Adam step t + 1 whether the run is done in one call or
+ * several, so continuing with t0 += T gives the particles of one longer call.
+ * mean6, cov36 as sicp_register.  Errors as sicp_register, plus SICP_EINVAL
+ * for t0 < 0 or t0 > 2^40. */
+int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float* state, int32_t K,
+                           int64_t t0, const sicp_params* p, double* mean6, double* cov36, int on_device);
+
 /* ---- many problems at once ---- */
 
 /* P independent runs of sicp_register (Sec. IV summary) in one persistent
@@ -289,6 +300,16 @@ int sicp_surrogate_params(sicp_ctx* ctx, int set, float* params, float* norm4);
  * SICP_ECUDA, SICP_ETIMEOUT. */
 int sicp_surrogate_loss_grad(sicp_ctx* ctx, const float* params, const float* qn, const float* dstar,
                              int64_t n, float lam, float delta, float* out_loss, float* out_grad);
+
+/* Save the context's surrogate (parameters and normalisation) to `path`, or
+ * load one saved there (which marks it trained on this context).  The file is
+ * "SICPSURR", u32 version 1, u32 parameter count 33040, float norm4[4], float
+ * params[33040], u32 FNV-1a checksum of the bytes between the magic and the
+ * checksum, all little-endian.  Loading checks size, magic, version, count,
+ * checksum and finiteness.  Errors: SICP_EINVAL (unreadable or corrupt file),
+ * SICP_ENOSURROGATE (saving without a surrogate), SICP_ECUDA. */
+int sicp_surrogate_save(sicp_ctx* ctx, const char* path);
+int sicp_surrogate_load(sicp_ctx* ctx, const char* path);
 
 /* Surrogate inference: for queries q [n][3] (metres) the predicted
  * displacement out_disp [n][3] (metres; the predicted nearest point is

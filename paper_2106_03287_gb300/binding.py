@@ -41,6 +41,7 @@ EXPORTS = (
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
     "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
+    "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
 )
 
 SURROGATE_NPARAM = 33040
@@ -97,6 +98,9 @@ def lib() -> ctypes.CDLL:
             "sicp_surrogate_params": (ctypes.c_int, [P, ctypes.c_int, P, P]),
             "sicp_surrogate_loss_grad": (ctypes.c_int, [P, P, P, P, I64, F32, F32, P, P]),
             "sicp_surrogate_infer": (ctypes.c_int, [P, P, I64, P, P, ctypes.c_int]),
+            "sicp_register_continue": (ctypes.c_int, [P, P, I64, P, I32, I64, pp, P, P, ctypes.c_int]),
+            "sicp_surrogate_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+            "sicp_surrogate_load": (ctypes.c_int, [P, ctypes.c_char_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -203,6 +207,21 @@ def sicp_register(ctx, src_xyz, particles, params: sicp_params):
                                     _ptr(out, np.float32), _ptr(mean, np.float64), _ptr(cov, np.float64),
                                     _on_device(src_xyz, particles)))
     return out, mean, cov
+
+
+def sicp_register_continue(ctx, src_xyz, state, t0: int, params: sicp_params):
+    """T = params.T more iterations of a run that has done t0; state [3][K][6]
+    float32 (particles, Adam m, Adam v) is updated in place.  Returns (mean [6], cov [6][6])."""
+    src_xyz = _host(src_xyz, np.float32)
+    if state.shape[0] != 3 or state.shape[2] != 6:
+        raise ValueError("state must be [3][K][6]")
+    K = state.shape[1]
+    mean = _empty(state, (6,), np.float64)
+    cov = _empty(state, (6, 6), np.float64)
+    _check(ctx, lib().sicp_register_continue(ctx, _ptr(src_xyz, np.float32), src_xyz.shape[0], _ptr(state, np.float32),
+                                             K, int(t0), ctypes.byref(params), _ptr(mean, np.float64),
+                                             _ptr(cov, np.float64), _on_device(src_xyz, state)))
+    return mean, cov
 
 
 def sicp_minibatch(ctx, seed: int, t0: int, T: int, N: int, m: int, device=None):
@@ -318,6 +337,14 @@ def sicp_surrogate_loss_grad(ctx, params, qn, dstar, lam: float = 0.1, delta: fl
                                                _ptr(dstar, np.float32), qn.shape[0], float(lam), float(delta),
                                                ctypes.byref(loss), _ptr(g, np.float32)))
     return float(loss.value), g
+
+
+def sicp_surrogate_save(ctx, path: str) -> None:
+    _check(ctx, lib().sicp_surrogate_save(ctx, os.fsencode(path)))
+
+
+def sicp_surrogate_load(ctx, path: str) -> None:
+    _check(ctx, lib().sicp_surrogate_load(ctx, os.fsencode(path)))
 
 
 def sicp_surrogate_infer(ctx, q):

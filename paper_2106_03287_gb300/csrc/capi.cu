@@ -59,6 +59,7 @@ struct LoopKey {
     float min_conf;
     uint64_t surr_gen;      // surrogate weights / normalisation version
     uint64_t seed;
+    int64_t t0;             // first iteration of the run
     const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -585,11 +586,21 @@ int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6
     return sync(ctx);
 }
 
-int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in, int32_t K,
-                  const sicp_params* p_in, float* particles_out, double* mean6, double* cov36, int on_device) {
+}  // extern "C"
+
+namespace {
+
+// One registration run of p->T iterations starting at iteration t0 (minibatch
+// stream position and Adam step t0 + 1).  adam_in (2 [K][6] arrays: m then v,
+// may be null: zeros) seeds the Adam moments; adam_out (may be null) receives
+// them after the run.
+int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in, int32_t K,
+                 const sicp_params* p_in, float* particles_out, double* mean6, double* cov36, int on_device,
+                 int64_t t0, const float* adam_in, float* adam_out) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!src_xyz || !particles_in || !particles_out || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (t0 < 0 || t0 > ((int64_t)1 << 40)) return set_err(ctx, SICP_EINVAL, "t0 must lie in [0, 2^40]");
     const sicp_params p = normalise(p_in);
     if (N < 1 || N > kMaxN) return set_err(ctx, SICP_EINVAL, "source needs 1 <= N <= 2^31-1 points");
     if (K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "particle count must be in [1, %d]", kMaxK);
@@ -635,8 +646,19 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
     SICP_CUDA(launch_check_finite((const float*)d_th0, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
     SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
-    SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
-    SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
+    if (adam_in) {
+        const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (!on_device && !host_finite(adam_in, 12 * (int64_t)K)) return set_err(ctx, SICP_EINVAL, "non-finite input");
+        SICP_CUDA(cudaMemcpyAsync(ctx->adam_m.p, adam_in, b_th, kin, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(ctx->adam_v.p, adam_in + 6 * (size_t)K, b_th, kin, ctx->stream));
+        if (on_device) {
+            SICP_CUDA(launch_check_finite((const float*)ctx->adam_m.p, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+            SICP_CUDA(launch_check_finite((const float*)ctx->adam_v.p, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+        }
+    } else {
+        SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
+        SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
+    }
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
     float* med_state = (float*)ctx->gbar.p + 6 * (size_t)K;
     SICP_CUDA(cudaMemsetAsync(med_state, 0, 2 * sizeof(float), ctx->stream));
@@ -668,6 +690,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     key.min_conf = surr ? p.surrogate_min_conf : 0.f;
     key.surr_gen = surr ? ctx->surr_gen : 0;
     key.seed = p.seed;
+    key.t0 = t0;
     key.ptrs[0] = ctx->src4.p;
     key.ptrs[1] = ctx->mb.p;
     key.ptrs[2] = ctx->theta.p;
@@ -685,7 +708,7 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
     const bool use_graph = getenv("SICP_NO_GRAPH") == nullptr;
     auto record = [&](GraphSlot* prof) -> int {
-        SICP_CUDA(launch_minibatch(p.seed, 0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
+        SICP_CUDA(launch_minibatch(p.seed, t0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
         GradArgs g;
         g.src = (const float4*)ctx->src4.p;
         g.m = p.m;
@@ -714,9 +737,10 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
             // the grid kernel and the surrogate path leave gbar; the exhaustive kernel leaves `chunks` partials
             SteinArgs a = (grid || bf) ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
-                                            (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t + 1)
+                                            (const float*)ctx->gbar.p, 1, 1.f, K, (float)N, t0 + t + 1)
                                : stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
-                                            (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N, t + 1);
+                                            (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N,
+                                            t0 + t + 1);
             a.med_state = med_state;
             SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
@@ -770,7 +794,31 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
     if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
     if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
     if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;
+    if (adam_out) {
+        if ((rc = copy_out(ctx, adam_out, ctx->adam_m.p, b_th, on_device))) return rc;
+        if ((rc = copy_out(ctx, adam_out + 6 * (size_t)K, ctx->adam_v.p, b_th, on_device))) return rc;
+    }
     return sync(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in, int32_t K,
+                  const sicp_params* p, float* particles_out, double* mean6, double* cov36, int on_device) {
+    return register_run(ctx, src_xyz, N, particles_in, K, p, particles_out, mean6, cov36, on_device, 0, nullptr,
+                        nullptr);
+}
+
+int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float* state, int32_t K, int64_t t0,
+                           const sicp_params* p, double* mean6, double* cov36, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    if (!state) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "particle count must be in [1, %d]", kMaxK);
+    // the particles are read before they are overwritten (staged into the context first)
+    return register_run(ctx, src_xyz, N, state, K, p, state, mean6, cov36, on_device, t0, state + 6 * (size_t)K,
+                        state + 6 * (size_t)K);
 }
 
 int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8) {

@@ -28,6 +28,9 @@
 #include <float.h>
 #include <math.h>
 
+#include <stdio.h>
+#include <string.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -1172,4 +1175,73 @@ extern "C" int sicp_surrogate_infer(sicp_ctx* ctx, const float* q, int64_t n, fl
     if ((rc = read_err_flag(ctx, &tc_err))) return rc;
     if (tc_err) return set_err(ctx, SICP_ETIMEOUT, "a tensor-core wait gave up");
     return SICP_OK;
+}
+
+// ---------------------------------------------------------------- weight file
+//
+// Little-endian file: "SICPSURR", u32 version (1), u32 parameter count
+// (33,040), float norm4[4] (centre, scale), float params[33040] (the order of
+// sicp_surrogate_params), u32 FNV-1a checksum of every byte after the magic
+// and before the checksum.
+
+namespace {
+
+constexpr char kMagic[8] = {'S', 'I', 'C', 'P', 'S', 'U', 'R', 'R'};
+constexpr uint32_t kFileVersion = 1;
+
+uint32_t fnv1a(const unsigned char* p, size_t n, uint32_t h = 2166136261u) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" int sicp_surrogate_save(sicp_ctx* ctx, const char* path) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!path) return set_err(ctx, SICP_EINVAL, "null path");
+    std::vector<float> body(4 + kNParam);
+    int rc = sicp_surrogate_params(ctx, 0, body.data() + 4, body.data());
+    if (rc) return rc;
+    std::vector<unsigned char> buf(8 + 8 + sizeof(float) * body.size() + 4);
+    unsigned char* w = buf.data();
+    memcpy(w, kMagic, 8);
+    const uint32_t hdr[2] = {kFileVersion, (uint32_t)kNParam};
+    memcpy(w + 8, hdr, 8);
+    memcpy(w + 16, body.data(), sizeof(float) * body.size());
+    const uint32_t sum = fnv1a(w + 8, buf.size() - 12);
+    memcpy(w + buf.size() - 4, &sum, 4);
+    FILE* f = fopen(path, "wb");
+    if (!f) return set_err(ctx, SICP_EINVAL, "cannot open %s for writing", path);
+    const size_t n = fwrite(buf.data(), 1, buf.size(), f);
+    const int cl = fclose(f);
+    if (n != buf.size() || cl != 0) return set_err(ctx, SICP_EINVAL, "write to %s failed", path);
+    return SICP_OK;
+}
+
+extern "C" int sicp_surrogate_load(sicp_ctx* ctx, const char* path) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!path) return set_err(ctx, SICP_EINVAL, "null path");
+    FILE* f = fopen(path, "rb");
+    if (!f) return set_err(ctx, SICP_EINVAL, "cannot open %s", path);
+    const size_t want = 8 + 8 + sizeof(float) * (4 + kNParam) + 4;
+    std::vector<unsigned char> buf(want + 1);
+    const size_t n = fread(buf.data(), 1, buf.size(), f);
+    fclose(f);
+    if (n != want) return set_err(ctx, SICP_EINVAL, "%s: %zu bytes, a weight file has %zu", path, n, want);
+    if (memcmp(buf.data(), kMagic, 8) != 0) return set_err(ctx, SICP_EINVAL, "%s: not a surrogate weight file", path);
+    uint32_t hdr[2], sum;
+    memcpy(hdr, buf.data() + 8, 8);
+    memcpy(&sum, buf.data() + want - 4, 4);
+    if (hdr[0] != kFileVersion || hdr[1] != (uint32_t)kNParam)
+        return set_err(ctx, SICP_EINVAL, "%s: version %u with %u parameters, expected %u with %d", path, hdr[0], hdr[1],
+                       kFileVersion, kNParam);
+    if (fnv1a(buf.data() + 8, want - 12) != sum) return set_err(ctx, SICP_EINVAL, "%s: checksum mismatch", path);
+    std::vector<float> body(4 + kNParam);
+    memcpy(body.data(), buf.data() + 16, sizeof(float) * body.size());
+    return sicp_surrogate_params(ctx, 1, body.data() + 4, body.data());
 }

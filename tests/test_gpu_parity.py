@@ -371,3 +371,45 @@ def test_full_size_kinect_sampled(ctx):
     mo, co = O.moments(th.astype(np.float64))
     assert np.allclose(mean, mo, atol=1e-12) and np.allclose(cov, co, atol=1e-12)
     assert np.all(np.isfinite(th))
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+
+@pytest.mark.parametrize("mode", [S.SICP_NN_GRID, S.SICP_NN_BRUTE_FP32, S.SICP_NN_BRUTE_BF16])
+def test_register_continue_equals_one_call(ctx, mode):
+    """A run split into calls (state = particles + Adam moments, t0) gives the
+    particles of one call: minibatch t and Adam step t + 1 depend only on t."""
+    d = synth.make_kinect_problem(9, M=20_000, N=3000, K=24)
+    S.sicp_set_reference(ctx, d["ref"])
+    p = S.sicp_default_params(T=20, m=120, lr=0.03, seed=4, nn_mode=mode)
+    full, mean_f, cov_f = S.sicp_register(ctx, d["src"], d["particles"], p)
+    state = np.zeros((3, 24, 6), np.float32)
+    state[0] = d["particles"]
+    p.T = 8
+    S.sicp_register_continue(ctx, d["src"], state, 0, p)
+    p.T = 12
+    mean, cov = S.sicp_register_continue(ctx, d["src"], state, 8, p)
+    assert np.array_equal(state[0], full)
+    assert np.array_equal(mean, mean_f) and np.array_equal(cov, cov_f)
+    # the same on device tensors
+    st = torch.zeros((3, 24, 6), dtype=torch.float32, device="cuda")
+    st[0] = torch.from_numpy(d["particles"]).cuda()
+    src = torch.from_numpy(d["src"]).cuda()
+    p.T = 20
+    S.sicp_register_continue(ctx, src, st, 0, p)
+    assert np.array_equal(st[0].cpu().numpy(), full)
+
+
+def test_register_continue_errors(ctx):
+    d = synth.make_box_problem(1)
+    S.sicp_set_reference(ctx, d["ref"])
+    p = S.sicp_default_params(T=3, m=50)
+    state = np.zeros((3, 32, 6), np.float32)
+    state[0] = d["particles"]
+    with pytest.raises(S.SicpError) as e:
+        S.sicp_register_continue(ctx, d["src"], state, -1, p)
+    assert e.value.code == S.SICP_EINVAL
+    state[1, 0, 0] = np.nan
+    with pytest.raises(S.SicpError) as e:
+        S.sicp_register_continue(ctx, d["src"], state, 0, p)
+    assert e.value.code == S.SICP_EINVAL

@@ -284,3 +284,35 @@ def test_exact_registration_is_independent_of_context_history(trained):
     finally:
         S.sicp_destroy(f)
     assert np.array_equal(a, b)
+
+
+def test_save_load_roundtrip_and_corrupt_files(ctx, tmp_path):
+    W = _random_params(21)
+    norm4 = np.array([0.5, -1.0, 2.0, 3.0], np.float32)
+    S.sicp_surrogate_params(ctx, W, norm4)
+    path = str(tmp_path / "field.sicp")
+    S.sicp_surrogate_save(ctx, path)
+    c = S.sicp_create(0)
+    try:
+        S.sicp_surrogate_load(c, path)
+        p, n = S.sicp_surrogate_params(c)
+        assert np.array_equal(p, W) and np.array_equal(n, norm4)
+        q = np.random.default_rng(0).uniform(-2, 2, (300, 3)).astype(np.float32)
+        a, b = S.sicp_surrogate_infer(ctx, q), S.sicp_surrogate_infer(c, q)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        raw = open(path, "rb").read()
+        bad = {"truncated": raw[:-5], "flipped": raw[:100] + bytes([raw[100] ^ 1]) + raw[101:],
+               "magic": b"XICPSURR" + raw[8:], "empty": b""}
+        for name, blob in bad.items():
+            f = tmp_path / f"{name}.sicp"
+            f.write_bytes(blob)
+            with pytest.raises(S.SicpError) as e:
+                S.sicp_surrogate_load(c, str(f))
+            assert e.value.code == S.SICP_EINVAL, name
+        with pytest.raises(S.SicpError) as e:
+            S.sicp_surrogate_load(c, str(tmp_path / "missing.sicp"))
+        assert e.value.code == S.SICP_EINVAL
+        p2, _ = S.sicp_surrogate_params(c)         # a failed load leaves the loaded field alone
+        assert np.array_equal(p2, W)
+    finally:
+        S.sicp_destroy(c)
