@@ -238,14 +238,14 @@ struct GradArgs {
     int32_t m;
     const float* theta;    // K x 6
     int32_t K;
-    float* partial;        // [chunks][K][6] sums of gradient terms (not divided by m)
+    float* partial;        // exhaustive search: [chunks][K][6] sums of gradient terms (not divided by m);
+                           // grid search: [K][m][6] terms of each query
     int32_t* out_nn;       // K x m or null
     unsigned long long* stats;  // search work counters or null
-    // grid search only: the last warp to finish a particle folds that
-    // particle's chunk partials into gbar = inv_m * sum (fixed chunk order);
-    // `done` holds one arrival counter per particle, zero between launches.
+    // grid search only: gbar = inv_m * (sum over the minibatch of the terms),
+    // reduced in a fixed order after the search kernel.
     float* gbar;           // K x 6
-    unsigned* done;        // K
+    unsigned* done;        // K arrival counters (unused by the grid search)
     float inv_m;
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);

@@ -104,18 +104,16 @@ __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, 
         const float rem = clip2 - dz * dz - dy * dy;
         if (rem >= 0.f) {
             w.rows += 1;
+            // the row's cells within reach along x; cell_start bounds their points (empty cells add none)
             const int rowi = z * g.dims.y + y;
-            const int2 span = __ldg(g.row_span + rowi);
-            if (span.x <= span.y) {
-                const float r = sqrtf(rem) + g.tol;
-                const int x0 = max(max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), span.x), xlo);
-                const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), span.y), xhi);
-                if (x0 <= x1) {
-                    const int64_t row = (int64_t)rowi * g.dims.x;
-                    b = __ldg(g.cell_start + row + x0);
-                    len = __ldg(g.cell_start + row + x1 + 1) - b;
-                    w.segs += len > 0;
-                }
+            const float r = sqrtf(rem) + g.tol;
+            const int x0 = max(max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), 0), xlo);
+            const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), g.dims.x - 1), xhi);
+            if (x0 <= x1) {
+                const int64_t row = (int64_t)rowi * g.dims.x;
+                b = __ldg(g.cell_start + row + x0);
+                len = __ldg(g.cell_start + row + x1 + 1) - b;
+                w.segs += len > 0;
             }
         }
     }
@@ -189,6 +187,8 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
     return false;
 }
 
+__device__ __forceinline__ void prove(const GridSearch& S, float3 q, Best& B, Work& w);
+
 __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best& B, Work& w) {
     const int lane = threadIdx.x & 31;
     const GridView& F = S.fine;
@@ -211,8 +211,16 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
             round_rows(F, q, lane < 9, sy + lane % 3 - 1, sz + lane / 3 - 1, sx - 1, sx + 1, bound2(B.d), B, w);
         }
     }
-    // prove it: walk the table with that bound on the fine level (bound under
-    // kFineReach cells) or the coarse level
+    prove(S, q, B, w);
+}
+
+// The exact nearest point of q given a starting answer B (any reference
+// point, or none): walk the table with the shrinking bound on the fine level
+// (bound under kFineReach cells) or the coarse level, and scan everything if
+// the table cannot settle it.
+__device__ __forceinline__ void prove(const GridSearch& S, float3 q, Best& B, Work& w) {
+    const int lane = threadIdx.x & 31;
+    const GridView& F = S.fine;
     const float reach = kFineReach * F.cell;
     const bool fine = B.d <= reach * reach;
     w.far += (lane == 0 && !fine);

@@ -62,65 +62,57 @@ __global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float*
     if (stats) add_stats(stats, w);
 }
 
-// grid (chunks, particle pairs).  Warp w of CTA (c, b) handles particle
-// b*kPb + w and minibatch entries [c*kKc, (c+1)*kKc), one query at a time.
-// Lane 0 accumulates the particle's gradient terms and writes the chunk's
-// partial sum; the last warp to finish a particle folds its chunk partials
-// into gbar in fixed chunk order.  Warps never wait for each other.
+// grid (minibatch entries, blocks of kPart particles).  Warp w of CTA (k, b)
+// handles minibatch entry k for the kSeq particles b*kPart + w*kSeq ...: the
+// first query runs the whole search; each next one is the same source point
+// under a neighbouring particle, so the previous answer is a starting bound
+// (kept when it lies within kReuse cells, else the seed map is used).  Lane 0
+// writes the query's gradient terms to qterms[j][k]; a fixed-order reduction
+// over k follows (launch_qterms_to_gbar).
+constexpr int kSeq = 4;                                   // particles per warp
+constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
+constexpr float kReuse = 2.f;
+
 __global__ void __launch_bounds__(kGradThreads, 16) k_grad_grid(GradArgs a, GridSearch S) {
-    __shared__ Pose P[kPb];
+    __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.y * kPb + warp;
-    if (j >= a.K) return;                      // whole warp: no block-wide barrier below
-    if (lane == 0) make_pose(a.theta + 6 * j, P[warp]);
-    __syncwarp();
-    float gr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int k = blockIdx.x;
+    const int j0 = blockIdx.y * kPart;
+    for (int i = threadIdx.x; i < kPart; i += blockDim.x)
+        if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
+    __syncthreads();
+    const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+    const float3 s = make_float3(s4.x, s4.y, s4.z);
+    const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
     Work w;
-    for (int kk = 0; kk < kKc; ++kk) {
-        const int k = blockIdx.x * kKc + kk;
-        if (k >= a.m) break;
-        const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
-        const float3 s = make_float3(s4.x, s4.y, s4.z);
-        const float3 q = apply_pose(P[warp], s);
-        Best B;
-        grid_search(S, q, B, w);
-        const bool found = B.i != kNone;   // false only for a non-finite distance
-        if (lane == 0) {
-            if (found) {
-                float t[6];
-                grad_terms(P[warp], s, make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z), t);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) gr[c] += t[c];
+    Best B;
+    B.i = kNone;
+    for (int i = 0; i < kSeq; ++i) {
+        const int jl = warp * kSeq + i, j = j0 + jl;
+        if (j >= a.K) break;                        // warp-uniform
+        const float3 q = apply_pose(P[jl], s);
+        bool seeded = false;
+        if (B.i != kNone) {
+            const float d = dist2(make_float4(B.p.x, B.p.y, B.p.z, 0.f), q);
+            if (d <= reuse2) {
+                B.d = d;
+                seeded = true;
+                w.queries += lane == 0;
+                prove(S, q, B, w);
             }
+        }
+        if (!seeded) grid_search(S, q, B, w);
+        if (lane == 0) {
+            float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const bool found = B.i != kNone;   // false only for a non-finite distance
+            if (found) grad_terms(P[jl], s, make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z), t);
+            float* dst = a.partial + ((int64_t)j * a.m + k) * 6;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) dst[c] = t[c];
             if (a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
         }
     }
     if (a.stats) add_stats(a.stats, w);
-    unsigned last = 0;
-    if (lane == 0) {
-        float* dst = a.partial + ((int64_t)blockIdx.x * a.K + j) * 6;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) dst[c] = gr[c];
-        __threadfence();
-        last = atomicAdd(a.done + j, 1u) == gridDim.x - 1;
-    }
-    if (!__shfl_sync(kFull, last, 0)) return;
-    __threadfence();
-    // lanes 0..29: component lane % 6, chunk subset lane / 6
-    constexpr int kParts = 5;
-    const int c = lane % 6, part = lane / 6;
-    float sum = 0.f;
-    if (part < kParts) {
-#pragma unroll 4
-        for (int ch = part; ch < (int)gridDim.x; ch += kParts) sum += __ldcg(a.partial + ((int64_t)ch * a.K + j) * 6 + c);
-    }
-    float tot = sum;
-#pragma unroll
-    for (int p = 1; p < kParts; ++p) tot += __shfl_sync(kFull, sum, lane + 6 * p < 32 ? lane + 6 * p : lane);
-    if (lane < 6) {
-        a.gbar[j * 6 + c] = tot * a.inv_m;
-        if (lane == 0) a.done[j] = 0u;
-    }
 }
 
 // ---------------------------------------------------------------- build kernels
@@ -427,7 +419,7 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
 
 GradLayout grad_layout_grid(int32_t m) {
     GradLayout L;
-    L.chunks = (m + kKc - 1) / kKc;
+    L.chunks = m;   // per-query terms, [K][m][6]
     L.threads = kGradThreads;
     return L;
 }
@@ -440,10 +432,11 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
 }
 
 cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch& g, cudaStream_t s) {
-    const GradLayout L = grad_layout_grid(a.m);
-    dim3 grid(L.chunks, (a.K + kPb - 1) / kPb);
+    dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
     k_grad_grid<<<grid, kGradThreads, 0, s>>>(a, g);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
 }
 
 }  // namespace sicp
