@@ -318,7 +318,7 @@ void sicp_destroy(sicp_ctx* c) {
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
     for (Grid* g : {&c->grid, &c->grid2}) {
-        void* gp[] = {g->sorted, g->cell_start, g->row_span, g->cell_of, g->counts, g->scan_sums, g->seed,
+        void* gp[] = {g->sorted, g->cell_start, g->cell_of, g->counts, g->scan_sums, g->seed,
                       g->seed_tmp};
         for (void* p : gp)
             if (p) cudaFree(p);

@@ -97,7 +97,6 @@ struct GridView {
     int3 dims;                      // cells per axis
     const float4* sorted;           // M, w = original index bits
     const int32_t* cell_start;      // ncells + 1
-    const int2* row_span;           // dims.y * dims.z: first and last non-empty x of the row
     const int32_t* seed;            // ncells: position in `sorted` of a point near the cell centre (fine level)
 };
 
@@ -106,13 +105,12 @@ struct Grid {
     int64_t ncells = 0;
     float4* sorted = nullptr;
     int32_t* cell_start = nullptr;
-    int2* row_span = nullptr;
     int32_t* cell_of = nullptr;     // M: cell id of each reference point (build scratch)
     int32_t* counts = nullptr;      // ncells + 1 (build scratch)
     int32_t* scan_sums = nullptr;   // build scratch
     int32_t* seed = nullptr;        // ncells (fine level only)
     int32_t* seed_tmp = nullptr;    // ncells (build scratch)
-    size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_rows = 0, cap_sums = 0,
+    size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_sums = 0,
            cap_seed = 0, cap_seed_tmp = 0;
 };
 
@@ -195,6 +193,7 @@ int ensure(sicp_ctx* c, Buf& b, size_t bytes);
     } while (0)
 
 // ---- kernel launchers (each returns the launch status) ----
+
 
 // points [n][3] -> float4 (w = index bits); flags[0] |= 1 on a non-finite value
 cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* flags, cudaStream_t s);

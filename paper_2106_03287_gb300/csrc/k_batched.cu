@@ -147,22 +147,6 @@ __global__ void kb_sort_cells(const int32_t* __restrict__ cell_start, int64_t nc
     }
 }
 
-__global__ void kb_row_span(const GridView* __restrict__ views, const int64_t* __restrict__ row_off, int P,
-                            int64_t nrows, int2* __restrict__ span) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
-        const int p = find_problem(row_off, P, r);
-        const GridView g = views[p];
-        const int32_t* cs = g.cell_start + (r - row_off[p]) * g.dims.x;
-        int lo = g.dims.x, hi = -1;
-        for (int x = 0; x < g.dims.x; ++x)
-            if (cs[x + 1] > cs[x]) {
-                if (lo > x) lo = x;
-                hi = x;
-            }
-        span[r] = make_int2(lo, hi);
-    }
-}
-
 __device__ __forceinline__ float3 centre_of(const GridView& g, int x, int y, int z) {
     return make_float3(g.origin.x + ((float)x + 0.5f) * g.cell, g.origin.y + ((float)y + 0.5f) * g.cell,
                        g.origin.z + ((float)z + 0.5f) * g.cell);
@@ -397,12 +381,12 @@ int3 level_dims(const float ext[3], double& c, int64_t max_cells) {
 struct BatchState {
     Buf ref4, src4, mb, theta, am, av, partial, moments, stage, flags, bar;
     Buf ref_off, src_off, part_off, item_off, lohi;
-    // per level: sorted points, cell_of, counts, cell_start, row_span, scan sums, views, cell/row offsets
+    // per level: sorted points, cell_of, counts, cell_start, scan sums, views, cell offsets
     struct Level {
-        Buf sorted, staging, cell_of, counts, cell_start, row_span, sums, views, cell_off, row_off, seed, seed_tmp;
+        Buf sorted, staging, cell_of, counts, cell_start, sums, views, cell_off, seed, seed_tmp;
         std::vector<GridView> hv;
-        std::vector<int64_t> h_cell_off, h_row_off;
-        int64_t ncells = 0, nrows = 0;
+        std::vector<int64_t> h_cell_off;
+        int64_t ncells = 0;
     } lv[2];
     Buf searches;
     // built-reference signature and captured graph
@@ -420,8 +404,8 @@ struct BatchState {
         for (Buf* x : bs)
             if (x->p) cudaFree(x->p);
         for (Level& L : lv) {
-            Buf* ls[] = {&L.sorted, &L.staging, &L.cell_of, &L.counts, &L.cell_start, &L.row_span, &L.sums,
-                         &L.views, &L.cell_off, &L.row_off, &L.seed, &L.seed_tmp};
+            Buf* ls[] = {&L.sorted, &L.staging, &L.cell_of, &L.counts, &L.cell_start, &L.sums,
+                         &L.views, &L.cell_off, &L.seed, &L.seed_tmp};
             for (Buf* x : ls)
                 if (x->p) cudaFree(x->p);
         }
@@ -447,7 +431,6 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
         BatchState::Level& L = B.lv[l];
         L.hv.assign(P, GridView{});
         L.h_cell_off.assign(P + 1, 0);
-        L.h_row_off.assign(P + 1, 0);
         for (int p = 0; p < P; ++p) {
             float ext[3];
             double X = 0.0, maxext = 0.0;
@@ -477,20 +460,16 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
             v.tol = (float)(1e-6 * (X + c));
             v.dims = d;
             L.h_cell_off[p + 1] = L.h_cell_off[p] + (int64_t)d.x * d.y * d.z;
-            L.h_row_off[p + 1] = L.h_row_off[p] + (int64_t)d.y * d.z;
         }
         L.ncells = L.h_cell_off[P];
-        L.nrows = L.h_row_off[P];
         if ((rc = ensure(ctx, L.sorted, sizeof(float4) * M))) return rc;
         if ((rc = ensure(ctx, L.staging, sizeof(float4) * M))) return rc;
         if ((rc = ensure(ctx, L.cell_of, sizeof(int32_t) * M))) return rc;
         if ((rc = ensure(ctx, L.counts, sizeof(int32_t) * (L.ncells + 1)))) return rc;
         if ((rc = ensure(ctx, L.cell_start, sizeof(int32_t) * (L.ncells + 1)))) return rc;
-        if ((rc = ensure(ctx, L.row_span, sizeof(int2) * L.nrows))) return rc;
         if ((rc = ensure(ctx, L.sums, sizeof(int32_t) * scan_sums_size(L.ncells)))) return rc;
         if ((rc = ensure(ctx, L.views, sizeof(GridView) * P))) return rc;
         if ((rc = ensure(ctx, L.cell_off, sizeof(int64_t) * (P + 1)))) return rc;
-        if ((rc = ensure(ctx, L.row_off, sizeof(int64_t) * (P + 1)))) return rc;
         if (l == 0) {
             if ((rc = ensure(ctx, L.seed, sizeof(int32_t) * L.ncells))) return rc;
             if ((rc = ensure(ctx, L.seed_tmp, sizeof(int32_t) * L.ncells))) return rc;
@@ -499,15 +478,12 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
             GridView& v = L.hv[p];
             v.sorted = (const float4*)L.sorted.p;
             v.cell_start = (const int32_t*)L.cell_start.p + L.h_cell_off[p];
-            v.row_span = (const int2*)L.row_span.p + L.h_row_off[p];
             v.seed = l == 0 ? (const int32_t*)L.seed.p + L.h_cell_off[p] : nullptr;
         }
         SICP_CUDA(cudaMemcpyAsync(L.views.p, L.hv.data(), sizeof(GridView) * P, cudaMemcpyHostToDevice, s));
         SICP_CUDA(cudaMemcpyAsync(L.cell_off.p, L.h_cell_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
-        SICP_CUDA(cudaMemcpyAsync(L.row_off.p, L.h_row_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
         const GridView* dv = (const GridView*)L.views.p;
         const int64_t* dco = (const int64_t*)L.cell_off.p;
-        const int64_t* dro = (const int64_t*)L.row_off.p;
         SICP_CUDA(cudaMemsetAsync(L.counts.p, 0, sizeof(int32_t) * (L.ncells + 1), s));
         kb_cell_assign<<<nblocks(M, 256), 256, 0, s>>>((const float4*)B.ref4.p, M, (const int64_t*)B.ref_off.p, P, dv,
                                                        dco, (int32_t*)L.cell_of.p, (int32_t*)L.counts.p);
@@ -521,8 +497,6 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
         SICP_CUDA(cudaGetLastError());
         kb_sort_cells<<<nblocks(L.ncells * 32, 256), 256, 0, s>>>((const int32_t*)L.cell_start.p, L.ncells,
                                                                   (const float4*)L.staging.p, (float4*)L.sorted.p);
-        SICP_CUDA(cudaGetLastError());
-        kb_row_span<<<nblocks(L.nrows, 128), 128, 0, s>>>(dv, dro, P, L.nrows, (int2*)L.row_span.p);
         SICP_CUDA(cudaGetLastError());
         if (l == 0) {
             int32_t* a = (int32_t*)L.seed.p;

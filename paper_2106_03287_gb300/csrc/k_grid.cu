@@ -4,7 +4,7 @@
 // level (cell 4c) over the same points:
 //   cell id of every point -> per-cell counts -> exclusive scan (cell_start)
 //   -> scatter into `sorted` (float4, w = original index) -> order each cell
-//   by index -> per row (y, z) the first and last non-empty x.
+//   by index.
 // The fine level also gets a seed map: for every cell, a point close to the
 // cell centre, found by jump flooding (each cell repeatedly adopts the
 // closest seed among its neighbours at offsets n/2, n/4, ..., 1, 1).
@@ -15,15 +15,17 @@
 // offsets (dy, dz) in increasing order of a lower bound on the distance from
 // the query to the row (offsets mirrored into the half of the cell the query
 // lies in).  A round gives each lane one row; the lane clips the row to the
-// ball of the current bound (skipping empty or out-of-reach rows) and
-// publishes the row segment; the warp flattens the round's segments and
+// ball of the current bound (skipping out-of-reach rows) and publishes the
+// row segment (two cell_start loads); the warp flattens the round's segments and
 // evaluates their points 32 at a time, so all lanes do the same work; a warp
 // minimum (squared distance, then lowest index) closes the round.
 // The seed of the query's cell gives a first point; a round over the
 // 3 x 3 x 3 cells around that point brings the bound close to the true
 // distance; then the table is walked from the start with that bound on the
 // fine level (bound under 6 cells) or the coarse level, until the next row is
-// out of reach.  A query the table cannot settle scans all points.
+// out of reach.  A query the table cannot settle scans all points.  In the
+// gradient kernel a query whose neighbouring particle's answer lies within
+// two fine cells starts the walk from that answer instead.
 // Every search uses the same fp32 squared distance and tie rule as the
 // exhaustive scan, so both give the same answer.
 //
@@ -159,21 +161,6 @@ __global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int64_t nce
     }
 }
 
-__global__ void k_row_span(const int32_t* __restrict__ cell_start, GridView g, int2* __restrict__ span) {
-    const int64_t rows = (int64_t)g.dims.y * g.dims.z;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t* cs = cell_start + r * g.dims.x;
-        int lo = g.dims.x, hi = -1;
-        for (int x = 0; x < g.dims.x; ++x) {
-            if (cs[x + 1] > cs[x]) {
-                if (lo > x) lo = x;
-                hi = x;
-            }
-        }
-        span[r] = make_int2(lo, hi);
-    }
-}
-
 __device__ __forceinline__ float3 cell_centre(const GridView& g, int x, int y, int z) {
     return make_float3(g.origin.x + ((float)x + 0.5f) * g.cell, g.origin.y + ((float)y + 0.5f) * g.cell,
                        g.origin.z + ((float)z + 0.5f) * g.cell);
@@ -270,13 +257,11 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     cudaStream_t s = ctx->stream;
     const int3 dims = dims_for(ext, c);
     const int64_t ncells = (int64_t)dims.x * dims.y * dims.z;
-    const int64_t rows = (int64_t)dims.y * dims.z;
     int rc;
     if ((rc = grow(ctx, G.sorted, G.cap_points, (size_t)M))) return rc;
     if ((rc = grow(ctx, G.cell_of, G.cap_cellof, (size_t)M))) return rc;
     if ((rc = grow(ctx, G.cell_start, G.cap_cells, (size_t)ncells + 1))) return rc;
     if ((rc = grow(ctx, G.counts, G.cap_counts, (size_t)ncells + 1))) return rc;
-    if ((rc = grow(ctx, G.row_span, G.cap_rows, (size_t)rows))) return rc;
     if ((rc = grow(ctx, G.scan_sums, G.cap_sums, scan_sums_size(ncells)))) return rc;
     if (seeds) {
         if ((rc = grow(ctx, G.seed, G.cap_seed, (size_t)ncells))) return rc;
@@ -294,7 +279,6 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     v.dims = dims;
     v.sorted = G.sorted;
     v.cell_start = G.cell_start;
-    v.row_span = G.row_span;
     v.seed = seeds ? G.seed : nullptr;
     G.ncells = ncells;
     SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
@@ -305,8 +289,6 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     k_scatter<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, G.cell_of, G.cell_start, G.counts, staging);
     SICP_CUDA(cudaGetLastError());
     k_sort_cells<<<blocks_for(ncells * 32, 256), 256, 0, s>>>(G.cell_start, ncells, staging, G.sorted);
-    SICP_CUDA(cudaGetLastError());
-    k_row_span<<<blocks_for(rows, 128), 128, 0, s>>>(G.cell_start, v, G.row_span);
     SICP_CUDA(cudaGetLastError());
     if (seeds) {
         int32_t* a = G.seed;
