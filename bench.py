@@ -173,7 +173,7 @@ class ClockSampler:
 
 def grad_kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_grid.cu", "common.cuh"):
+    for f in ("k_grid.cu", "grid_search.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2106_03287_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -539,6 +539,14 @@ def run_ours_batched(args):
     evals = sum(Ks) * cfg["m"] * cfg["T"]
     for _ in range(max(args.warmup, 3)):
         S.sicp_register_batched(ctx, dev, p)
+    # work counters of one (untimed) step: algorithmic bytes of the searches
+    S.sicp_stats(ctx, True)
+    S.sicp_register_batched(ctx, dev, p)
+    st = S.sicp_stats(ctx, False).astype(np.float64)
+    queries = st[0]
+    rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
+    bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q
+    S.sicp_profile(ctx, 1)   # the persistent launch of each timed step joins the totals
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -553,9 +561,22 @@ def run_ours_batched(args):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    prof = S.sicp_profile(ctx, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     ms_max = slowest_rank_ms(ms, world, "cuda")
+    kernel_ms = prof[0] / prof[1] if prof[1] else None
+    peak, peak_kind = measured_peak()
+    alg_bytes = bytes_per_query * queries
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9 if kernel_ms else None
+    roofline = {"kernel": "kb_persistent (all T iterations of all problems: transform + grid NN + gradient, "
+                          "then the Stein/Adam phase, grid barriers between)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} copy bandwidth",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": alg_bytes, "queries_per_launch": queries,
+                "avg_launch_us": kernel_ms * 1e3 if kernel_ms else None, "launches_timed": int(prof[1]),
+                "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
+                              "far_frac": st[4] / queries, "exhaustive_frac": st[5] / queries}}
     host = S.pack_batch([(d["ref"], d["src"], d["particles"]) for d in raw])
     for key in ("ref", "src", "par"):
         host[key] = torch.from_numpy(host[key]).pin_memory().numpy()   # pinned staging of the packed inputs
@@ -572,6 +593,10 @@ def run_ours_batched(args):
            "h2d_bytes_per_step": 12 * (Mtot + Ntot) + 24 * sum(Ks), "d2h_bytes_per_step": 24 * sum(Ks) + 8 * 42 * len(raw),
            "ms_per_step": 1e3 * statistics.mean(wall)}
     S.sicp_destroy(ctx)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(raw[0], cfg, budget_s=10.0)
+        cpu["sample"] = "problem 0 of the batch: " + cpu["sample"]
     if rank == 0:
         line = {"metric": "particle_point_evals_per_sec", "value": world * evals / (ms_max / 1e3),
                 "unit": "particle_point_evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -585,7 +610,7 @@ def run_ours_batched(args):
                 "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": (2 + 2 * 9 + 3 + 4) * args.steps,
-                "roofline": None, "cpu_baseline": None}
+                "roofline": roofline, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

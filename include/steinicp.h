@@ -337,7 +337,10 @@ int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8);
  * host while the next run executes.  Copies the totals since the previous
  * call into out4 (may be NULL): gradient-kernel ms, gradient launches timed,
  * Stein-kernel ms, Stein launches timed; then zeroes them and sets the
- * stride (0 = off).  Synchronises the context's stream. */
+ * stride (0 = off).  While the stride is > 0, each sicp_register_batched call
+ * adds its one persistent launch (all T iterations, with the minibatch draw
+ * before it and the moments after it) to the gradient-kernel totals.
+ * Synchronises the context's stream. */
 int sicp_profile(sicp_ctx* ctx, int stride, double* out4);
 
 #ifdef __cplusplus

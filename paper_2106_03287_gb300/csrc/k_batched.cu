@@ -231,6 +231,7 @@ struct BatchArgs {
     float mu[6], sigma[3], kappa[3];
     unsigned* bar;                       // arrival count, generation
     int* err;
+    unsigned long long* stats;           // search work counters or null
 };
 
 // Grid-wide barrier with a bounded wait; false if any CTA gave up waiting.
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
 #pragma unroll
                 for (int a = 0; a < 6; ++a) dst[a] = gr[a];
             }
+            if (b.stats) add_stats(b.stats, w);
             __syncwarp();
         }
         if (!grid_barrier(b.bar, b.err)) return;
@@ -636,6 +638,7 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
     const int ctas = per_sm * ctx->num_sms;
 
     BatchArgs a;
+    memset(&a, 0, sizeof a);   // the bytes (padding too) key the captured graph
     a.P = P;
     a.T = p.T;
     a.m = p.m;
@@ -664,7 +667,13 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
     }
     a.bar = (unsigned*)B.bar.p;
     a.err = (int*)B.flags.p + 2;
+    a.stats = ctx->stats_on ? (unsigned long long*)ctx->stats.p : nullptr;
 
+    // with kernel timing on (sicp_profile), the launch's duration joins the
+    // context's gradient-kernel totals
+    float prof_ms = 0.f;
+    const bool to_prof = !elapsed_ms && ctx->prof_stride > 0;
+    if (to_prof) elapsed_ms = &prof_ms;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (elapsed_ms) {
         SICP_CUDA(cudaEventCreate(&e0));
@@ -729,6 +738,10 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
         cudaEventElapsedTime(elapsed_ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (to_prof) {
+            ctx->prof[0] += prof_ms;
+            ctx->prof[1] += 1.0;
+        }
     }
     if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
     if (flags[2]) return set_err(ctx, SICP_ETIMEOUT, "a grid barrier of the persistent kernel timed out");
