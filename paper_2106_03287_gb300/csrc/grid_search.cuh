@@ -18,7 +18,6 @@ constexpr int kWarps = kThreads / 32;  // queries in flight per CTA, one warp ea
 constexpr int kGradThreads = 64;       // gradient kernel CTA: one warp per particle
 constexpr int kPb = kGradThreads / 32;  // particles per CTA in the gradient kernel
 constexpr int kKc = 4;                 // minibatch entries per warp in the gradient kernel
-constexpr int kFirstRound = 8;         // table entries in the first round of a walk
 constexpr int kCoarseFactor = 4;
 constexpr float kFineReach = 6.f;      // the far phase proves on the fine level below this many cells
 constexpr int kTableRadius = 48;
@@ -172,9 +171,8 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
     const QueryCell c = query_cell(g, q);
     for (int base = 0; base < n;) {
         if (cleared(g, tab, base, B.d)) return bound2(B.d) <= cap2;
-        const int width = base == 0 ? kFirstRound : 32;
         const int e = base + lane;
-        const bool has = lane < width && e < n;
+        const bool has = e < n;
         int y = 0, z = 0;
         if (has) {
             const short2 o = __ldg(tab.off + e);
@@ -182,7 +180,7 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
             z = c.cz + c.sz * o.y;
         }
         round_rows(g, q, has, y, z, 0, g.dims.x - 1, fminf(bound2(B.d), cap2), B, w);
-        base += width;
+        base += 32;
     }
     return false;
 }
@@ -196,20 +194,14 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
     B.i = kNone;
     B.p = make_float3(0.f, 0.f, 0.f);
     w.queries += lane == 0;
-    // seed of the query's cell, then the 3 x 3 x 3 cells around the seed point
-    {
-        const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
-        const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
-        const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
-        const int s = __ldg(F.seed + ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx);
-        if (s >= 0) {
-            const float4 r = __ldg(F.sorted + s);
-            take(B, r, q, __float_as_int(r.w));
-            const int sx = cell_coord(r.x, F.origin.x, F.inv_cell, F.dims.x);
-            const int sy = cell_coord(r.y, F.origin.y, F.inv_cell, F.dims.y);
-            const int sz = cell_coord(r.z, F.origin.z, F.inv_cell, F.dims.z);
-            round_rows(F, q, lane < 9, sy + lane % 3 - 1, sz + lane / 3 - 1, sx - 1, sx + 1, bound2(B.d), B, w);
-        }
+    // the seed of the query's cell is the starting answer (every lane loads it)
+    const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
+    const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
+    const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
+    const int s = __ldg(F.seed + ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx);
+    if (s >= 0) {
+        const float4 r = __ldg(F.sorted + s);
+        take(B, r, q, __float_as_int(r.w));
     }
     prove(S, q, B, w);
 }

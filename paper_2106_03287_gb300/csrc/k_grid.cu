@@ -19,11 +19,12 @@
 // row segment (two cell_start loads); the warp flattens the round's segments and
 // evaluates their points 32 at a time, so all lanes do the same work; a warp
 // minimum (squared distance, then lowest index) closes the round.
-// The seed of the query's cell gives a first point; a round over the
-// 3 x 3 x 3 cells around that point brings the bound close to the true
-// distance; then the table is walked from the start with that bound on the
-// fine level (bound under 6 cells) or the coarse level, until the next row is
-// out of reach.  A query the table cannot settle scans all points.  In the
+// The seed of the query's cell gives a first point and bound; then the table
+// is walked from the start, 32 rows a round, with that bound on the fine level
+// (bound under 6 cells) or the coarse level, until the next row is out of
+// reach.  (A first round over the 3 x 3 x 3 cells around the seed, to tighten
+// the bound before the walk, cost more than it saved: the walk's first 32 rows
+// already hold them.)  A query the table cannot settle scans all points.  In the
 // gradient kernel a query whose neighbouring particle's answer lies within
 // two fine cells starts the walk from that answer instead.
 // Every search uses the same fp32 squared distance and tie rule as the
@@ -71,11 +72,11 @@ __global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float*
 // (kept when it lies within kReuse cells, else the seed map is used).  Lane 0
 // writes the query's gradient terms to qterms[j][k]; a fixed-order reduction
 // over k follows (launch_qterms_to_gbar).
-constexpr int kSeq = 4;                                   // particles per warp
+constexpr int kSeq = 2;                                   // particles per warp
 constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
 constexpr float kReuse = 2.f;
 
-__global__ void __launch_bounds__(kGradThreads, 16) k_grad_grid(GradArgs a, GridSearch S) {
+__global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, GridSearch S) {
     __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x;
