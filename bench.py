@@ -311,7 +311,7 @@ def run_ours(args):
     S.sicp_stats(ctx, True)
     step()
     st = S.sicp_stats(ctx, False).astype(np.float64)
-    queries = st[0]
+    queries = max(st[0], 1.0)   # grid-search counters (zero in the exhaustive modes)
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
     coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
     bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q

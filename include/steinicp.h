@@ -208,7 +208,9 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
  * size that scales them (G = -N gbar + grad log prior); t the 1-based Adam
  * step; p supplies lr, Adam constants and the prior.  Optional outputs:
  * out_phi [K][6] the Stein direction, out_h [2] the translation and rotation
- * bandwidths.  Errors: SICP_EINVAL (K < 1, t < 1, N < 1). */
+ * bandwidths.  Errors: SICP_EINVAL (K < 1, t < 1, N < 1), SICP_ETIMEOUT (the
+ * CTAs that share one block's update wait for one another with a bounded
+ * wait; nothing is written when it gives up). */
 int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_v,
                     const float* gbar, int32_t K, int64_t N, int64_t t, const sicp_params* p,
                     float* out_phi, float* out_h, int on_device);

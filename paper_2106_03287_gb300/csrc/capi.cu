@@ -221,6 +221,8 @@ SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, c
     a.out_phi = nullptr;
     a.out_h = nullptr;
     a.med_state = nullptr;
+    a.arrive = nullptr;
+    a.err = nullptr;
     return a;
 }
 
@@ -547,7 +549,7 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
     float* av = am + 6 * K;
     float* gb = av + 6 * K;
     float* phi = gb + 6 * K;
-    float* hh = phi + 6 * K;   // 2 floats in the padding
+    float* hh = phi + 6 * K;   // 2 floats in the padding, then the 2 Stein arrival counters
     const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     SICP_CUDA(cudaMemcpyAsync(th, particles, b, kin, ctx->stream));
     SICP_CUDA(cudaMemcpyAsync(am, adam_m, b, kin, ctx->stream));
@@ -561,7 +563,12 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
     SteinArgs a = stein_args(p, th, am, av, gb, 1, 1.f, K, (float)N, t);
     a.out_phi = phi;
     a.out_h = hh;
+    a.arrive = (unsigned*)(hh + 2);
+    a.err = (int*)ctx->flags.p + 3;
+    SICP_CUDA(cudaMemsetAsync(a.arrive, 0, 2 * sizeof(unsigned), ctx->stream));
     SICP_CUDA(launch_stein_adam(a, ctx->stream));
+    if ((rc = read_flags(ctx, flags))) return rc;
+    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded wait of the Stein update gave up");
     const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     SICP_CUDA(cudaMemcpyAsync(particles, th, b, kout, ctx->stream));
     SICP_CUDA(cudaMemcpyAsync(adam_m, am, b, kout, ctx->stream));
@@ -660,8 +667,9 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
     }
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
+    // after gbar: the two blocks' previous medians, then their Stein arrival counters
     float* med_state = (float*)ctx->gbar.p + 6 * (size_t)K;
-    SICP_CUDA(cudaMemsetAsync(med_state, 0, 2 * sizeof(float), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(med_state, 0, 4 * sizeof(float), ctx->stream));
 
     const int stride = ctx->prof_stride;
     LoopKey key;
@@ -742,6 +750,8 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
                                             (const float*)ctx->partial.p, chunks, 1.f / (float)p.m, K, (float)N,
                                             t0 + t + 1);
             a.med_state = med_state;
+            a.arrive = (unsigned*)(med_state + 2);
+            a.err = (int*)ctx->flags.p + 3;
             SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;
@@ -790,7 +800,8 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     int flags[4];
     if ((rc = read_flags(ctx, flags))) return rc;
     if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
-    if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded tensor-core wait gave up");
+    if (flags[3])
+        return set_err(ctx, SICP_ETIMEOUT, "a bounded wait on the GPU gave up (tensor-core search or Stein update)");
     if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
     if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
     if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;

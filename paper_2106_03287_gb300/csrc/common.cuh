@@ -267,6 +267,10 @@ struct SteinArgs {
     // the two blocks' medians of the previous iteration (in/out; 0: none) or
     // null: starts the median selection next to the previous median
     float* med_state;
+    // two arrival counters (one per block) and an error flag, or null: with
+    // them the update of each block is split over several CTAs (particles)
+    unsigned* arrive;
+    int* err;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);

@@ -1,7 +1,10 @@
 // Stein update + Adam (Eq. stein_icp_phi, the RBF kernels that follow it, and
 // Sec. V), plus the FP64 particle moments.  The translation and rotation
 // blocks are independent (own kernel, bandwidth, gradient and Adam
-// components), so the update runs as two CTAs of 1024 threads, one per block.
+// components), so each block has its own CTAs of 1024 threads: P of them
+// (P = ceil(K / 32), at most 32), each taking the Stein direction and the
+// Adam step of a share of the particles after computing the block's bandwidth
+// itself (the same value in every CTA).
 //
 // Per iteration, for K particles theta_j with mean ICP gradients gbar_j:
 //   G_j   = -N gbar_j + grad log prior(theta_j)          (Eq. posterior)
@@ -13,10 +16,16 @@
 // with a two-term 2 pi (Cody-Waite reduction), which avoids three transcendental
 // calls per pair.
 //
-// The medians are exact order statistics of the fp32 distances: a radix select
-// over their bit patterns (non-negative floats order like unsigned ints), with
-// the distances recomputed from shared-memory particles on every pass.
+// The medians are exact order statistics of the fp32 distances.  Within a
+// registration run the selection starts from the previous iteration's median:
+// one pass counts the distances below a bracket around it and bins those
+// inside; the two middle ranks are then found among the few values of their
+// bins.  Otherwise (first iteration, or a rank outside the bracket) a radix
+// select over the bit patterns (non-negative floats order like unsigned ints)
+// finds them.
 #include <float.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "stein_device.cuh"
@@ -26,8 +35,11 @@ namespace {
 
 using namespace sd;
 
-// CTA b updates block b (translation, rotation) of every particle.
-__global__ void __launch_bounds__(kThreads) k_stein_adam(SteinArgs a) { stein_adam_one_block(a, blockIdx.x); }
+// CTAs [b P, (b + 1) P) update block b (translation, rotation), CTA q of them
+// the particles [q Kq, (q + 1) Kq).
+__global__ void __launch_bounds__(kThreads) k_stein_adam(SteinArgs a, int P) {
+    stein_adam_one_block(a, blockIdx.x / P, blockIdx.x % P, P);
+}
 
 __global__ void k_moments(const float* __restrict__ th, int K, double* __restrict__ out) {
     __shared__ double mean[6];
@@ -53,11 +65,29 @@ cudaError_t kernel_attrs_init() {
     return cudaFuncSetAttribute(k_stein_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
+// CTAs per block: at most 32 particles each (one warp per particle), at most 32 CTAs.
+int stein_ctas_per_block(int32_t K) { return std::min(32, std::max(1, (K + 31) / 32)); }
+
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s) {
     const size_t pairs = (size_t)a.K * (a.K - 1) / 2;
     const size_t smem = sizeof(float) * (18 * (size_t)a.K + (pairs <= (size_t)kCacheFloats ? pairs : 0));
-    k_stein_adam<<<2, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    const int P = (a.arrive && a.err) ? stein_ctas_per_block(a.K) : 1;
+    if (P == 1) {
+        k_stein_adam<<<2, kThreads, smem, s>>>(a, 1);
+        return cudaGetLastError();
+    }
+    // the CTAs of a block wait for one another: all must be resident at once
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * P);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_stein_adam, a, P);
 }
 
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s) {

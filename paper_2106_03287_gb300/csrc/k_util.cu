@@ -152,27 +152,30 @@ unsigned grid_1d(int64_t n, int threads, int cap = 4096) {
     return (unsigned)b;
 }
 
-// gbar[j] = inv_m * (sum over k of qterms[j][k]) in a fixed order: one warp per
-// particle, lanes over the minibatch, then a fixed butterfly.  Clears the
-// fallback count for the next iteration.
-__global__ void k_qterms_to_gbar(const float* __restrict__ qterms, int K, int m, float inv_m, float* __restrict__ gbar,
-                                 int* fb_count) {
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && fb_count) *fb_count = 0;
-    if (j >= K) return;
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+// gbar[j] = inv_m * (sum over k of qterms[j][k]) in a fixed order.  CTA j
+// reads particle j's m x 6 terms as rows of 192 floats (32 minibatch entries
+// x 6 components, coalesced): thread (e, c) sums component c of entries
+// e, e + 32, ...; then warp c adds the 32 partial sums of component c with a
+// fixed butterfly.  Clears the fallback count for the next iteration.
+constexpr int kGbarThreads = 192;
+__global__ void __launch_bounds__(kGbarThreads) k_qterms_to_gbar(const float* __restrict__ qterms, int K, int m,
+                                                                 float inv_m, float* __restrict__ gbar, int* fb_count) {
+    __shared__ float part[6][33];
+    const int j = blockIdx.x, t = threadIdx.x;
+    if (j == 0 && t == 0 && fb_count) *fb_count = 0;
+    const int e = t / 6, c = t % 6;
     const float* row = qterms + (int64_t)j * m * 6;
-    for (int k = lane; k < m; k += 32)
+    float acc = 0.f;
+#pragma unroll 4
+    for (int k = e; k < m; k += 32) acc += __ldg(row + 6 * k + c);
+    part[c][e] = acc;
+    __syncthreads();
+    const int w = t >> 5, lane = t & 31;
+    if (w < 6) {
+        float v = part[w][lane];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += __ldg(row + 6 * k + c);
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-        for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-    if (lane < 6) {
-        float v = acc[0];
-#pragma unroll
-        for (int c = 1; c < 6; ++c) v = lane == c ? acc[c] : v;
-        gbar[6 * j + lane] = v * inv_m;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) gbar[6 * j + w] = v * inv_m;
     }
 }
 
@@ -201,7 +204,8 @@ cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, 
 
 cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
                                   cudaStream_t s) {
-    k_qterms_to_gbar<<<(K + 7) / 8, 256, 0, s>>>(qterms, K, m, inv_m, gbar, fb_count);
+    if (K <= 0) return cudaSuccess;
+    k_qterms_to_gbar<<<K, kGbarThreads, 0, s>>>(qterms, K, m, inv_m, gbar, fb_count);
     return cudaGetLastError();
 }
 

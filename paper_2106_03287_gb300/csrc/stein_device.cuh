@@ -67,11 +67,13 @@ __device__ __forceinline__ void for_each_pair(const Team& T, const float* D, boo
     }
 }
 
-// Exact value of rank `rank` (0-based) among the unique pair distances: radix
-// select over their bit patterns with 11-, 11- and 10-bit digits, counting
-// with one shared atomic per distinct bin per warp.
-__device__ unsigned select_rank(const Team& T, const float* D, bool cached, const float* th, int K, int block,
-                                unsigned rank, unsigned* hist, unsigned* s_u, unsigned* wsum) {
+// Exact value of rank `rank` (0-based) among non-negative floats: radix select
+// over their bit patterns with 11-, 11- and 10-bit digits, counting with one
+// shared atomic per distinct bin per warp.  visit(f) calls f(valid, value)
+// for every value, the same number of times on every thread of the team.
+template <class Visit>
+__device__ unsigned radix_select(const Team& T, Visit visit, unsigned rank, unsigned* hist, unsigned* s_u,
+                                 unsigned* wsum) {
     const int lane = threadIdx.x & 31, lt = threadIdx.x - T.t0, lw = lt >> 5;
     unsigned prefix = 0, mask = 0, rem = rank + 1;
     const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
@@ -79,7 +81,7 @@ __device__ unsigned select_rank(const Team& T, const float* D, bool cached, cons
         const int shift = shifts[pass], nb = 1 << widths[pass];
         for (int i = lt; i < nb; i += T.n) hist[i] = 0;
         team_sync(T);
-        for_each_pair(T, D, cached, th, K, block, [&](bool v, float x) {
+        visit([&](bool v, float x) {
             const unsigned b = __float_as_uint(x);
             const bool m = v && (b & mask) == prefix;
             const unsigned bin = m ? (b >> shift) & (unsigned)(nb - 1) : 0xffffffffu;
@@ -134,56 +136,130 @@ __device__ unsigned select_rank(const Team& T, const float* D, bool cached, cons
     return prefix;
 }
 
-constexpr int kBracketMax = 1024;   // values the warm start selects among
+// Rank `rank` among the unique pair distances of one block.
+__device__ unsigned select_rank(const Team& T, const float* D, bool cached, const float* th, int K, int block,
+                                unsigned rank, unsigned* hist, unsigned* s_u, unsigned* wsum) {
+    return radix_select(
+        T, [&](auto f) { for_each_pair(T, D, cached, th, K, block, f); }, rank, hist, s_u, wsum);
+}
+
+constexpr float kBracketRel = 0.25f;   // half-width of the bracket, relative to the previous median
+constexpr int kBins = 2048;            // linear bins over the bracket
+constexpr int kBinMax = 1024;          // values of one target bin ranked directly
 
 // Warm start of the selection: the unique-pair distances of unique ranks
-// u[0], u[1] (cached in D, n of them) are looked for among the values within
-// 1/32 relative of m_prev, the previous iteration's median.  True, with the
-// two values in v[], when both ranks fall inside that bracket and it holds at
-// most kBracketMax values; the caller takes the full selection otherwise.
-// Exact either way: the values found are the same order statistics.
+// u[0] <= u[1] (cached in D, n of them) are looked for in the bracket
+// [lo, hi] = m_prev * (1 -+ kBracketRel) around the previous iteration's
+// median.  One pass counts the values below lo and sorts those inside into
+// kBins linear bins of the bracket; bin(x) = floor((x - lo) * kBins / (hi -
+// lo)) is monotone in x in floating point, so a lower bin holds only smaller
+// values.  A scan of the bin counts gives the bin of each target rank and its
+// rank inside the bin; the values of that bin are then ranked directly.  True,
+// with the two values in v[], when both ranks fall inside the bracket and each
+// target bin holds at most kBinMax values; the caller takes the full selection
+// otherwise.  Exact either way: the values found are the same order statistics.
 __device__ bool bracket_select(const Team& T, const float* D, int n, const unsigned u[2], float m_prev, float* C,
-                               unsigned* s_u, float v[2]) {
-    const int lane = threadIdx.x & 31, lt = threadIdx.x - T.t0;
-    const float lo = m_prev * (1.f - 1.f / 32.f), hi = m_prev * (1.f + 1.f / 32.f);
-    if (lt == 0) {
-        s_u[0] = 0;   // values below the bracket
-        s_u[1] = 0;   // values inside it
-    }
+                               unsigned* hist, unsigned* s_u, unsigned* wsum, float v[2]) {
+    const int lane = threadIdx.x & 31, lt = threadIdx.x - T.t0, lw = lt >> 5;
+    const float lo = m_prev * (1.f - kBracketRel), hi = m_prev * (1.f + kBracketRel);
+    const float scale = (float)kBins / (hi - lo);
+    auto bin_of = [&](float x) { return min(kBins - 1, (int)((x - lo) * scale)); };
+    for (int b = lt; b < kBins; b += T.n) hist[b] = 0;
+    if (lt == 0) s_u[0] = 0;   // values below the bracket
     team_sync(T);
     for (int base = 0; base < n; base += T.n) {
         const int p = base + lt;
         const float x = p < n ? D[p] : FLT_MAX;
         const unsigned below = __ballot_sync(0xffffffffu, p < n && x < lo);
-        const bool in = p < n && x >= lo && x <= hi;
-        const unsigned inm = __ballot_sync(0xffffffffu, in);
-        unsigned at = 0;
-        if (lane == 0) {
-            if (below) atomicAdd(&s_u[0], (unsigned)__popc(below));
-            if (inm) at = atomicAdd(&s_u[1], (unsigned)__popc(inm));
-        }
-        at = __shfl_sync(0xffffffffu, at, 0) + __popc(inm & ((1u << lane) - 1u));
-        if (in && at < (unsigned)kBracketMax) C[at] = x;
+        if (lane == 0 && below) atomicAdd(&s_u[0], (unsigned)__popc(below));
+        if (p < n && x >= lo && x <= hi) atomicAdd(&hist[bin_of(x)], 1u);
     }
     team_sync(T);
-    const unsigned c_lt = s_u[0], nc = s_u[1];
-    const bool ok = nc <= (unsigned)kBracketMax && u[0] >= c_lt && u[1] < c_lt + nc;
-    team_sync(T);
-    if (!ok) return false;
-    // rank of each bracketed value (ties by position: a permutation of 0 .. nc-1)
-    for (int i = lt; i < (int)nc; i += T.n) {
-        const float x = C[i];
-        unsigned r = c_lt;
-        for (int j = 0; j < (int)nc; ++j) {
-            const float y = C[j];
-            r += (y < x) || (y == x && j < i);
-        }
-        if (r == u[0]) s_u[2] = __float_as_uint(x);
-        if (r == u[1]) s_u[3] = __float_as_uint(x);
+    const unsigned c_lt = s_u[0];
+    // team-wide scan of the bin counts: thread lt owns bins [lt*per, lt*per + per)
+    const int per = kBins / T.n;
+    unsigned tot = 0;
+    for (int q = 0; q < per; ++q) tot += hist[lt * per + q];
+    unsigned incl = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned x = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += x;
+    }
+    if (lane == 31) wsum[lw] = incl;
+    if (lt == 0) {
+        s_u[1] = 0xffffffffu;   // bin of u[0] (none yet)
+        s_u[3] = 0xffffffffu;   // bin of u[1]
     }
     team_sync(T);
-    v[0] = __uint_as_float(s_u[2]);
-    v[1] = __uint_as_float(s_u[3]);
+    if (lw == 0) {
+        const unsigned x = lane < (T.n >> 5) ? wsum[lane] : 0u;
+        unsigned xi = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += y;
+        }
+        if (lane < (T.n >> 5)) wsum[lane] = xi - x;
+    }
+    team_sync(T);
+    {
+        unsigned acc = c_lt + wsum[lw] + incl - tot;   // values below this thread's first bin
+        for (int q = 0; q < per; ++q) {
+            const unsigned c = hist[lt * per + q];
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+                if (acc <= u[w] && u[w] < acc + c) {
+                    s_u[1 + 2 * w] = (unsigned)(lt * per + q);
+                    s_u[2 + 2 * w] = u[w] - acc;
+                }
+            acc += c;
+        }
+    }
+    team_sync(T);
+    const unsigned b0 = s_u[1], r0 = s_u[2], b1 = s_u[3], r1 = s_u[4];
+    const bool found = b0 != 0xffffffffu && b1 != 0xffffffffu && hist[b0] <= (unsigned)kBinMax &&
+                       hist[b1] <= (unsigned)kBinMax;
+    team_sync(T);
+    if (!found) return false;
+    // gather the values of the target bins (C[0 ..) for b0, C[kBinMax ..) for b1)
+    if (lt == 0) {
+        s_u[5] = 0;
+        s_u[6] = 0;
+    }
+    team_sync(T);
+    for (int base = 0; base < n; base += T.n) {
+        const int p = base + lt;
+        if (p < n) {
+            const float x = D[p];
+            if (x >= lo && x <= hi) {
+                const unsigned b = (unsigned)bin_of(x);
+                if (b == b0) C[atomicAdd(&s_u[5], 1u)] = x;
+                if (b == b1 && b1 != b0) C[kBinMax + atomicAdd(&s_u[6], 1u)] = x;
+            }
+        }
+    }
+    team_sync(T);
+    const unsigned e0 = s_u[5], e1 = b1 != b0 ? s_u[6] : e0;
+    const float* E1 = b1 != b0 ? C + kBinMax : C;
+    const unsigned rr[2] = {r0, r1};
+    // value of local rank r in a bin: the x with #(< x) <= r < #(<= x)
+    for (int w = 0; w < 2; ++w) {
+        const float* E = w ? E1 : C;
+        const unsigned e = w ? e1 : e0;
+        for (int i = lt; i < (int)e; i += T.n) {
+            const float x = E[i];
+            unsigned less = 0, leq = 0;
+            for (int k = 0; k < (int)e; ++k) {
+                less += E[k] < x;
+                leq += E[k] <= x;
+            }
+            if (less <= rr[w] && rr[w] < leq) s_u[7 + w] = __float_as_uint(x);
+        }
+    }
+    team_sync(T);
+    v[0] = __uint_as_float(s_u[7]);
+    v[1] = __uint_as_float(s_u[8]);
     team_sync(T);
     return true;
 }
@@ -199,10 +275,11 @@ __device__ float bandwidth(const Team& T, const float* th, int K, int block, flo
     if (K < 2) return 1.f;
     const int lt = threadIdx.x - T.t0;
     if (cached) {
-        const int n = K * K;
-        for (int p = lt; p < n; p += T.n) {
-            const int j = p / K, l = p % K;
-            if (j < l) D[j * K - j * (j + 1) / 2 + (l - j - 1)] = pair_d2(th, j, l, block);
+        // unique pairs j < l, row by row: warp w of the team takes rows w, w + warps, ...
+        const int lane = threadIdx.x & 31, warps = T.n >> 5;
+        for (int j = lt >> 5; j < K - 1; j += warps) {
+            const int row = j * K - j * (j + 1) / 2 - j - 1;   // D index of (j, l) is row + l
+            for (int l = j + 1 + lane; l < K; l += 32) D[row + l] = pair_d2(th, j, l, block);
         }
         team_sync(T);
     }
@@ -212,7 +289,7 @@ __device__ float bandwidth(const Team& T, const float* th, int K, int block, flo
         // full-multiset rank r >= K is unique rank (r - K) / 2
         const unsigned u[2] = {(r_lo - uK) / 2, (r_hi - uK) / 2};
         float v[2];
-        if (bracket_select(T, D, K * (K - 1) / 2, u, m_prev, C, s_u, v)) {
+        if (bracket_select(T, D, K * (K - 1) / 2, u, m_prev, C, hist, s_u, wsum, v)) {
             const float med = r_hi != r_lo ? 0.5f * (v[0] + v[1]) : v[0];
             if (med_out) *med_out = med;
             return med > 0.f ? med / logf((float)K + 1.f) : 1.f;
@@ -366,26 +443,38 @@ __device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
     }
 }
 
+constexpr long long kArriveSpins = 1ll << 22;   // ~0.3 s of 64 ns polls
+
 // The same update for one block only (b = 0: translation x, y, z; b = 1:
-// rotation), by the whole CTA: the two blocks share nothing (each has its own
-// kernel, bandwidth, gradient components and Adam components), so two CTAs
-// can take them on two SMs.  Same arithmetic and summation order as
-// stein_adam_block, so the results are bit-identical.
-__device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) {
+// rotation), by CTA q of P: the two blocks share nothing (each has its own
+// kernel, bandwidth, gradient components and Adam components), and within a
+// block CTA q takes the Stein direction and the Adam step of particles
+// [q Kq, (q + 1) Kq), Kq = ceil(K / P).  Every CTA of the block computes the
+// same bandwidth from all particles (identical arithmetic), so they exchange
+// nothing but one arrival: a CTA writes theta only after all P CTAs of its
+// block have read it (a.arrive[b] counts arrivals; bounded wait, a.err set on
+// timeout, and then nothing is written).  P > 1 needs all CTAs co-resident
+// (cooperative launch).
+__device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, int q, int P) {
     extern __shared__ float sm[];
     float* th = sm;               // K x 6 (all components: pair_d2 indexes the full rows)
     float* G = sm + 6 * a.K;      // K x 6, columns 3b..3b+2 used
-    float* Ph = sm + 12 * a.K;    // K x 6, columns 3b..3b+2 used
+    float* Ph = sm + 12 * a.K;    // K x 6, columns 3b..3b+2 of this CTA's particles used
     float* D = sm + 18 * a.K;     // unique pair distances of block b when they fit
     __shared__ unsigned hist[2048];
-    __shared__ unsigned s_u[4];
+    __shared__ unsigned s_u[9];
     __shared__ unsigned wsum[32];
-    __shared__ float bracket[kBracketMax];
+    __shared__ float bracket[2 * kBinMax];
+    __shared__ unsigned s_target;
+    __shared__ int s_fail;
     const int K = a.K, tid = threadIdx.x;
     const int pairs = K * (K - 1) / 2;
     const bool cached = pairs <= kCacheFloats;
     const int c0 = 3 * b;
+    const int Kq = (K + P - 1) / P, i0 = min(K, q * Kq), i1 = min(K, i0 + Kq);
 
+    const float m_prev = a.med_state ? a.med_state[b] : 0.f;   // read before the arrival below
+    if (tid == 0) s_fail = 0;
     for (int idx = tid; idx < 6 * K; idx += blockDim.x) th[idx] = a.theta[idx];
     if (a.chunks == 1) {
         for (int e = tid; e < 3 * K; e += blockDim.x) {
@@ -412,27 +501,26 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) 
         }
     }
     __syncthreads();
+    if (P > 1 && tid == 0) s_target = (atomicAdd(a.arrive + b, 1u) / (unsigned)P + 1u) * (unsigned)P;
 
     const Team T = {0, (int)blockDim.x, 1};
-    const float m_prev = a.med_state ? a.med_state[b] : 0.f;
     float med = 0.f;
     const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum, m_prev, bracket, &med);
-    if (tid == 0 && a.out_h) a.out_h[b] = h;
-    if (tid == 0 && a.med_state) a.med_state[b] = med;
     const float inv_h = 1.f / h, two_h = 2.f / h;
 
+    // S lanes per particle (power of two <= 32), each summing over j = lane (mod S)
     int S = 32;
-    while (S > 1 && K * S > (int)blockDim.x) S >>= 1;
+    while (S > 1 && Kq * S > (int)blockDim.x) S >>= 1;
     const int groups = blockDim.x / S;
     const int g_id = tid / S, g_lane = tid % S;
-    const int rounds = (K + groups - 1) / groups;
+    const int rounds = (i1 - i0 + groups - 1) / groups;
     const float invK = 1.f / (float)K;
     const float omb1 = 1.f - a.beta1, omb2 = 1.f - a.beta2;
     const float c1 = -expm1f((float)a.t * log1pf(-omb1));
     const float c2 = -expm1f((float)a.t * log1pf(-omb2));
     for (int r = 0; r < rounds; ++r) {
-        const int i = r * groups + g_id;
-        const bool valid = i < K;
+        const int i = i0 + r * groups + g_id;
+        const bool valid = i < i1;
         float acc[3] = {0.f, 0.f, 0.f};
         if (valid) {
             const float* ti = th + 6 * i + c0;
@@ -459,7 +547,31 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b) 
         }
     }
     __syncthreads();
-    for (int e = tid; e < 3 * K; e += blockDim.x) {
+    if (P > 1) {
+        // every CTA of the block has read theta (and the previous median) once all have arrived
+        if (tid == 0) {
+            const unsigned target = s_target;
+            long long spins = 0;
+            for (;;) {
+                unsigned now;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(a.arrive + b) : "memory");
+                if ((int)(now - target) >= 0) break;
+                if (++spins > kArriveSpins) {
+                    s_fail = 1;
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        if (s_fail) return;
+    }
+    if (q == 0 && tid == 0) {
+        if (a.out_h) a.out_h[b] = h;
+        if (a.med_state) a.med_state[b] = med;
+    }
+    for (int e = 3 * i0 + tid; e < 3 * i1; e += blockDim.x) {
         const int idx = 6 * (e / 3) + c0 + e % 3;
         const float phi = Ph[idx];
         if (a.out_phi) a.out_phi[idx] = phi;
