@@ -223,6 +223,7 @@ SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, c
     a.med_state = nullptr;
     a.arrive = nullptr;
     a.err = nullptr;
+    a.gen = 0;
     return a;
 }
 
@@ -565,6 +566,7 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
     a.out_h = hh;
     a.arrive = (unsigned*)(hh + 2);
     a.err = (int*)ctx->flags.p + 3;
+    a.gen = 1;
     SICP_CUDA(cudaMemsetAsync(a.arrive, 0, 2 * sizeof(unsigned), ctx->stream));
     SICP_CUDA(launch_stein_adam(a, ctx->stream));
     if ((rc = read_flags(ctx, flags))) return rc;
@@ -752,6 +754,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
             a.med_state = med_state;
             a.arrive = (unsigned*)(med_state + 2);
             a.err = (int*)ctx->flags.p + 3;
+            a.gen = (uint32_t)(t + 1);
             SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;

@@ -268,9 +268,11 @@ struct SteinArgs {
     // null: starts the median selection next to the previous median
     float* med_state;
     // two arrival counters (one per block) and an error flag, or null: with
-    // them the update of each block is split over several CTAs (particles)
+    // them the update of each block is split over several CTAs (particles).
+    // gen: 1-based count of such updates since the counters were zeroed.
     unsigned* arrive;
     int* err;
+    uint32_t gen;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);

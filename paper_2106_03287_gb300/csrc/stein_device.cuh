@@ -452,8 +452,9 @@ constexpr long long kArriveSpins = 1ll << 22;   // ~0.3 s of 64 ns polls
 // [q Kq, (q + 1) Kq), Kq = ceil(K / P).  Every CTA of the block computes the
 // same bandwidth from all particles (identical arithmetic), so they exchange
 // nothing but one arrival: a CTA writes theta only after all P CTAs of its
-// block have read it (a.arrive[b] counts arrivals; bounded wait, a.err set on
-// timeout, and then nothing is written).  P > 1 needs all CTAs co-resident
+// block have read it (a.arrive[b] counts arrivals, a.gen * P of them by the end
+// of update a.gen; bounded wait, a.err set on timeout, and then nothing is
+// written).  P > 1 needs all CTAs co-resident
 // (cooperative launch).
 __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, int q, int P) {
     extern __shared__ float sm[];
@@ -465,7 +466,6 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     __shared__ unsigned s_u[9];
     __shared__ unsigned wsum[32];
     __shared__ float bracket[2 * kBinMax];
-    __shared__ unsigned s_target;
     __shared__ int s_fail;
     const int K = a.K, tid = threadIdx.x;
     const int pairs = K * (K - 1) / 2;
@@ -501,7 +501,7 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
         }
     }
     __syncthreads();
-    if (P > 1 && tid == 0) s_target = (atomicAdd(a.arrive + b, 1u) / (unsigned)P + 1u) * (unsigned)P;
+    if (P > 1 && tid == 0) atomicAdd(a.arrive + b, 1u);   // this CTA has read theta
 
     const Team T = {0, (int)blockDim.x, 1};
     float med = 0.f;
@@ -550,7 +550,7 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     if (P > 1) {
         // every CTA of the block has read theta (and the previous median) once all have arrived
         if (tid == 0) {
-            const unsigned target = s_target;
+            const unsigned target = a.gen * (unsigned)P;
             long long spins = 0;
             for (;;) {
                 unsigned now;
