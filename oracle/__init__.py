@@ -80,6 +80,7 @@ def _setup(L):
         "or_stein_phi": (None, [_p, _p, _i32, _f64, _f64, _p]),
         "or_adam": (None, [_p, _p, _p, _p, _i64, _i64, _f64, _f64, _f64, _f64]),
         "or_moments": (None, [_p, _i32, _p, _p]),
+        "or_moments_circular": (None, [_p, _i32, _p, _p]),
         "or_step": (None, [_p, _i64, _p, _i64, _p, _p, _p, _i32, _p, _i64, _p, _p, _p, _p]),
         "or_register": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _p, _p, _p, _p]),
         "or_num_threads": (ctypes.c_int, []),
@@ -253,6 +254,16 @@ def moments(theta):
     mean = np.empty(6)
     cov = np.empty(36)
     _L().or_moments(_ptr(th), th.shape[0], _ptr(mean), _ptr(cov))
+    return mean, cov.reshape(6, 6)
+
+
+def moments_circular(theta):
+    """Mean and covariance with circular statistics for the three angles
+    (reading R13 of oracle.c)."""
+    th = _f64a(theta).reshape(-1, 6)
+    mean = np.empty(6)
+    cov = np.empty(36)
+    _L().or_moments_circular(_ptr(th), th.shape[0], _ptr(mean), _ptr(cov))
     return mean, cov.reshape(6, 6)
 
 

@@ -36,6 +36,11 @@
  *      in ascending index order.
  *  R12 correspondence ties go to the lowest reference index; distances are
  *      the exact sum of squared differences.
+ *  R13 circular moments (for rotation blocks whose particles straddle +-pi):
+ *      each angle's mean is the circular mean atan2(sum sin, sum cos) (0 if
+ *      both sums vanish); the covariance is that of the deviations
+ *      [theta_t - mean_t ; wrap(theta_r - mean_r)], divisor K-1 (0 for K = 1).
+ *      Translations keep the arithmetic mean.
  */
 #include <math.h>
 #include <stdint.h>
@@ -391,6 +396,36 @@ OR_EXPORT void or_moments(const double* th, int32_t K, double mean[6], double co
         for (int b = 0; b < 6; ++b) {
             double s = 0.0;
             for (int32_t j = 0; j < K; ++j) s += (th[6 * j + a] - mean[a]) * (th[6 * j + b] - mean[b]);
+            cov[6 * a + b] = (K > 1) ? s / (double)(K - 1) : 0.0;
+        }
+}
+
+/* Circular moments (R13): translation as or_moments, rotation angles by their
+ * circular mean, covariance of the wrapped deviations. */
+OR_EXPORT void or_moments_circular(const double* th, int32_t K, double mean[6], double cov[36]) {
+    for (int a = 0; a < 6; ++a) {
+        if (a < 3) {
+            double s = 0.0;
+            for (int32_t j = 0; j < K; ++j) s += th[6 * j + a];
+            mean[a] = s / (double)K;
+        } else {
+            double ss = 0.0, sc = 0.0;
+            for (int32_t j = 0; j < K; ++j) {
+                ss += sin(th[6 * j + a]);
+                sc += cos(th[6 * j + a]);
+            }
+            mean[a] = (ss == 0.0 && sc == 0.0) ? 0.0 : atan2(ss, sc);
+        }
+    }
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) {
+            double s = 0.0;
+            for (int32_t j = 0; j < K; ++j) {
+                double da = th[6 * j + a] - mean[a], db = th[6 * j + b] - mean[b];
+                if (a >= 3) da = or_wrap(da);
+                if (b >= 3) db = or_wrap(db);
+                s += da * db;
+            }
             cov[6 * a + b] = (K > 1) ? s / (double)(K - 1) : 0.0;
         }
 }

@@ -290,6 +290,45 @@ def test_svgd_recovers_a_gaussian_target():
     assert np.all((ratio > 0.9) & (ratio < 1.1)), ratio
 
 
+def _circ_mean_resultant(a):
+    return abs(np.mean(np.exp(1j * a)))
+
+
+def test_svgd_with_the_priors_recovers_gaussian_and_von_mises():
+    """With no data (gbar = 0) and prior = 1, G is the gradient of the log
+    prior alone (Eqs. trans_prior, rot_prior), so SVGD must transport the
+    particles to the prior itself: N(mu, sigma) per translation axis (sigma
+    read as the variance) and von Mises(mu, kappa) per angle, whose mean
+    resultant length is I1(kappa)/I0(kappa).  One angle's mean sits next to
+    +-pi, so the particles straddle the cut."""
+    special = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(1)
+    K = 200
+    mu = np.array([0.3, -0.2, 0.1, 3.0, -0.4, 0.2])
+    var = np.array([0.0025, 0.01, 0.0004])
+    kappa = np.array([20.0, 50.0, 8.0])
+    th = np.ascontiguousarray(rng.uniform(-0.5, 0.5, (K, 6)))
+    th[:, 3] += 3.0
+    mom, vel = np.zeros_like(th), np.zeros_like(th)
+    for t in range(1, 1201):
+        G = O.log_post_grad(th, np.zeros_like(th), 1000, 1, mu, var, kappa)
+        phi = O.stein_phi(th, G, *O.bandwidths(th))
+        O.adam(th, mom, vel, -phi, t, 0.01)
+    sd = np.sqrt(var)
+    assert np.all(np.abs(th[:, :3].mean(0) - mu[:3]) < 2 * sd / math.sqrt(K))
+    ratio = th[:, :3].std(0, ddof=1) / sd
+    assert np.all((ratio > 0.9) & (ratio < 1.1)), ratio
+    mean_c, _ = O.moments_circular(th)
+    circ_sd = 1.0 / np.sqrt(kappa)
+    dmu = np.angle(np.exp(1j * (mean_c[3:] - mu[3:])))
+    assert np.all(np.abs(dmu) < 2 * circ_sd / math.sqrt(K)), dmu
+    R = np.array([_circ_mean_resultant(th[:, 3 + a]) for a in range(3)])
+    A = special.i1(kappa) / special.i0(kappa)
+    # circular spread sqrt(-2 ln R) against the target's, within 10%
+    spread = np.sqrt(-2 * np.log(R)) / np.sqrt(-2 * np.log(A))
+    assert np.all((spread > 0.9) & (spread < 1.1)), spread
+
+
 # ---------------------------------------------------------------- Adam
 
 def test_adam_constant_gradient_closed_form():
@@ -313,6 +352,54 @@ def test_moments_match_numpy():
     assert np.allclose(cov, np.cov(th.T), atol=1e-14)
     m1, c1 = O.moments(th[:1])
     assert np.array_equal(m1, th[0]) and np.all(c1 == 0)
+
+
+def test_circular_moments_two_angles_across_pi():
+    # the circular mean of pi - 0.1 and -pi + 0.1 is pi (the arithmetic mean is 0);
+    # the wrapped deviations are -0.1 and +0.1, so the variance is 0.02
+    th = np.zeros((2, 6))
+    th[:, 4] = [math.pi - 0.1, -math.pi + 0.1]
+    mean, cov = O.moments_circular(th)
+    assert abs(abs(mean[4]) - math.pi) < 1e-15
+    assert abs(cov[4, 4] - 0.02) < 1e-15
+    assert np.count_nonzero(cov) == 1 and np.all(mean[[0, 1, 2, 3, 5]] == 0)
+    m_lin, c_lin = O.moments(th)
+    assert m_lin[4] == 0 and abs(c_lin[4, 4] - (2 * math.pi - 0.2) ** 2 / 2) < 1e-12   # plain: across the circle
+
+
+@pytest.mark.parametrize("centre", [0.3, math.pi, -2.5])
+def test_circular_moments_symmetric_samples(centre):
+    """Angles c +- d_i (so their circular mean is c), each shifted by a random
+    multiple of 2 pi: the mean is c mod 2 pi, and the covariance is that of
+    [t, d] computed directly."""
+    rng = np.random.default_rng(4)
+    n = 40
+    dev = rng.normal(0, 0.3, (n, 3))
+    t = rng.normal(0, 0.1, (2 * n, 3))
+    rot = np.concatenate([centre + dev, centre - dev])
+    rot += 2 * math.pi * rng.integers(-3, 4, rot.shape)
+    th = np.concatenate([t, rot], axis=1)
+    mean, cov = O.moments_circular(th)
+    assert np.allclose(mean[:3], t.mean(0), atol=1e-15)
+    assert np.all(np.abs(np.angle(np.exp(1j * (mean[3:] - centre)))) < 1e-13)
+    direct = np.cov(np.concatenate([t, np.concatenate([dev, -dev])], axis=1).T)
+    assert np.allclose(cov, direct, atol=1e-13)
+
+
+def test_circular_moments_shift_equivariance_and_single_particle():
+    rng = np.random.default_rng(5)
+    th = np.c_[rng.normal(0, 0.1, (50, 3)), rng.uniform(-math.pi, math.pi, (50, 3))]
+    th[:, 3:] = 0.8 + 0.4 * np.tanh(th[:, 3:])      # a cluster of angles
+    mean, cov = O.moments_circular(th)
+    sh = th.copy()
+    sh[:, 3:] += 2.9                                # moves the cluster across +-pi
+    mean2, cov2 = O.moments_circular(sh)
+    assert np.all(np.abs(np.angle(np.exp(1j * (mean2[3:] - mean[3:] - 2.9)))) < 1e-13)
+    assert np.allclose(cov2, cov, atol=1e-13) and np.allclose(mean2[:3], mean[:3], atol=1e-15)
+    one = np.array([[0.1, 0.2, 0.3, 7.0, -4.0, 0.5]])
+    m1, c1 = O.moments_circular(one)
+    assert np.allclose(m1, [0.1, 0.2, 0.3, 7.0 - 2 * math.pi, -4.0 + 2 * math.pi, 0.5], atol=1e-15)
+    assert np.all(c1 == 0)
 
 
 def test_single_particle_recovers_known_pose_noise_free():
