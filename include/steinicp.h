@@ -220,6 +220,19 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
 int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
                  int on_device);
 
+/* The same moments with circular statistics for the three angles, for
+ * particle sets whose rotations straddle +-pi (the plain mean of angles near
+ * pi and -pi lands near 0).  Mean of angle a: atan2(sum_j sin theta_j,a,
+ * sum_j cos theta_j,a), 0 when both sums vanish; covariance [6][6] of the
+ * deviations [theta_t - mean_t ; wrap(theta_r - mean_r)], wrap(x) =
+ * atan2(sin x, cos x), divisor K-1 (zero for K = 1); translations as
+ * sicp_moments.  The paper uses the particles' mean and covariance
+ * downstream (the odometry subsection of the experiments) and gives no
+ * formula for angles; this is the standard circular mean.  Float64
+ * throughout.  Errors: SICP_EINVAL (K < 1). */
+int sicp_moments_circular(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
+                          int on_device);
+
 /* ---- allocation-free variant ---- */
 
 /* The mean ICP gradient of sicp_icp_grad with SICP_NN_BRUTE_FP32, for

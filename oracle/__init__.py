@@ -259,7 +259,7 @@ def moments(theta):
 
 def moments_circular(theta):
     """Mean and covariance with circular statistics for the three angles
-    (reading R13 of oracle.c)."""
+    (reading R15 of oracle.c)."""
     th = _f64a(theta).reshape(-1, 6)
     mean = np.empty(6)
     cov = np.empty(36)

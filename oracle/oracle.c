@@ -36,7 +36,7 @@
  *      in ascending index order.
  *  R12 correspondence ties go to the lowest reference index; distances are
  *      the exact sum of squared differences.
- *  R13 circular moments (for rotation blocks whose particles straddle +-pi):
+ *  R15 circular moments (for rotation blocks whose particles straddle +-pi):
  *      each angle's mean is the circular mean atan2(sum sin, sum cos) (0 if
  *      both sums vanish); the covariance is that of the deviations
  *      [theta_t - mean_t ; wrap(theta_r - mean_r)], divisor K-1 (0 for K = 1).
@@ -400,7 +400,7 @@ OR_EXPORT void or_moments(const double* th, int32_t K, double mean[6], double co
         }
 }
 
-/* Circular moments (R13): translation as or_moments, rotation angles by their
+/* Circular moments (R15): translation as or_moments, rotation angles by their
  * circular mean, covariance of the wrapped deviations. */
 OR_EXPORT void or_moments_circular(const double* th, int32_t K, double mean[6], double cov[36]) {
     for (int a = 0; a < 6; ++a) {

@@ -5,7 +5,8 @@ from .binding import (  # noqa: F401
     EXPORTS, SICP_EINVAL, SICP_ENOMEM, SICP_ENOREF, SICP_ENOSURROGATE, SICP_ECUDA, SICP_ETIMEOUT,
     SICP_NN_BRUTE_BF16, SICP_NN_BRUTE_FP32, SICP_NN_GRID, SICP_NN_SURROGATE, SICP_OK, SicpError,
     LIB_PATH, lib, sicp_create, sicp_default_params, sicp_destroy, sicp_icp_grad, sicp_last_error,
-    sicp_minibatch, sicp_moments, sicp_nn, sicp_params, sicp_profile, sicp_register, sicp_set_reference,
+    sicp_minibatch, sicp_moments, sicp_moments_circular, sicp_nn, sicp_params, sicp_profile, sicp_register,
+    sicp_set_reference,
     sicp_stats, sicp_stein_adam, sicp_icp_grad_noalloc, sicp_register_batched, sicp_autotune_batched, pack_batch,
     SURROGATE_NPARAM, sicp_surrogate_train, sicp_surrogate_params, sicp_surrogate_loss_grad, sicp_surrogate_infer,
     sicp_register_continue, sicp_surrogate_save, sicp_surrogate_load,

@@ -38,7 +38,7 @@ _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 # Every C entry point declared in include/steinicp.h.
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
-    "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
+    "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments", "sicp_moments_circular",
     "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "sicp_icp_grad": (ctypes.c_int, [P, P, I64, P, I32, P, I32, I32, P, P, ctypes.c_int]),
             "sicp_stein_adam": (ctypes.c_int, [P, P, P, P, P, I32, I64, I64, pp, P, P, ctypes.c_int]),
             "sicp_moments": (ctypes.c_int, [P, P, I32, P, P, ctypes.c_int]),
+            "sicp_moments_circular": (ctypes.c_int, [P, P, I32, P, P, ctypes.c_int]),
             "sicp_stats": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_profile": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_icp_grad_noalloc": (ctypes.c_int, [P, I64, P, I64, P, I32, P, I32, P, P]),
@@ -278,6 +279,16 @@ def sicp_moments(ctx, particles):
     cov = _empty(particles, (6, 6), np.float64)
     _check(ctx, lib().sicp_moments(ctx, _ptr(particles, np.float32), particles.shape[0], _ptr(mean, np.float64),
                                    _ptr(cov, np.float64), _on_device(particles)))
+    return mean, cov
+
+
+def sicp_moments_circular(ctx, particles):
+    """Mean [6] and covariance [6][6] with circular statistics for the angles."""
+    particles = _host(particles, np.float32)
+    mean = _empty(particles, (6,), np.float64)
+    cov = _empty(particles, (6, 6), np.float64)
+    _check(ctx, lib().sicp_moments_circular(ctx, _ptr(particles, np.float32), particles.shape[0],
+                                            _ptr(mean, np.float64), _ptr(cov, np.float64), _on_device(particles)))
     return mean, cov
 
 

@@ -580,7 +580,12 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
     return sync(ctx);
 }
 
-int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36, int on_device) {
+}  // extern "C"
+
+namespace {
+
+int moments_entry(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36, int on_device,
+                  bool circular) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!particles || K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "moments needs 1 <= K <= %d", kMaxK);
@@ -589,10 +594,26 @@ int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6
     int rc = stage_in(ctx, particles, sizeof(float) * 6 * K, on_device, ctx->tmp_in, &d_th);
     if (rc) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
-    SICP_CUDA(launch_moments((const float*)d_th, K, (double*)ctx->moments.p, ctx->stream));
+    if (circular)
+        SICP_CUDA(launch_moments_circular((const float*)d_th, K, (double*)ctx->moments.p, ctx->stream));
+    else
+        SICP_CUDA(launch_moments((const float*)d_th, K, (double*)ctx->moments.p, ctx->stream));
     if ((rc = copy_out(ctx, mean6, ctx->moments.p, 6 * sizeof(double), on_device))) return rc;
     if ((rc = copy_out(ctx, cov36, (double*)ctx->moments.p + 6, 36 * sizeof(double), on_device))) return rc;
     return sync(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36, int on_device) {
+    return moments_entry(ctx, particles, K, mean6, cov36, on_device, false);
+}
+
+int sicp_moments_circular(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
+                          int on_device) {
+    return moments_entry(ctx, particles, K, mean6, cov36, on_device, true);
 }
 
 }  // extern "C"

@@ -276,6 +276,7 @@ struct SteinArgs {
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);
+cudaError_t launch_moments_circular(const float* theta, int32_t K, double* out42, cudaStream_t s);
 
 // Learned closest-point field (k_mlp.cu)
 cudaError_t surrogate_kernel_attrs();

@@ -59,6 +59,43 @@ __global__ void k_moments(const float* __restrict__ th, int K, double* __restric
     if (tid < 6) out[tid] = mean[tid];
 }
 
+// The same with circular statistics for the three angles: the mean of angle
+// a is atan2(sum sin, sum cos) (0 when both sums vanish), and the covariance
+// is that of [theta_t - mean_t ; wrap(theta_r - mean_r)], wrap(x) = atan2(sin
+// x, cos x), for particles whose angles straddle +-pi.
+__device__ __forceinline__ double wrap_d(double x) { return atan2(sin(x), cos(x)); }
+
+__global__ void k_moments_circular(const float* __restrict__ th, int K, double* __restrict__ out) {
+    __shared__ double mean[6];
+    const int tid = threadIdx.x;
+    if (tid < 3) {
+        double s = 0.0;
+        for (int j = 0; j < K; ++j) s += (double)th[6 * j + tid];
+        mean[tid] = s / (double)K;
+    } else if (tid < 6) {
+        double ss = 0.0, sc = 0.0;
+        for (int j = 0; j < K; ++j) {
+            const double x = (double)th[6 * j + tid];
+            ss += sin(x);
+            sc += cos(x);
+        }
+        mean[tid] = (ss == 0.0 && sc == 0.0) ? 0.0 : atan2(ss, sc);
+    }
+    __syncthreads();
+    if (tid < 36) {
+        const int a = tid / 6, b = tid % 6;
+        double s = 0.0;
+        for (int j = 0; j < K; ++j) {
+            double da = (double)th[6 * j + a] - mean[a], db = (double)th[6 * j + b] - mean[b];
+            if (a >= 3) da = wrap_d(da);
+            if (b >= 3) db = wrap_d(db);
+            s += da * db;
+        }
+        out[6 + tid] = (K > 1) ? s / (double)(K - 1) : 0.0;
+    }
+    if (tid < 6) out[tid] = mean[tid];
+}
+
 }  // namespace
 
 cudaError_t kernel_attrs_init() {
@@ -92,6 +129,11 @@ cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s) {
 
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s) {
     k_moments<<<1, 64, 0, s>>>(theta, K, out42);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_circular(const float* theta, int32_t K, double* out42, cudaStream_t s) {
+    k_moments_circular<<<1, 64, 0, s>>>(theta, K, out42);
     return cudaGetLastError();
 }
 
