@@ -61,7 +61,7 @@ _i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes
 class _Params(ctypes.Structure):
     _fields_ = [("T", _i32), ("m", _i32), ("lr", _f64), ("beta1", _f64), ("beta2", _f64),
                 ("eps", _f64), ("seed", _u64), ("prior", _i32), ("mu", _f64 * 6),
-                ("sigma", _f64 * 3), ("kappa", _f64 * 3)]
+                ("sigma", _f64 * 3), ("kappa", _f64 * 3), ("normals", _p)]
 
 
 def _setup(L):
@@ -72,8 +72,10 @@ def _setup(L):
         "or_rotation": (None, [_p, _p, _p]),
         "or_nn": (None, [_p, _i64, _p, _i64, _p, _p]),
         "or_nn2": (None, [_p, _i64, _p, _i64, _p, _p, _p]),
-        "or_icp_grad": (None, [_p, _i64, _p, _p, _i32, _p, _i32, _p, _p, _p]),
-        "or_icp_grad_given_nn": (None, [_p, _p, _p, _i32, _p, _i32, _p, _p]),
+        "or_icp_grad": (None, [_p, _i64, _p, _p, _i32, _p, _i32, _p, _p, _p, _p]),
+        "or_icp_grad_given_nn": (None, [_p, _p, _p, _i32, _p, _i32, _p, _p, _p]),
+        "or_knn": (None, [_p, _i64, _i32, _p]),
+        "or_neighbourhood_cov": (None, [_p, _i64, _i32, _p, _p]),
         "or_log_post_grad": (None, [_p, _p, _i32, _f64, _i32, _p, _p, _p, _p]),
         "or_median": (_f64, [_p, _i64]),
         "or_bandwidths": (None, [_p, _i32, _p, _p]),
@@ -123,6 +125,7 @@ class Params:
     mu: tuple = (0.0,) * 6
     sigma: tuple = (1.0,) * 3
     kappa: tuple = (1.0,) * 3
+    normals: object = None     # None: point-to-point; M x 3 unit normals: point-to-plane (R16)
 
     def c(self) -> _Params:
         p = _Params()
@@ -131,6 +134,9 @@ class Params:
         p.mu[:] = list(self.mu)
         p.sigma[:] = list(self.sigma)
         p.kappa[:] = list(self.kappa)
+        if self.normals is not None:
+            self._normals64 = _f64a(self.normals)     # kept alive with the parameters
+            p.normals = _ptr(self._normals64)
         return p
 
 
@@ -187,7 +193,16 @@ def transform(theta, pts):
     return np.asarray(pts, np.float64) @ R.T + np.asarray(theta[:3], np.float64)
 
 
-def icp_grad(ref, src, mb, theta):
+def _normals_ptr(normals, M):
+    if normals is None:
+        return None, None
+    n = _f64a(normals).reshape(M, 3)
+    return n, _ptr(n)
+
+
+def icp_grad(ref, src, mb, theta, normals=None):
+    """gbar, correspondences and L/2 of each particle; with normals (M x 3)
+    the point-to-plane metric (reading R16 of oracle.c)."""
     ref, src = _f32(ref), _f32(src)
     mb = np.ascontiguousarray(mb, np.int32)
     th = _f64a(theta).reshape(-1, 6)
@@ -195,20 +210,52 @@ def icp_grad(ref, src, mb, theta):
     g = np.empty((K, 6))
     nnk = np.empty((K, m), np.int64)
     loss = np.empty(K)
-    _L().or_icp_grad(_ptr(ref), ref.shape[0], _ptr(src), _ptr(mb), m, _ptr(th), K, _ptr(g),
+    keep, np_ = _normals_ptr(normals, ref.shape[0])
+    _L().or_icp_grad(_ptr(ref), ref.shape[0], _ptr(src), _ptr(mb), m, _ptr(th), K, np_, _ptr(g),
                      _ptr(nnk), _ptr(loss))
     return g, nnk, loss
 
 
-def icp_grad_given_nn(ref, src, mb, theta, nnk):
+def icp_grad_given_nn(ref, src, mb, theta, nnk, normals=None):
     ref, src = _f32(ref), _f32(src)
     mb = np.ascontiguousarray(mb, np.int32)
     th = _f64a(theta).reshape(-1, 6)
     K, m = th.shape[0], mb.shape[0]
     nnk = np.ascontiguousarray(nnk, np.int64).reshape(K, m)
     g = np.empty((K, 6))
-    _L().or_icp_grad_given_nn(_ptr(ref), _ptr(src), _ptr(mb), m, _ptr(th), K, _ptr(nnk), _ptr(g))
+    keep, np_ = _normals_ptr(normals, ref.shape[0])
+    _L().or_icp_grad_given_nn(_ptr(ref), _ptr(src), _ptr(mb), m, _ptr(th), K, _ptr(nnk), np_, _ptr(g))
     return g
+
+
+def knn(ref, k: int):
+    """The k nearest reference points of every reference point (itself
+    included), nearest first, ranked by fp32 squared distance with ties to
+    the lower index: M x k indices."""
+    ref = _f32(ref)
+    if not 1 <= k <= min(64, ref.shape[0]):
+        raise ValueError("knn needs 1 <= k <= min(64, M)")
+    idx = np.empty((ref.shape[0], k), np.int64)
+    _L().or_knn(_ptr(ref), ref.shape[0], k, _ptr(idx))
+    return idx
+
+
+def neighbourhood_cov(ref, idx):
+    ref = _f32(ref)
+    idx = np.ascontiguousarray(idx, np.int64)
+    M, k = idx.shape
+    cov = np.empty((M, 9))
+    _L().or_neighbourhood_cov(_ptr(ref), M, k, _ptr(idx), _ptr(cov))
+    return cov.reshape(M, 3, 3)
+
+
+def normals(ref, k: int):
+    """Unit normal of every reference point (reading R16 of oracle.c): the
+    eigenvector of the smallest eigenvalue of the fp64 covariance of its k
+    nearest neighbours, from LAPACK (numpy.linalg.eigh).  Returns the
+    normals (M x 3) and the ascending eigenvalues (M x 3)."""
+    w, v = np.linalg.eigh(neighbourhood_cov(ref, knn(ref, k)))
+    return np.ascontiguousarray(v[:, :, 0]), w
 
 
 def log_post_grad(theta, gbar, N, prior=0, mu=(0,) * 6, sigma=(1,) * 3, kappa=(1,) * 3):

@@ -36,6 +36,16 @@
  *      in ascending index order.
  *  R12 correspondence ties go to the lowest reference index; distances are
  *      the exact sum of squared differences.
+ *  R16 point-to-plane metric (named, not printed: the paper's comparison
+ *      table and trajectory errors use it): correspondences as R12; residual
+ *      e = n . (R s + u - r) with n the unit normal at r; the gradient is
+ *      that of (1/2m) sum e^2 with r and n held fixed, i.e. the point-to-point
+ *      terms with the residual vector replaced by e n.  The normal at a
+ *      reference point is the eigenvector of the smallest eigenvalue of the
+ *      covariance of its k nearest reference points (itself included), the
+ *      neighbours ranked by the fp32 squared distance fmaf(dx, dx, fmaf(dy,
+ *      dy, dz * dz)) with dx = r_x - q_x in fp32, ties to the lower index (the
+ *      decision is taken in the kernel's precision); the covariance in fp64.
  *  R15 circular moments (for rotation blocks whose particles straddle +-pi):
  *      each angle's mean is the circular mean atan2(sum sin, sum cos) (0 if
  *      both sums vanish); the covariance is that of the deviations
@@ -216,7 +226,7 @@ static void or_transform(const double R[9], const double th[6], const float* s, 
  * minibatch, (1/2m) sum ||R s + u - r||^2. */
 static double or_grad_given_nn_one(const float* ref, const float* src, const int32_t* mb,
                                    int32_t m, const double th[6], const int64_t* nn,
-                                   double g[6]) {
+                                   const double* normals, double g[6]) {
     double R[9], dR[27];
     or_rotation(th, R, dR);
     double acc[6] = {0, 0, 0, 0, 0, 0}, loss = 0.0;
@@ -226,6 +236,12 @@ static double or_grad_given_nn_one(const float* ref, const float* src, const int
         or_transform(R, th, s, sp);
         const float* r = ref + 3 * nn[k];
         for (int a = 0; a < 3; ++a) e[a] = sp[a] - (double)r[a];
+        if (normals) {
+            /* point-to-plane (R16): the residual vector becomes (n . e) n */
+            const double* n = normals + 3 * nn[k];
+            const double en = n[0] * e[0] + n[1] * e[1] + n[2] * e[2];
+            for (int a = 0; a < 3; ++a) e[a] = en * n[a];
+        }
         /* d s'/d u = I */
         for (int a = 0; a < 3; ++a) acc[a] += e[a];
         /* d s'/d theta_{3+a} = dR_a s */
@@ -244,9 +260,10 @@ static double or_grad_given_nn_one(const float* ref, const float* src, const int
 
 /* For each of K particles (th: K x 6): correspondences of the transformed
  * minibatch (nn_out: K x m, may be NULL) and gbar (K x 6).  loss_out (K, may be
- * NULL) receives L/2 over the minibatch. */
+ * NULL) receives L/2 over the minibatch.  normals (M x 3, may be NULL): the
+ * point-to-plane metric (R16). */
 OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const int32_t* mb,
-                           int32_t m, const double* th, int32_t K, double* gbar,
+                           int32_t m, const double* th, int32_t K, const double* normals, double* gbar,
                            int64_t* nn_out, double* loss_out) {
     int64_t* nn = (int64_t*)malloc(sizeof(int64_t) * (size_t)K * (size_t)m);
     double* qs = (double*)malloc(sizeof(double) * 3 * (size_t)K * (size_t)m);
@@ -262,7 +279,7 @@ OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const 
         nn[q] = or_nn_one(ref, M, qs + 3 * q, &d2);
     }
     for (int32_t j = 0; j < K; ++j) {
-        double l = or_grad_given_nn_one(ref, src, mb, m, th + 6 * j, nn + (int64_t)j * m, gbar + 6 * j);
+        double l = or_grad_given_nn_one(ref, src, mb, m, th + 6 * j, nn + (int64_t)j * m, normals, gbar + 6 * j);
         if (loss_out) loss_out[j] = l;
     }
     if (nn_out) memcpy(nn_out, nn, sizeof(int64_t) * (size_t)K * (size_t)m);
@@ -273,9 +290,59 @@ OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const 
 /* Same gradient with the correspondences given (K x m reference indices). */
 OR_EXPORT void or_icp_grad_given_nn(const float* ref, const float* src, const int32_t* mb,
                                     int32_t m, const double* th, int32_t K, const int64_t* nn,
-                                    double* gbar) {
+                                    const double* normals, double* gbar) {
     for (int32_t j = 0; j < K; ++j)
-        or_grad_given_nn_one(ref, src, mb, m, th + 6 * j, nn + (int64_t)j * m, gbar + 6 * j);
+        or_grad_given_nn_one(ref, src, mb, m, th + 6 * j, nn + (int64_t)j * m, normals, gbar + 6 * j);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reference normals for the point-to-plane metric (R16)                     */
+/* ------------------------------------------------------------------------ */
+
+/* The k nearest reference points of every reference point (itself included),
+ * nearest first: exhaustive, fp32 squared distances, ties to the lower index.
+ * idx: M x k. */
+OR_EXPORT void or_knn(const float* ref, int64_t M, int32_t k, int64_t* idx) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < M; ++i) {
+        float bd[64];
+        int64_t bi[64];
+        int32_t n = 0;
+        const float qx = ref[3 * i], qy = ref[3 * i + 1], qz = ref[3 * i + 2];
+        for (int64_t r = 0; r < M; ++r) {
+            const float dx = ref[3 * r] - qx, dy = ref[3 * r + 1] - qy, dz = ref[3 * r + 2] - qz;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (n == k && !(d2 < bd[k - 1])) continue;      /* r > every kept index: equal loses */
+            int32_t p = n < k ? n++ : k - 1;                /* insertion position from the end */
+            while (p > 0 && d2 < bd[p - 1]) {
+                bd[p] = bd[p - 1];
+                bi[p] = bi[p - 1];
+                --p;
+            }
+            bd[p] = d2;
+            bi[p] = r;
+        }
+        for (int32_t c = 0; c < k; ++c) idx[i * k + c] = c < n ? bi[c] : -1;
+    }
+}
+
+/* Covariance (divisor k) of each point's neighbourhood idx (M x k): M x 9. */
+OR_EXPORT void or_neighbourhood_cov(const float* ref, int64_t M, int32_t k, const int64_t* idx, double* cov) {
+    for (int64_t i = 0; i < M; ++i) {
+        double mu[3] = {0, 0, 0};
+        for (int32_t c = 0; c < k; ++c)
+            for (int a = 0; a < 3; ++a) mu[a] += (double)ref[3 * idx[i * k + c] + a];
+        for (int a = 0; a < 3; ++a) mu[a] /= (double)k;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int32_t c = 0; c < k; ++c) {
+                    const float* p = ref + 3 * idx[i * k + c];
+                    s += ((double)p[a] - mu[a]) * ((double)p[b] - mu[b]);
+                }
+                cov[9 * i + 3 * a + b] = s / (double)k;
+            }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -440,6 +507,7 @@ typedef struct {
     uint64_t seed;
     int32_t prior;
     double mu[6], sigma[3], kappa[3];
+    const double* normals;   /* NULL: point-to-point; else M x 3: point-to-plane (R16) */
 } or_params;
 
 /* Iteration t (0-based) in place on th, mom, vel (each K x 6).  Optional
@@ -454,7 +522,7 @@ OR_EXPORT void or_step(const float* ref, int64_t M, const float* src, int64_t N,
     double* phi = (double*)malloc(sizeof(double) * 6 * (size_t)K);
     double* g = (double*)malloc(sizeof(double) * 6 * (size_t)K);
     or_minibatch(p->seed, t, N, p->m, mb);
-    or_icp_grad(ref, M, src, mb, p->m, th, K, gbar, NULL, NULL);
+    or_icp_grad(ref, M, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
     or_log_post_grad(th, gbar, K, (double)N, p->prior, p->mu, p->sigma, p->kappa, G);
     double h_t, h_r;
     or_bandwidths(th, K, &h_t, &h_r);

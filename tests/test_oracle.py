@@ -177,6 +177,129 @@ def test_icp_gradient_central_differences():
     assert checked >= 5
 
 
+# ---------------------------------------------------------------- point-to-plane (reading R16)
+
+def _half_loss_plane(theta, ref, normals, src_mb):
+    """Point-to-plane L/2 over a minibatch, nearest neighbours recomputed
+    (scipy rotation + cKDTree), normals held fixed; independent of the oracle."""
+    R = Rotation.from_euler("xyz", theta[3:]).as_matrix()
+    q = src_mb.astype(np.float64) @ R.T + theta[:3]
+    _, i = cKDTree(ref.astype(np.float64)).query(q)
+    e = np.einsum("ij,ij->i", normals[i], q - ref[i].astype(np.float64))
+    return 0.5 * np.mean(e ** 2), i
+
+
+def test_point_to_plane_gradient_central_differences():
+    rng = np.random.default_rng(6)
+    ref = rng.uniform(-1, 1, (400, 3)).astype(np.float32)
+    nrm = rng.normal(size=(400, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    src = rng.uniform(-1, 1, (200, 3)).astype(np.float32)
+    mb = O.minibatch(4, 0, 200, 60)
+    h = 1e-6
+    checked = 0
+    for trial in range(10):
+        th = np.r_[rng.normal(0, 0.1, 3), rng.uniform(-0.5, 0.5, 3)]
+        g, nnk, loss = O.icp_grad(ref, src, mb, th[None], normals=nrm)
+        l0, i0 = _half_loss_plane(th, ref, nrm, src[mb])
+        assert abs(loss[0] - l0) < 1e-12 * max(1.0, l0) and np.array_equal(nnk[0], i0)
+        fd = np.empty(6)
+        stable = True
+        for a in range(6):
+            tp, tm = th.copy(), th.copy()
+            tp[a] += h
+            tm[a] -= h
+            lp, ip = _half_loss_plane(tp, ref, nrm, src[mb])
+            lm, im = _half_loss_plane(tm, ref, nrm, src[mb])
+            stable &= np.array_equal(ip, i0) and np.array_equal(im, i0)
+            fd[a] = (lp - lm) / (2 * h)
+        if not stable:
+            continue
+        checked += 1
+        assert np.abs(fd - g[0]).max() <= 1e-7 * np.abs(g[0]).max() + 1e-12
+    assert checked >= 5
+
+
+def test_point_to_plane_gradient_closed_form():
+    """A planar reference z = 0 on a 1 cm lattice; source points over lattice
+    points, lifted by delta and slid by eps < half a cell within the plane.
+    At the identity pose the point-to-plane residual is delta along z, so
+    gbar = (0, 0, delta, delta mean(y), -delta mean(x), 0); point-to-point
+    adds the in-plane slide to the translation."""
+    xs, ys = np.meshgrid(np.arange(-20, 21) * 0.01, np.arange(-15, 16) * 0.01)
+    ref = np.c_[xs.ravel(), ys.ravel(), np.zeros(xs.size)].astype(np.float32)
+    nrm = np.tile([0.0, 0.0, -1.0], (ref.shape[0], 1))          # the sign of a normal is irrelevant
+    delta, eps = 0.003, 0.002
+    pick = np.random.default_rng(2).choice(ref.shape[0], 300, replace=False)
+    src = (ref[pick].astype(np.float64) + [eps, 0.0, delta]).astype(np.float32)
+    mb = np.arange(300, dtype=np.int32)
+    th = np.zeros((1, 6))
+    g, nnk, _ = O.icp_grad(ref, src, mb, th, normals=nrm)
+    assert np.array_equal(nnk[0], pick)
+    s = src.astype(np.float64)
+    dz = s[:, 2] - 0.0
+    expect = [0.0, 0.0, dz.mean(), np.mean(dz * s[:, 1]), -np.mean(dz * s[:, 0]), 0.0]
+    assert np.allclose(g[0], expect, atol=1e-15)
+    g_pp, _, _ = O.icp_grad(ref, src, mb, th)
+    assert abs(g_pp[0, 0] - np.mean(s[:, 0] - ref[pick, 0])) < 1e-12 and abs(g_pp[0, 0]) > 1e-3
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_knn_matches_kdtree(k):
+    rng = np.random.default_rng(k)
+    ref = rng.uniform(-1, 1, (3000, 3)).astype(np.float32)
+    idx = O.knn(ref, k)
+    d, i = cKDTree(ref.astype(np.float64)).query(ref.astype(np.float64), k + 1)
+    assert np.array_equal(idx[:, 0], np.arange(3000))             # each point is its own nearest
+    same = np.array([set(idx[r]) == set(i[r, :k]) for r in range(3000)])
+    # a set may differ only where the k-th and (k+1)-th fp64 distances tie to fp32 rounding
+    near_tie = np.abs(d[:, k] - d[:, k - 1]) <= 1e-6 * d[:, k]
+    assert np.all(same | near_tie) and same.mean() > 0.99
+    # ties go to the lower index: duplicates of point 7 follow it in index order
+    dup = np.concatenate([ref[:100], ref[7:8], ref[7:8]])
+    di = O.knn(dup, 3)
+    assert list(di[7]) == [7, 100, 101] and list(di[101]) == [7, 100, 101]
+
+
+def test_neighbourhood_cov_matches_numpy():
+    rng = np.random.default_rng(3)
+    ref = rng.normal(size=(500, 3)).astype(np.float32)
+    idx = rng.integers(0, 500, (50, 12))
+    cov = O.neighbourhood_cov(ref, idx)
+    for r in range(50):
+        assert np.allclose(cov[r], np.cov(ref[idx[r]].astype(np.float64).T, bias=True), atol=1e-14)
+
+
+def test_normals_of_a_plane_and_a_sphere():
+    rng = np.random.default_rng(8)
+    xy = rng.uniform(-1, 1, (2000, 2))
+    z = 0.3 * xy[:, 0] - 0.2 * xy[:, 1] + 0.5
+    plane = np.c_[xy, z].astype(np.float32)
+    n, w = O.normals(plane, 12)
+    true = np.array([0.3, -0.2, -1.0]) / np.linalg.norm([0.3, -0.2, -1.0])
+    assert np.all(np.abs(n @ true) > 1 - 1e-9)
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-12)
+    # Fibonacci sphere: the normal of a small symmetric patch is radial
+    N = 20000
+    i = np.arange(N) + 0.5
+    phi, cz = np.pi * (1 + 5 ** 0.5) * i, 1 - 2 * i / N
+    sph = np.c_[np.sqrt(1 - cz ** 2) * np.cos(phi), np.sqrt(1 - cz ** 2) * np.sin(phi), cz].astype(np.float32)
+    n, w = O.normals(sph, 16)
+    radial = sph.astype(np.float64) / np.linalg.norm(sph.astype(np.float64), axis=1, keepdims=True)
+    assert np.all(np.abs(np.einsum("ij,ij->i", n, radial)) > 0.999)
+
+
+def test_point_to_plane_run_recovers_known_pose_noise_free():
+    """K = 1 with the point-to-plane metric on a noise-free box: the
+    generating pose zeroes every residual, and the run lands on it."""
+    d = synth.make_box_problem(0, K=1, noise=0.0)
+    nrm, _ = O.normals(d["ref"], 10)
+    th, _, _ = O.register(d["ref"], d["src"], d["particles"], O.Params(T=300, m=100, seed=7, normals=nrm))
+    err = th[0] - d["theta_true"]
+    assert np.abs(err[:3]).max() < 1e-3
+    assert np.abs(err[3:]).max() < math.radians(0.05)
+
+
 def test_icp_gradient_single_point_closed_form():
     ref = np.array([[0.3, -0.2, 0.5]], np.float32)
     src = np.array([[0.1, 0.4, -0.2]], np.float32)
