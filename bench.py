@@ -54,6 +54,8 @@ def parse():
                     help="search of the registration loop (default: per workload)")
     ap.add_argument("--profile-stride", type=int, default=5,
                     help="time the gradient and Stein kernels of every s-th iteration with CUDA events")
+    ap.add_argument("--metric", default="point", choices=["point", "plane"],
+                    help="ICP error metric: point-to-point (the paper's Stein ICP) or point-to-plane")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -100,10 +102,19 @@ def make_problem(workload: str, seed: int):
     return d, dict(synth.WORKLOADS[workload])
 
 
-def workload_config(workload, d, cfg, nn_mode_name):
+NORMAL_K = 10   # neighbours of the reference normals of the point-to-plane metric
+SETREF_LAUNCHES = 22   # kernels of one sicp_set_reference on the kinect-sized grid (7 seed-flooding steps)
+
+
+def metric_name(metric):
+    return "point-to-point" if metric == "point" else f"point-to-plane (normals from {NORMAL_K} nearest neighbours)"
+
+
+def workload_config(workload, d, cfg, nn_mode_name, metric="point"):
     return {"workload": workload, "reference_points": int(d["ref"].shape[0]),
             "source_points": int(d["src"].shape[0]), "particles": int(d["particles"].shape[0]),
-            "minibatch": cfg["m"], "iterations": cfg["T"], "adam_lr": cfg["lr"], "nn": nn_mode_name}
+            "minibatch": cfg["m"], "iterations": cfg["T"], "adam_lr": cfg["lr"], "nn": nn_mode_name,
+            "metric": metric_name(metric)}
 
 
 FALLBACK_BF16_TFLOPS = 1900.0
@@ -192,13 +203,15 @@ def ncu_traffic_per_query():
     return rec["dram_bytes"] / rec["queries"]
 
 
-def cpu_baseline(d, cfg, budget_s=15.0):
-    """The oracle as it stands, on a bounded number of iterations of the same workload."""
+def cpu_baseline(d, cfg, budget_s=15.0, metric="point"):
+    """The oracle as it stands, on a bounded number of iterations of the same workload
+    (point-to-plane: the reference normals are computed before the timed sample)."""
     import oracle as O
     ref, src = d["ref"], d["src"]
     th = d["particles"].astype(np.float64).copy()
     mom, vel = np.zeros_like(th), np.zeros_like(th)
-    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0)
+    normals = O.normals(ref, NORMAL_K)[0] if metric == "plane" else None
+    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals)
     K = th.shape[0]
     t0 = time.perf_counter()
     O.step(ref, src, th, mom, vel, p, 0)
@@ -222,7 +235,8 @@ def run_reference(args):
     import oracle as O
     ref, src = d["ref"], d["src"]
     K = d["particles"].shape[0]
-    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0)
+    normals = O.normals(ref, NORMAL_K)[0] if args.metric == "plane" else None
+    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals)
     th = d["particles"].astype(np.float64).copy()
     mom, vel = np.zeros_like(th), np.zeros_like(th)
     t0 = time.perf_counter()
@@ -247,7 +261,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "particle_point_evals_per_sec", "value": value,
             "unit": "particle_point_evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, d, cfg, "exhaustive"),
+            "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, d, cfg, "exhaustive", args.metric),
             "iters_per_sec": per_step / (ms / 1e3),
             "cpu_baseline": {"value": value, "unit": "particle_point_evals/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
@@ -278,6 +293,11 @@ def run_ours(args):
              "fp32": "exhaustive fp32",
              "surrogate": "learned closest-point field for the first iterations, exact voxel grid after and as fallback"}
     nn_mode, mode_name = modes[nn], names[nn]
+    plane = args.metric == "plane"
+    if plane:
+        if nn not in ("grid", "fp32"):
+            raise SystemExit("the point-to-plane metric runs with --nn grid or --nn fp32")
+        nn_mode |= S.SICP_POINT_TO_PLANE
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = S.sicp_create(local, stream)
@@ -300,6 +320,8 @@ def run_ours(args):
     def step():
         if nn != "surrogate":
             S.sicp_set_reference(ctx, ref_d)
+            if plane:
+                S.sicp_reference_normals(ctx, NORMAL_K, want=False)
         return S.sicp_register(ctx, src_d, par_d, p)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -314,7 +336,7 @@ def run_ours(args):
     queries = max(st[0], 1.0)   # grid-search counters (zero in the exhaustive modes)
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
     coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
-    bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q
+    bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q + (16 if plane else 0)   # + the normal
     if args.profile_stride > 0:
         S.sicp_profile(ctx, args.profile_stride)
         step()   # capture the profiling graphs outside the timed region
@@ -351,7 +373,8 @@ def run_ours(args):
         alg_bytes = bytes_per_query * queries_per_launch
         achieved = alg_bytes / (grad_ms * 1e-3) / 1e9 if grad_ms else None
         tpq = ncu_traffic_per_query()
-        roofline = {"kernel": "k_grad_grid (transform + grid NN + gradient, one iteration)", "bound": "hbm",
+        roofline = {"kernel": "k_grad_grid (transform + grid NN + gradient, one iteration)"
+                              + (", point-to-plane" if plane else ""), "bound": "hbm",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} copy bandwidth",
                     "frac": achieved / peak if achieved else None,
                     "traffic": tpq * queries_per_launch if tpq else None,
@@ -393,6 +416,8 @@ def run_ours(args):
         for _ in range(2):
             if with_ref:
                 S.sicp_set_reference(ctx, ref_h)
+                if plane:
+                    S.sicp_reference_normals(ctx, NORMAL_K, want=False)
             S.sicp_register(ctx, src_h, par_h, p)
         wall = []
         for _ in range(args.steps):
@@ -401,6 +426,8 @@ def run_ours(args):
             t0 = time.perf_counter()
             if with_ref:
                 S.sicp_set_reference(ctx, ref_h)
+                if plane:
+                    S.sicp_reference_normals(ctx, NORMAL_K, want=False)
             out = S.sicp_register(ctx, src_h, par_h, p)
             wall.append(time.perf_counter() - t0)
         e2e = {"value": world * evals / statistics.mean(wall), "unit": "particle_point_evals/s",
@@ -412,20 +439,23 @@ def run_ours(args):
         comparison = compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(d, cfg)
+        cpu = cpu_baseline(d, cfg, metric=args.metric)
     S.sicp_destroy(ctx)
-    per_iter = {"grid": 2, "fp32": 2, "bf16": 3}.get(nn)
+    per_iter = {"grid": 3, "fp32": 2, "bf16": 3}.get(nn)
     if per_iter is not None:
-        launches_per_step = 9 + 4 + per_iter * cfg["T"]
-    else:   # surrogate, fallback, reduction and Stein for the surrogate iterations; grid and Stein after
+        # reference build (pack, bbox, two grid levels, seed map: 22 launches on the kinect grid, counted
+        # in an ncu launch list), the run's pack / finite check / minibatch / moments, and per iteration
+        # the gradient kernel(s) and the Stein kernel; point-to-plane adds the normals kernel
+        launches_per_step = SETREF_LAUNCHES + 4 + per_iter * cfg["T"] + (1 if plane else 0)
+    else:   # surrogate, fallback, reduction and Stein for the surrogate iterations; grid, reduction and Stein after
         si = min(cfg.get("surrogate_iters", 0), cfg["T"])
-        launches_per_step = 4 + 4 * si + 2 * (cfg["T"] - si)
+        launches_per_step = 4 + 4 * si + 3 * (cfg["T"] - si)
     if rank == 0:
         line = {"metric": "particle_point_evals_per_sec", "value": value, "unit": "particle_point_evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded generators; no dataset)",
-                "config": {**workload_config(args.workload, d, cfg, mode_name),
+                "config": {**workload_config(args.workload, d, cfg, mode_name, args.metric),
                            "l2": "256 MB buffer written between timed steps (outside the events)",
                            "parallelism": f"independent problem per rank x{world}"},
                 "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),

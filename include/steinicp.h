@@ -46,7 +46,8 @@ extern "C" {
 
 #define SICP_OK 0
 #define SICP_EINVAL (-1)        /* bad size, pointer, mode or non-finite input */
-#define SICP_ENOREF (-2)        /* no reference cloud set on the context */
+#define SICP_ENOREF (-2)        /* no reference cloud set on the context (or no normals for
+                                   SICP_POINT_TO_PLANE) */
 #define SICP_ENOMEM (-3)        /* device allocation failed */
 #define SICP_ECUDA (-4)         /* a CUDA runtime call failed */
 #define SICP_ETIMEOUT (-5)      /* a bounded device wait gave up */
@@ -58,6 +59,16 @@ extern "C" {
                                    same results as SICP_NN_BRUTE_FP32 */
 #define SICP_NN_GRID 2          /* uniform voxel grid, exact */
 #define SICP_NN_SURROGATE 3     /* learned closest-point field, then exact grid */
+/* Metric flag, OR-ed into the search mode of sicp_register (nn_mode) and
+ * sicp_icp_grad (mode), with SICP_NN_GRID or SICP_NN_BRUTE_FP32: the
+ * point-to-plane error, which the paper uses for its method comparison and
+ * trajectory errors without printing it.  Correspondences stay the nearest
+ * reference point r (Eq. correspondences); the residual becomes
+ * e = n . (R s + u - r) with n the unit normal at r, and gbar the gradient of
+ * (1/2m) sum e^2 with r and n held fixed (the terms of Eqs. trans_gradient /
+ * rotation_gradient with the residual vector replaced by e n).  Needs
+ * sicp_reference_normals on the current reference. */
+#define SICP_POINT_TO_PLANE 0x100
 
 typedef struct sicp_ctx sicp_ctx;
 
@@ -219,6 +230,17 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
  * [K][6], accumulated in float64.  Errors: SICP_EINVAL (K < 1). */
 int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36,
                  int on_device);
+
+/* Unit normals of the current reference for the point-to-plane metric: the
+ * eigenvector of the smallest eigenvalue of the float64 covariance (divisor
+ * k) of each point's k nearest reference points (itself included; ranked by
+ * the library's fp32 squared distance, ties to the lower index).  The context
+ * keeps them for SICP_POINT_TO_PLANE until the next sicp_set_reference.
+ * out_normals ([M][3] float32, original order, may be NULL) receives a copy;
+ * a normal's sign is arbitrary (the metric does not depend on it).  Errors:
+ * SICP_ENOREF (no reference), SICP_EINVAL (k outside [3, min(32, M)]),
+ * SICP_ENOMEM, SICP_ECUDA. */
+int sicp_reference_normals(sicp_ctx* ctx, int32_t k, float* out_normals, int on_device);
 
 /* The same moments with circular statistics for the three angles, for
  * particle sets whose rotations straddle +-pi (the plain mean of angles near

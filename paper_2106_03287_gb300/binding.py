@@ -32,14 +32,15 @@ SICP_NN_BRUTE_FP32 = 0
 SICP_NN_BRUTE_BF16 = 1
 SICP_NN_GRID = 2
 SICP_NN_SURROGATE = 3
+SICP_POINT_TO_PLANE = 0x100   # metric flag, OR-ed into nn_mode / mode (grid or fp32 exhaustive search)
 
 _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOSURROGATE"}
 
 # Every C entry point declared in include/steinicp.h.
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
-    "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments", "sicp_moments_circular",
-    "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
+    "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
+    "sicp_moments_circular", "sicp_reference_normals", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
 )
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "sicp_register_continue": (ctypes.c_int, [P, P, I64, P, I32, I64, pp, P, P, ctypes.c_int]),
             "sicp_surrogate_save": (ctypes.c_int, [P, ctypes.c_char_p]),
             "sicp_surrogate_load": (ctypes.c_int, [P, ctypes.c_char_p]),
+            "sicp_reference_normals": (ctypes.c_int, [P, I32, P, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -190,10 +192,22 @@ def sicp_last_error(ctx) -> str:
     return lib().sicp_last_error(ctx).decode()
 
 
+_REF_SIZE = {}   # reference size of each context, as set through this binding
+
+
+def ctx_reference_size(ctx) -> int:
+    """M of the reference last set on `ctx` through sicp_set_reference."""
+    if ctx.value not in _REF_SIZE:
+        raise SicpError(SICP_ENOREF, "no reference cloud set through this binding")
+    return _REF_SIZE[ctx.value]
+
+
 def sicp_set_reference(ctx, xyz, cell_size: float = 0.0) -> None:
     xyz = _host(xyz, np.float32)
+    _REF_SIZE.pop(ctx.value, None)
     _check(ctx, lib().sicp_set_reference(ctx, _ptr(xyz, np.float32), xyz.shape[0], float(cell_size),
                                          _on_device(xyz)))
+    _REF_SIZE[ctx.value] = int(xyz.shape[0])
 
 
 def sicp_register(ctx, src_xyz, particles, params: sicp_params):
@@ -280,6 +294,24 @@ def sicp_moments(ctx, particles):
     _check(ctx, lib().sicp_moments(ctx, _ptr(particles, np.float32), particles.shape[0], _ptr(mean, np.float64),
                                    _ptr(cov, np.float64), _on_device(particles)))
     return mean, cov
+
+
+def sicp_reference_normals(ctx, k: int = 10, want: bool = True, device: bool = False):
+    """Compute (and keep on the context, for SICP_POINT_TO_PLANE) the unit
+    normals of the current reference from k nearest neighbours; returns them
+    as [M][3] float32 (a numpy array, or a CUDA tensor with device=True), or
+    None with want=False."""
+    out = None
+    if want:
+        M = int(ctx_reference_size(ctx))
+        if device:
+            import torch
+            out = torch.empty((M, 3), dtype=torch.float32, device="cuda")
+        else:
+            out = np.empty((M, 3), np.float32)
+    _check(ctx, lib().sicp_reference_normals(ctx, int(k), _ptr(out, np.float32) if out is not None else None,
+                                             1 if device else 0))
+    return out
 
 
 def sicp_moments_circular(ctx, particles):

@@ -60,7 +60,7 @@ struct LoopKey {
     uint64_t surr_gen;      // surrogate weights / normalisation version
     uint64_t seed;
     int64_t t0;             // first iteration of the run
-    const void* ptrs[12];
+    const void* ptrs[13];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -146,6 +146,14 @@ int read_flags(sicp_ctx* ctx, int* flags_host) {
 }
 
 int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
+    if (mode & SICP_POINT_TO_PLANE) {
+        const int32_t base = mode & ~SICP_POINT_TO_PLANE;
+        if (base != SICP_NN_GRID && base != SICP_NN_BRUTE_FP32)
+            return set_err(ctx, SICP_EINVAL, "the point-to-plane metric works with SICP_NN_GRID or SICP_NN_BRUTE_FP32");
+        if (ctx->normals_k == 0)
+            return set_err(ctx, SICP_ENOREF, "the point-to-plane metric needs sicp_reference_normals on this reference");
+        return SICP_OK;
+    }
     if (mode == SICP_NN_BRUTE_FP32 || mode == SICP_NN_GRID || mode == SICP_NN_BRUTE_BF16) return SICP_OK;
     if (mode == SICP_NN_SURROGATE && allow_surrogate) {
         if (surrogate_ready(ctx)) return SICP_OK;
@@ -316,7 +324,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done,
-                   &c->bf16_tiles};
+                   &c->bf16_tiles, &c->normals};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -357,6 +365,7 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
     ctx->M = 0;
     surrogate_invalidate(ctx);   // a surrogate belongs to the reference it was trained on
     ctx->bf16_ready = false;
+    ctx->normals_k = 0;          // and so do normals
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_xyz, M, ctx->ref4, (int*)ctx->flags.p, ctx->stream));
     int flags[4];
@@ -454,6 +463,8 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     int rc = check_mode(ctx, mode, true);
     if (rc) return rc;
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
+    const bool plane = (mode & SICP_POINT_TO_PLANE) != 0;
+    mode &= ~SICP_POINT_TO_PLANE;
     if (!on_device) {
         if (!host_finite(src_xyz, 3 * N) || !host_finite(particles, 6 * (int64_t)K))
             return set_err(ctx, SICP_EINVAL, "non-finite input");
@@ -508,6 +519,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.stats = stats_ptr(ctx);
     g.gbar = d_g;
     g.inv_m = 1.f / (float)m;
+    g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     g.done = (unsigned*)ctx->done.p;
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
@@ -643,14 +655,16 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
         return set_err(ctx, SICP_EINVAL, "non-finite input");
     DeviceScope ds(ctx->device);
-    const bool surr = p.nn_mode == SICP_NN_SURROGATE;
+    const bool plane = (p.nn_mode & SICP_POINT_TO_PLANE) != 0;
+    const int32_t nn_mode = p.nn_mode & ~SICP_POINT_TO_PLANE;
+    const bool surr = nn_mode == SICP_NN_SURROGATE;
     if (surr && (int64_t)K * p.m > ((int64_t)1 << 24))
         return set_err(ctx, SICP_EINVAL, "surrogate mode needs K * m <= 2^24 queries per iteration");
-    const bool bf = p.nn_mode == SICP_NN_BRUTE_BF16;
+    const bool bf = nn_mode == SICP_NN_BRUTE_BF16;
     if (bf && (int64_t)K * p.m > ((int64_t)1 << 26))
         return set_err(ctx, SICP_EINVAL, "the tensor-core search needs K * m <= 2^26");
-    const bool grid = p.nn_mode == SICP_NN_GRID || surr;   // the surrogate's exact iterations use the grid
-    const int32_t exact_mode = surr ? SICP_NN_GRID : p.nn_mode;
+    const bool grid = nn_mode == SICP_NN_GRID || surr;   // the surrogate's exact iterations use the grid
+    const int32_t exact_mode = surr ? SICP_NN_GRID : nn_mode;
     const int chunks = (grid ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
     const int32_t surr_T = surr ? (p.surrogate_iters < p.T ? p.surrogate_iters : p.T) : 0;
     const size_t b_th = sizeof(float) * 6 * K;
@@ -734,6 +748,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.ptrs[9] = stats_ptr(ctx);
     key.ptrs[10] = ctx->gbar.p;
     key.ptrs[11] = ctx->done.p;
+    key.ptrs[12] = plane ? ctx->normals.p : nullptr;
 
     GraphCache& gc = *ctx->graphs;
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
@@ -751,6 +766,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         g.gbar = (float*)ctx->gbar.p;
         g.done = (unsigned*)ctx->done.p;
         g.inv_m = 1.f / (float)p.m;
+        g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
         int np = 0;
         for (int32_t t = 0; t < p.T; ++t) {
             const bool timed = prof && stride > 0 && (t % stride) == 0;

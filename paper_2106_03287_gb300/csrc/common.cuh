@@ -75,6 +75,14 @@ __device__ __forceinline__ void grad_terms(const Pose& P, float3 s, float3 e, fl
     }
 }
 
+// Point-to-plane: the residual vector d = s' - r replaced by (n . d) n, n the
+// unit normal at r (xyz of n4), so that grad_terms gives the gradient of
+// (n . d)^2 / 2.
+__device__ __forceinline__ float3 plane_residual(float4 n4, float3 d) {
+    const float e = fmaf(n4.x, d.x, fmaf(n4.y, d.y, n4.z * d.z));
+    return make_float3(e * n4.x, e * n4.y, e * n4.z);
+}
+
 // Exact squared distance, the comparison every search mode uses.
 __device__ __forceinline__ float dist2(float4 r, float3 q) {
     float dx = r.x - q.x, dy = r.y - q.y, dz = r.z - q.z;
@@ -178,6 +186,8 @@ struct sicp_ctx {
     int bf16_R = 0;                      // reference tiles of 256 points
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
+    sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
+    int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
 };
 
 namespace sicp {
@@ -246,6 +256,9 @@ struct GradArgs {
     float* gbar;           // K x 6
     unsigned* done;        // K arrival counters (unused by the grid search)
     float inv_m;
+    // point-to-plane metric: unit normals by original reference index (w
+    // unused); null: point-to-point
+    const float4* normals;
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
 

@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(kGradMaxThreads) k_grad_brute(GradArgs a, cons
     const bool found = bi != 0x7fffffff;      // false only for a non-finite distance
     if (valid && found) {
         const float4 r = ref[bi];
-        grad_terms(P, s, make_float3(q.x - r.x, q.y - r.y, q.z - r.z), g);
+        float3 d = make_float3(q.x - r.x, q.y - r.y, q.z - r.z);
+        if (a.normals) d = plane_residual(__ldg(a.normals + bi), d);
+        grad_terms(P, s, d, g);
     }
     if (valid && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? bi : -1;
     block_sum6(g, red);

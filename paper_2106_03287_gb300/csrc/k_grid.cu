@@ -108,7 +108,11 @@ __global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, Grid
         if (lane == 0) {
             float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const bool found = B.i != kNone;   // false only for a non-finite distance
-            if (found) grad_terms(P[jl], s, make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z), t);
+            if (found) {
+                float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
+                if (a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
+                grad_terms(P[jl], s, d, t);
+            }
             float* dst = a.partial + ((int64_t)j * a.m + k) * 6;
 #pragma unroll
             for (int c = 0; c < 6; ++c) dst[c] = t[c];
