@@ -295,8 +295,8 @@ def run_ours(args):
     nn_mode, mode_name = modes[nn], names[nn]
     plane = args.metric == "plane"
     if plane:
-        if nn not in ("grid", "fp32"):
-            raise SystemExit("the point-to-plane metric runs with --nn grid or --nn fp32")
+        if nn == "surrogate":
+            raise SystemExit("the point-to-plane metric runs with the exact searches (--nn grid, fp32 or bf16)")
         nn_mode |= S.SICP_POINT_TO_PLANE
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -317,11 +317,14 @@ def run_ours(args):
         training = {"queries": SURR_QUERIES, "epochs": SURR_EPOCHS, "batch": 4096, "seconds": time.perf_counter() - t0,
                     "final_loss": loss}
 
+    def set_ref(ref):
+        S.sicp_set_reference(ctx, ref)
+        if plane:
+            S.sicp_reference_normals(ctx, NORMAL_K, want=False)
+
     def step():
         if nn != "surrogate":
-            S.sicp_set_reference(ctx, ref_d)
-            if plane:
-                S.sicp_reference_normals(ctx, NORMAL_K, want=False)
+            set_ref(ref_d)
         return S.sicp_register(ctx, src_d, par_d, p)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -415,9 +418,7 @@ def run_ours(args):
         with_ref = nn != "surrogate"   # the learned field stays with the reference it was trained on
         for _ in range(2):
             if with_ref:
-                S.sicp_set_reference(ctx, ref_h)
-                if plane:
-                    S.sicp_reference_normals(ctx, NORMAL_K, want=False)
+                set_ref(ref_h)
             S.sicp_register(ctx, src_h, par_h, p)
         wall = []
         for _ in range(args.steps):
@@ -425,9 +426,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if with_ref:
-                S.sicp_set_reference(ctx, ref_h)
-                if plane:
-                    S.sicp_reference_normals(ctx, NORMAL_K, want=False)
+                set_ref(ref_h)
             out = S.sicp_register(ctx, src_h, par_h, p)
             wall.append(time.perf_counter() - t0)
         e2e = {"value": world * evals / statistics.mean(wall), "unit": "particle_point_evals/s",
@@ -436,7 +435,8 @@ def run_ours(args):
 
     comparison = None
     if nn in ("bf16", "surrogate"):
-        comparison = compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, args.steps)
+        comparison = compare_paths(S, ctx, nn, p, lambda: set_ref(ref_d), src_d, par_d, cfg, K, flush, stream,
+                                   args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, cfg, metric=args.metric)
@@ -485,16 +485,17 @@ def timed_runs(fn, flush, stream, steps):
     return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
 
-def compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, steps):
+def compare_paths(S, ctx, nn, p, set_ref, src_d, par_d, cfg, K, flush, stream, steps):
     """bf16: the same run with the fp32 exhaustive search (the precision
-    comparison).  surrogate: the all-exact run (the ablation) and the final
-    pose mean / spread of the surrogate run against it."""
+    comparison; same metric).  surrogate: the all-exact run (the ablation) and
+    the final pose mean / spread of the surrogate run against it.  set_ref()
+    sets the reference (and its normals for the point-to-plane metric)."""
     import ctypes
     q = S.sicp_params()
     ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
     if nn == "bf16":
-        q.nn_mode = S.SICP_NN_BRUTE_FP32
-        run = lambda: (S.sicp_set_reference(ctx, ref_d), S.sicp_register(ctx, src_d, par_d, q))[1]
+        q.nn_mode = S.SICP_NN_BRUTE_FP32 | (p.nn_mode & S.SICP_POINT_TO_PLANE)
+        run = lambda: (set_ref(), S.sicp_register(ctx, src_d, par_d, q))[1]
         name = "exhaustive fp32 search"
     else:
         q.nn_mode = S.SICP_NN_GRID
@@ -503,7 +504,7 @@ def compare_paths(S, ctx, nn, p, ref_d, src_d, par_d, cfg, K, flush, stream, ste
     ms = timed_runs(run, flush, stream, steps)
     th_o, mean_o, cov_o = [np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in run()]
     if nn != "surrogate":
-        S.sicp_set_reference(ctx, ref_d)
+        set_ref()
     th_s, mean_s, cov_s = [np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in S.sicp_register(ctx, src_d, par_d, p)]
     sd_o, sd_s = np.sqrt(np.diag(cov_o)), np.sqrt(np.diag(cov_s))
     return {"other": name, "other_value": K * cfg["m"] * cfg["T"] / (ms / 1e3),

@@ -60,7 +60,8 @@ extern "C" {
 #define SICP_NN_GRID 2          /* uniform voxel grid, exact */
 #define SICP_NN_SURROGATE 3     /* learned closest-point field, then exact grid */
 /* Metric flag, OR-ed into the search mode of sicp_register (nn_mode) and
- * sicp_icp_grad (mode), with SICP_NN_GRID or SICP_NN_BRUTE_FP32: the
+ * sicp_icp_grad (mode), with SICP_NN_GRID, SICP_NN_BRUTE_FP32 or
+ * SICP_NN_BRUTE_BF16 (not with the learned field): the
  * point-to-plane error, which the paper uses for its method comparison and
  * trajectory errors without printing it.  Correspondences stay the nearest
  * reference point r (Eq. correspondences); the residual becomes

@@ -32,7 +32,7 @@ SICP_NN_BRUTE_FP32 = 0
 SICP_NN_BRUTE_BF16 = 1
 SICP_NN_GRID = 2
 SICP_NN_SURROGATE = 3
-SICP_POINT_TO_PLANE = 0x100   # metric flag, OR-ed into nn_mode / mode (grid or fp32 exhaustive search)
+SICP_POINT_TO_PLANE = 0x100   # metric flag, OR-ed into nn_mode / mode (with the grid, fp32 or bf16 search)
 
 _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOSURROGATE"}
 

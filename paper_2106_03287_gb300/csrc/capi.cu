@@ -148,8 +148,8 @@ int read_flags(sicp_ctx* ctx, int* flags_host) {
 int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
     if (mode & SICP_POINT_TO_PLANE) {
         const int32_t base = mode & ~SICP_POINT_TO_PLANE;
-        if (base != SICP_NN_GRID && base != SICP_NN_BRUTE_FP32)
-            return set_err(ctx, SICP_EINVAL, "the point-to-plane metric works with SICP_NN_GRID or SICP_NN_BRUTE_FP32");
+        if (base != SICP_NN_GRID && base != SICP_NN_BRUTE_FP32 && base != SICP_NN_BRUTE_BF16)
+            return set_err(ctx, SICP_EINVAL, "the point-to-plane metric works with the exact searches (grid, FP32, BF16)");
         if (ctx->normals_k == 0)
             return set_err(ctx, SICP_ENOREF, "the point-to-plane metric needs sicp_reference_normals on this reference");
         return SICP_OK;
@@ -528,7 +528,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
     } else if (bf) {
         SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, m, g.theta, K, (float*)ctx->partial.p, d_g, out_nn ? d_nn : nullptr,
-                                   (int*)ctx->flags.p + 3));
+                                   (int*)ctx->flags.p + 3, g.normals));
     } else {
         SICP_CUDA(launch_grad(ctx, mode, g));
         if (mode != SICP_NN_GRID)
@@ -778,7 +778,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
                                                 (int*)ctx->flags.p + 3));
             else if (bf)
                 SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, p.m, theta, K, (float*)ctx->partial.p, (float*)ctx->gbar.p,
-                                           nullptr, (int*)ctx->flags.p + 3));
+                                           nullptr, (int*)ctx->flags.p + 3, g.normals));
             else
                 SICP_CUDA(launch_grad(ctx, exact_mode, g));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));

@@ -315,9 +315,10 @@ cudaError_t bf16_kernel_attrs();
 int bf16_prepare(sicp_ctx* ctx);   // reference tiles of the current reference (needs the grid)
 // err: set when a bounded wait gave up
 cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* idx, float* d2, int* err);
-// per-query gradient terms into qterms [K][m][6], then gbar [K][6]; out_nn [K][m] or null
+// per-query gradient terms into qterms [K][m][6], then gbar [K][6]; out_nn [K][m] or null;
+// normals (unit, by original index) select the point-to-plane metric, null point-to-point
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
-                             float* qterms, float* gbar, int32_t* out_nn, int* err);
+                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals);
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);

@@ -141,6 +141,7 @@ struct BfArgs {
     float* out_d2;             // grad = 0
     float* qterms;             // grad = 1: [K][m][6]
     int* err;
+    const float4* normals;     // grad = 1, point-to-plane: unit normals by original index; null: point-to-point
 };
 
 // Wait for phase `parity` of the mbarrier; false (and the error flag set)
@@ -390,8 +391,9 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs a) {
                         Pose P;
                         make_pose(a.theta + 6 * j, P);
                         const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
-                        grad_terms(P, make_float3(s4.x, s4.y, s4.z), make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z),
-                                   t6);
+                        float3 dv = make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z);
+                        if (a.normals) dv = plane_residual(__ldg(a.normals + bi), dv);
+                        grad_terms(P, make_float3(s4.x, s4.y, s4.z), dv, t6);
                     }
 #pragma unroll
                     for (int cc = 0; cc < 6; ++cc) a.qterms[o * 6 + cc] = t6[cc];
@@ -469,8 +471,9 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
 }
 
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
-                             float* qterms, float* gbar, int32_t* out_nn, int* err) {
+                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals) {
     BfArgs a = bf_args(ctx, err);
+    a.normals = normals;
     a.grad = 1;
     a.src = src;
     a.mb = mb;

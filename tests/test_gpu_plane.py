@@ -26,7 +26,7 @@ from paper_2106_03287_gb300 import synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 PL = S.SICP_POINT_TO_PLANE
-MODES = [S.SICP_NN_GRID, S.SICP_NN_BRUTE_FP32]
+MODES = [S.SICP_NN_GRID, S.SICP_NN_BRUTE_FP32, S.SICP_NN_BRUTE_BF16]
 
 
 @pytest.fixture(scope="module")
@@ -130,6 +130,21 @@ def test_plane_gradient_full_size_kinect(ctx):
     _check_plane_grad(ctx, d["ref"], d["src"], d["particles"], mb, S.SICP_NN_GRID, nrm)
 
 
+def test_plane_bf16_equals_fp32_and_lidar_full_size(ctx):
+    """The tensor-core search finds the fp32 search's correspondences, so with
+    the point-to-plane metric the two gradients are sums of the same terms in
+    another order (1e-5 relative); at LiDAR sizes (100,000 queries against the
+    ~112,000-point scan) as well."""
+    d = synth.make_lidar_problem(1)
+    S.sicp_set_reference(ctx, d["ref"])
+    S.sicp_reference_normals(ctx, 10, want=False)
+    mb = O.minibatch(7, 0, d["src"].shape[0], 500)
+    g_bf, nn_bf = S.sicp_icp_grad(ctx, d["src"], mb, d["particles"], S.SICP_NN_BRUTE_BF16 | PL)
+    g_fp, nn_fp = S.sicp_icp_grad(ctx, d["src"], mb, d["particles"], S.SICP_NN_BRUTE_FP32 | PL)
+    assert np.array_equal(nn_bf, nn_fp)
+    assert np.all(np.abs(g_bf - g_fp) <= 1e-5 * np.abs(g_fp).max(1, keepdims=True))
+
+
 def test_plane_run_recovers_known_pose(ctx):
     """K = 1 with the point-to-plane metric on a noise-free box lands on the
     generating pose (1 mm, 0.05 deg), as the oracle does."""
@@ -185,10 +200,9 @@ def test_plane_errors(ctx):
             S.sicp_reference_normals(ctx, k)
         assert e.value.code == S.SICP_EINVAL
     S.sicp_reference_normals(ctx, 10, want=False)
-    for mode in (S.SICP_NN_BRUTE_BF16 | PL, S.SICP_NN_SURROGATE | PL):
-        with pytest.raises(S.SicpError) as e:
-            S.sicp_icp_grad(ctx, d["src"], mb, d["particles"], mode)
-        assert e.value.code == S.SICP_EINVAL
+    with pytest.raises(S.SicpError) as e:                    # the learned field has no reference point
+        S.sicp_icp_grad(ctx, d["src"], mb, d["particles"], S.SICP_NN_SURROGATE | PL)
+    assert e.value.code == S.SICP_EINVAL
     S.sicp_icp_grad(ctx, d["src"], mb, d["particles"], S.SICP_NN_GRID | PL)
     S.sicp_set_reference(ctx, d["ref"])                         # a new reference drops the normals
     with pytest.raises(S.SicpError) as e:
