@@ -61,7 +61,7 @@ _i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes
 class _Params(ctypes.Structure):
     _fields_ = [("T", _i32), ("m", _i32), ("lr", _f64), ("beta1", _f64), ("beta2", _f64),
                 ("eps", _f64), ("seed", _u64), ("prior", _i32), ("mu", _f64 * 6),
-                ("sigma", _f64 * 3), ("kappa", _f64 * 3), ("normals", _p)]
+                ("sigma", _f64 * 3), ("kappa", _f64 * 3), ("normals", _p), ("independent", _i32)]
 
 
 def _setup(L):
@@ -126,6 +126,7 @@ class Params:
     sigma: tuple = (1.0,) * 3
     kappa: tuple = (1.0,) * 3
     normals: object = None     # None: point-to-point; M x 3 unit normals: point-to-plane (R16)
+    independent: bool = False  # independent SGD-ICP runs, no Stein coupling (R17)
 
     def c(self) -> _Params:
         p = _Params()
@@ -134,6 +135,7 @@ class Params:
         p.mu[:] = list(self.mu)
         p.sigma[:] = list(self.sigma)
         p.kappa[:] = list(self.kappa)
+        p.independent = 1 if self.independent else 0
         if self.normals is not None:
             self._normals64 = _f64a(self.normals)     # kept alive with the parameters
             p.normals = _ptr(self._normals64)
@@ -388,3 +390,39 @@ def mlp_split(params):
         out.append(p[o:o + n].reshape(sh))
         o += n
     return out
+
+
+# ---------------------------------------------------------------- distribution quality (reading R17)
+
+def gaussian_kl(m0, S0, m1, S1):
+    """KL(N(m0, S0) || N(m1, S1)) in closed form (float64):
+    1/2 [tr(S1^-1 S0) + (m1 - m0)^T S1^-1 (m1 - m0) - d + ln det S1 - ln det S0]."""
+    m0, m1 = np.asarray(m0, np.float64), np.asarray(m1, np.float64)
+    S0, S1 = np.asarray(S0, np.float64), np.asarray(S1, np.float64)
+    d = m0.shape[0]
+    S1i = np.linalg.inv(S1)
+    dm = m1 - m0
+    _, ld0 = np.linalg.slogdet(S0)
+    _, ld1 = np.linalg.slogdet(S1)
+    return 0.5 * (np.trace(S1i @ S0) + dm @ S1i @ dm - d + ld1 - ld0)
+
+
+def _gauss_logpdf(x, m, S):
+    d = m.shape[0]
+    L = np.linalg.cholesky(S)
+    y = np.linalg.solve(L, (x - m).T)
+    return -0.5 * np.sum(y * y, axis=0) - np.log(np.diag(L)).sum() - 0.5 * d * np.log(2 * np.pi)
+
+
+def gaussian_ovl(m0, S0, m1, S1, z0, z1):
+    """Overlapping coefficient, integral of min(p0, p1), of two Gaussians by
+    Monte Carlo on given standard-normal draws z0, z1 ([n][d] each):
+    1/2 [mean over x = m0 + L0 z0 of min(1, p1/p0) + mean over x = m1 + L1 z1
+    of min(1, p0/p1)], L the Cholesky factors."""
+    m0, m1 = np.asarray(m0, np.float64), np.asarray(m1, np.float64)
+    S0, S1 = np.asarray(S0, np.float64), np.asarray(S1, np.float64)
+    x0 = m0 + np.asarray(z0, np.float64) @ np.linalg.cholesky(S0).T
+    x1 = m1 + np.asarray(z1, np.float64) @ np.linalg.cholesky(S1).T
+    a = np.minimum(1.0, np.exp(_gauss_logpdf(x0, m1, S1) - _gauss_logpdf(x0, m0, S0)))
+    b = np.minimum(1.0, np.exp(_gauss_logpdf(x1, m0, S0) - _gauss_logpdf(x1, m1, S1)))
+    return 0.5 * (a.mean() + b.mean())

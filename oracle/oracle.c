@@ -46,6 +46,11 @@
  *      neighbours ranked by the fp32 squared distance fmaf(dx, dx, fmaf(dy,
  *      dy, dz * dz)) with dx = r_x - q_x in fp32, ties to the lower index (the
  *      decision is taken in the kernel's precision); the covariance in fp64.
+ *  R17 Monte Carlo ground truth (the experiments' reference distribution:
+ *      many SGD-ICP runs from spread initial poses): with `independent` set,
+ *      every particle is its own SGD-ICP run (Sec. III-B) with Adam on its own
+ *      log-posterior gradient, phi_j = G_j, exactly the K = 1 update; the runs
+ *      share the per-iteration minibatch of R11.
  *  R15 circular moments (for rotation blocks whose particles straddle +-pi):
  *      each angle's mean is the circular mean atan2(sum sin, sum cos) (0 if
  *      both sums vanish); the covariance is that of the deviations
@@ -508,6 +513,7 @@ typedef struct {
     int32_t prior;
     double mu[6], sigma[3], kappa[3];
     const double* normals;   /* NULL: point-to-point; else M x 3: point-to-plane (R16) */
+    int32_t independent;     /* 1: independent SGD-ICP runs, phi_j = G_j (R17) */
 } or_params;
 
 /* Iteration t (0-based) in place on th, mom, vel (each K x 6).  Optional
@@ -524,9 +530,13 @@ OR_EXPORT void or_step(const float* ref, int64_t M, const float* src, int64_t N,
     or_minibatch(p->seed, t, N, p->m, mb);
     or_icp_grad(ref, M, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
     or_log_post_grad(th, gbar, K, (double)N, p->prior, p->mu, p->sigma, p->kappa, G);
-    double h_t, h_r;
-    or_bandwidths(th, K, &h_t, &h_r);
-    or_stein_phi(th, G, K, h_t, h_r, phi);
+    double h_t = 1.0, h_r = 1.0;
+    if (p->independent) {
+        memcpy(phi, G, sizeof(double) * 6 * (size_t)K);
+    } else {
+        or_bandwidths(th, K, &h_t, &h_r);
+        or_stein_phi(th, G, K, h_t, h_r, phi);
+    }
     for (int64_t i = 0; i < 6 * (int64_t)K; ++i) g[i] = -phi[i];
     or_adam(th, mom, vel, g, 6 * (int64_t)K, t + 1, p->lr, p->beta1, p->beta2, p->eps);
     if (gbar_out) memcpy(gbar_out, gbar, sizeof(double) * 6 * (size_t)K);

@@ -300,6 +300,63 @@ def test_point_to_plane_run_recovers_known_pose_noise_free():
     assert np.abs(err[3:]).max() < math.radians(0.05)
 
 
+# ---------------------------------------------------------------- Monte Carlo ground truth, KL, OVL (R17)
+
+def test_independent_runs_are_single_particle_runs():
+    """Independent mode: K particles evolve exactly as K separate K = 1 runs
+    (SGD-ICP with Adam) with the same minibatch stream."""
+    d = synth.make_box_problem(2, M=600, N=200, K=5)
+    p = O.Params(T=20, m=40, seed=3, independent=True)
+    th, _, _ = O.register(d["ref"], d["src"], d["particles"], p)
+    for j in range(5):
+        one, _, _ = O.register(d["ref"], d["src"], d["particles"][j:j + 1], O.Params(T=20, m=40, seed=3))
+        assert np.array_equal(th[j], one[0])
+    coupled, _, _ = O.register(d["ref"], d["src"], d["particles"], O.Params(T=20, m=40, seed=3))
+    assert not np.array_equal(coupled, th)
+
+
+def _random_spd(rng, d, scale):
+    A = rng.normal(size=(d, d))
+    return scale * (A @ A.T / d + 0.2 * np.eye(d))
+
+
+def test_gaussian_kl_closed_forms_and_monte_carlo():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(12)
+    m0, m1 = rng.normal(size=6), rng.normal(size=6)
+    S0, S1 = _random_spd(rng, 6, 0.5), _random_spd(rng, 6, 0.8)
+    assert abs(O.gaussian_kl(m0, S0, m0, S0)) < 1e-12
+    # one axis differs, the rest identical: the 1-D formula
+    mu0, s0, mu1, s1 = 0.3, 0.7, -0.2, 1.3
+    D0, D1 = np.eye(6), np.eye(6)
+    D0[2, 2], D1[2, 2] = s0 ** 2, s1 ** 2
+    a, b = np.zeros(6), np.zeros(6)
+    a[2], b[2] = mu0, mu1
+    one_d = math.log(s1 / s0) + (s0 ** 2 + (mu0 - mu1) ** 2) / (2 * s1 ** 2) - 0.5
+    assert abs(O.gaussian_kl(a, D0, b, D1) - one_d) < 1e-12
+    # E_p0[log p0 - log p1] by Monte Carlo with scipy's densities
+    x = stats.multivariate_normal(m0, S0).rvs(400_000, random_state=5)
+    diff = stats.multivariate_normal(m0, S0).logpdf(x) - stats.multivariate_normal(m1, S1).logpdf(x)
+    assert abs(O.gaussian_kl(m0, S0, m1, S1) - diff.mean()) < 4 * diff.std() / math.sqrt(x.shape[0])
+
+
+def test_gaussian_ovl_closed_forms():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(13)
+    n = 200_000
+    z0, z1 = rng.standard_normal((n, 6)), rng.standard_normal((n, 6))
+    m0 = rng.normal(size=6)
+    S = _random_spd(rng, 6, 0.3)
+    assert O.gaussian_ovl(m0, S, m0, S, z0, z1) == 1.0
+    # equal covariances: OVL = 2 Phi(-delta / 2), delta the Mahalanobis distance of the means
+    for shift in (0.3, 1.0, 2.5):
+        m1 = m0 + shift * np.linalg.cholesky(S) @ np.r_[1.0, np.zeros(5)]
+        expect = 2 * stats.norm.cdf(-shift / 2)
+        assert abs(O.gaussian_ovl(m0, S, m1, S, z0, z1) - expect) < 0.005, shift
+    far = m0 + 100.0
+    assert O.gaussian_ovl(m0, S, far, S, z0, z1) < 1e-6
+
+
 def test_icp_gradient_single_point_closed_form():
     ref = np.array([[0.3, -0.2, 0.5]], np.float32)
     src = np.array([[0.1, 0.4, -0.2]], np.float32)
