@@ -48,9 +48,9 @@
  *      decision is taken in the kernel's precision); the covariance in fp64.
  *  R17 Monte Carlo ground truth (the experiments' reference distribution:
  *      many SGD-ICP runs from spread initial poses): with `independent` set,
- *      every particle is its own SGD-ICP run (Sec. III-B) with Adam on its own
- *      log-posterior gradient, phi_j = G_j, exactly the K = 1 update; the runs
- *      share the per-iteration minibatch of R11.
+ *      every particle j is its own SGD-ICP run (Sec. III-B): its own
+ *      minibatch stream (R11 with seed + j), Adam on its own log-posterior
+ *      gradient, phi_j = G_j -- exactly the K = 1 run with seed + j.
  *  R15 circular moments (for rotation blocks whose particles straddle +-pi):
  *      each angle's mean is the circular mean atan2(sum sin, sum cos) (0 if
  *      both sums vanish); the covariance is that of the deviations
@@ -527,8 +527,15 @@ OR_EXPORT void or_step(const float* ref, int64_t M, const float* src, int64_t N,
     double* G = (double*)malloc(sizeof(double) * 6 * (size_t)K);
     double* phi = (double*)malloc(sizeof(double) * 6 * (size_t)K);
     double* g = (double*)malloc(sizeof(double) * 6 * (size_t)K);
-    or_minibatch(p->seed, t, N, p->m, mb);
-    or_icp_grad(ref, M, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
+    if (p->independent) {
+        for (int32_t j = 0; j < K; ++j) {
+            or_minibatch(p->seed + (uint64_t)j, t, N, p->m, mb);
+            or_icp_grad(ref, M, src, mb, p->m, th + 6 * j, 1, p->normals, gbar + 6 * j, NULL, NULL);
+        }
+    } else {
+        or_minibatch(p->seed, t, N, p->m, mb);
+        or_icp_grad(ref, M, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
+    }
     or_log_post_grad(th, gbar, K, (double)N, p->prior, p->mu, p->sigma, p->kappa, G);
     double h_t = 1.0, h_r = 1.0;
     if (p->independent) {

@@ -303,13 +303,13 @@ def test_point_to_plane_run_recovers_known_pose_noise_free():
 # ---------------------------------------------------------------- Monte Carlo ground truth, KL, OVL (R17)
 
 def test_independent_runs_are_single_particle_runs():
-    """Independent mode: K particles evolve exactly as K separate K = 1 runs
-    (SGD-ICP with Adam) with the same minibatch stream."""
+    """Independent mode: particle j evolves exactly as the separate K = 1 run
+    (SGD-ICP with Adam) with seed + j."""
     d = synth.make_box_problem(2, M=600, N=200, K=5)
     p = O.Params(T=20, m=40, seed=3, independent=True)
     th, _, _ = O.register(d["ref"], d["src"], d["particles"], p)
     for j in range(5):
-        one, _, _ = O.register(d["ref"], d["src"], d["particles"][j:j + 1], O.Params(T=20, m=40, seed=3))
+        one, _, _ = O.register(d["ref"], d["src"], d["particles"][j:j + 1], O.Params(T=20, m=40, seed=3 + j))
         assert np.array_equal(th[j], one[0])
     coupled, _, _ = O.register(d["ref"], d["src"], d["particles"], O.Params(T=20, m=40, seed=3))
     assert not np.array_equal(coupled, th)
