@@ -70,6 +70,14 @@ extern "C" {
  * rotation_gradient with the residual vector replaced by e n).  Needs
  * sicp_reference_normals on the current reference. */
 #define SICP_POINT_TO_PLANE 0x100
+/* Flag for sicp_register (nn_mode), with an exact search: every particle j is
+ * an independent SGD-ICP run (Sec. III-B) with its own minibatch stream (that
+ * of seed + j) and Adam on its own log-posterior gradient, phi_j = G_j,
+ * instead of the Stein coupling; particle j then evolves exactly as the
+ * K = 1 run with seed + j.  This is the Monte Carlo reference distribution of
+ * the paper's experiments: many SGD-ICP runs from spread initial poses.
+ * Needs 4 K T m bytes of minibatch indices. */
+#define SICP_INDEPENDENT 0x200
 
 typedef struct sicp_ctx sicp_ctx;
 
@@ -242,6 +250,25 @@ int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6
  * SICP_ENOREF (no reference), SICP_EINVAL (k outside [3, min(32, M)]),
  * SICP_ENOMEM, SICP_ECUDA. */
 int sicp_reference_normals(sicp_ctx* ctx, int32_t k, float* out_normals, int on_device);
+
+/* Distribution quality (no context; float64).  The paper scores a pose
+ * distribution against its Monte Carlo reference (SICP_INDEPENDENT runs from
+ * spread initial poses) by the KL divergence, computed from the samples'
+ * covariances, and by the overlapping coefficient (OVL).  Both act on the
+ * Gaussians N(mean0, cov0) and N(mean1, cov1) of dimension d (1..64;
+ * covariances row-major d x d, symmetric positive definite).
+ * sicp_gaussian_kl: *out = KL(N0 || N1) = 1/2 [tr(S1^-1 S0) + (m1 - m0)^T
+ * S1^-1 (m1 - m0) - d + ln det S1 - ln det S0].
+ * sicp_gaussian_ovl: *out = the integral of min(p0, p1), estimated from the
+ * caller's standard-normal draws z0, z1 ([n][d] each, n >= 1) as 1/2 [mean
+ * over x = m0 + L0 z0 of min(1, p1(x)/p0(x)) + mean over x = m1 + L1 z1 of
+ * min(1, p0(x)/p1(x))], L the Cholesky factors; 1 for identical Gaussians.
+ * Errors: SICP_EINVAL (null pointer, d or n out of range, a non-finite value,
+ * a covariance that is not positive definite). */
+int sicp_gaussian_kl(const double* mean0, const double* cov0, const double* mean1, const double* cov1,
+                     int32_t d, double* out);
+int sicp_gaussian_ovl(const double* mean0, const double* cov0, const double* mean1, const double* cov1,
+                      int32_t d, const double* z0, const double* z1, int64_t n, double* out);
 
 /* The same moments with circular statistics for the three angles, for
  * particle sets whose rotations straddle +-pi (the plain mean of angles near

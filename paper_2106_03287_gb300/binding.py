@@ -33,6 +33,7 @@ SICP_NN_BRUTE_BF16 = 1
 SICP_NN_GRID = 2
 SICP_NN_SURROGATE = 3
 SICP_POINT_TO_PLANE = 0x100   # metric flag, OR-ed into nn_mode / mode (with the grid, fp32 or bf16 search)
+SICP_INDEPENDENT = 0x200      # sicp_register flag: independent SGD-ICP runs (the Monte Carlo reference)
 
 _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOSURROGATE"}
 
@@ -40,7 +41,7 @@ _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
-    "sicp_moments_circular", "sicp_reference_normals", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
+    "sicp_moments_circular", "sicp_reference_normals", "sicp_gaussian_kl", "sicp_gaussian_ovl", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
 )
@@ -104,6 +105,8 @@ def lib() -> ctypes.CDLL:
             "sicp_surrogate_save": (ctypes.c_int, [P, ctypes.c_char_p]),
             "sicp_surrogate_load": (ctypes.c_int, [P, ctypes.c_char_p]),
             "sicp_reference_normals": (ctypes.c_int, [P, I32, P, ctypes.c_int]),
+            "sicp_gaussian_kl": (ctypes.c_int, [P, P, P, P, I32, P]),
+            "sicp_gaussian_ovl": (ctypes.c_int, [P, P, P, P, I32, P, P, ctypes.c_int64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -312,6 +315,49 @@ def sicp_reference_normals(ctx, k: int = 10, want: bool = True, device: bool = F
     _check(ctx, lib().sicp_reference_normals(ctx, int(k), _ptr(out, np.float32) if out is not None else None,
                                              1 if device else 0))
     return out
+
+
+def _gauss_args(m0, S0, m1, S1):
+    m0, m1 = np.ascontiguousarray(m0, np.float64).ravel(), np.ascontiguousarray(m1, np.float64).ravel()
+    d = m0.shape[0]
+    S0 = np.ascontiguousarray(S0, np.float64).reshape(d, d)
+    S1 = np.ascontiguousarray(S1, np.float64).reshape(d, d)
+    return m0, S0, m1, S1, d
+
+
+def _plain_check(rc, what):
+    if rc != SICP_OK:
+        raise SicpError(rc, what)
+
+
+def sicp_gaussian_kl(m0, S0, m1, S1) -> float:
+    """KL(N(m0, S0) || N(m1, S1))."""
+    m0, S0, m1, S1, d = _gauss_args(m0, S0, m1, S1)
+    out = ctypes.c_double()
+    _plain_check(lib().sicp_gaussian_kl(_ptr(m0, np.float64), _ptr(S0, np.float64), _ptr(m1, np.float64),
+                                        _ptr(S1, np.float64), d, ctypes.byref(out)),
+                 "sicp_gaussian_kl: bad sizes, non-finite values or a covariance that is not positive definite")
+    return out.value
+
+
+def sicp_gaussian_ovl(m0, S0, m1, S1, n: int = 100_000, seed: int = 0, z0=None, z1=None) -> float:
+    """Overlapping coefficient of N(m0, S0) and N(m1, S1) by Monte Carlo; the
+    standard-normal draws z0, z1 ([n][d]) come from numpy's generator seeded
+    with `seed` unless given."""
+    m0, S0, m1, S1, d = _gauss_args(m0, S0, m1, S1)
+    if z0 is None or z1 is None:
+        rng = np.random.default_rng(seed)
+        z0, z1 = rng.standard_normal((n, d)), rng.standard_normal((n, d))
+    z0 = np.ascontiguousarray(z0, np.float64).reshape(-1, d)
+    z1 = np.ascontiguousarray(z1, np.float64).reshape(-1, d)
+    if z0.shape != z1.shape:
+        raise ValueError("z0 and z1 must have the same shape")
+    out = ctypes.c_double()
+    _plain_check(lib().sicp_gaussian_ovl(_ptr(m0, np.float64), _ptr(S0, np.float64), _ptr(m1, np.float64),
+                                         _ptr(S1, np.float64), d, _ptr(z0, np.float64), _ptr(z1, np.float64),
+                                         z0.shape[0], ctypes.byref(out)),
+                 "sicp_gaussian_ovl: bad sizes, non-finite values or a covariance that is not positive definite")
+    return out.value
 
 
 def sicp_moments_circular(ctx, particles):

@@ -145,10 +145,13 @@ int read_flags(sicp_ctx* ctx, int* flags_host) {
     return sync(ctx);
 }
 
-int check_mode(sicp_ctx* ctx, int32_t mode, bool allow_surrogate) {
-    if (mode & SICP_POINT_TO_PLANE) {
-        const int32_t base = mode & ~SICP_POINT_TO_PLANE;
-        if (base != SICP_NN_GRID && base != SICP_NN_BRUTE_FP32 && base != SICP_NN_BRUTE_BF16)
+// Search mode plus flags: `allowed` is the set of flag bits the caller accepts.
+int check_mode(sicp_ctx* ctx, int32_t mode, int32_t allowed, bool allow_surrogate) {
+    const int32_t flags = mode & (SICP_POINT_TO_PLANE | SICP_INDEPENDENT);
+    if (flags & ~allowed) return set_err(ctx, SICP_EINVAL, "mode flags 0x%x are not accepted here", flags & ~allowed);
+    mode &= ~flags;
+    if (flags & SICP_POINT_TO_PLANE) {
+        if (mode != SICP_NN_GRID && mode != SICP_NN_BRUTE_FP32 && mode != SICP_NN_BRUTE_BF16)
             return set_err(ctx, SICP_EINVAL, "the point-to-plane metric works with the exact searches (grid, FP32, BF16)");
         if (ctx->normals_k == 0)
             return set_err(ctx, SICP_ENOREF, "the point-to-plane metric needs sicp_reference_normals on this reference");
@@ -411,7 +414,7 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
     if (n < 0 || n > kMaxN) return set_err(ctx, SICP_EINVAL, "query count out of range");
     if (n == 0) return SICP_OK;
     if (!q || !out_idx) return set_err(ctx, SICP_EINVAL, "null query or output pointer");
-    int rc = check_mode(ctx, mode, false);
+    int rc = check_mode(ctx, mode, 0, false);
     if (rc) return rc;
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     if (!on_device && !host_finite(q, 3 * n)) return set_err(ctx, SICP_EINVAL, "non-finite query");
@@ -460,7 +463,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     const bool surr = mode == SICP_NN_SURROGATE;
     if (surr && (out_nn || (int64_t)K * m > ((int64_t)1 << 24)))
         return set_err(ctx, SICP_EINVAL, "surrogate mode needs out_nn = NULL and K * m <= 2^24");
-    int rc = check_mode(ctx, mode, true);
+    int rc = check_mode(ctx, mode, SICP_POINT_TO_PLANE, true);
     if (rc) return rc;
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     const bool plane = (mode & SICP_POINT_TO_PLANE) != 0;
@@ -520,6 +523,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.gbar = d_g;
     g.inv_m = 1.f / (float)m;
     g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
+    g.mb_stride = 0;
     if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     g.done = (unsigned*)ctx->done.p;
     SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
@@ -528,7 +532,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
     } else if (bf) {
         SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, m, g.theta, K, (float*)ctx->partial.p, d_g, out_nn ? d_nn : nullptr,
-                                   (int*)ctx->flags.p + 3, g.normals));
+                                   (int*)ctx->flags.p + 3, g.normals, 0));
     } else {
         SICP_CUDA(launch_grad(ctx, mode, g));
         if (mode != SICP_NN_GRID)
@@ -650,14 +654,16 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if (p.m < 1 || p.m > N) return set_err(ctx, SICP_EINVAL, "minibatch m=%d outside [1, N=%lld]", p.m, (long long)N);
     int rc = check_params(ctx, p);
     if (rc) return rc;
-    if ((rc = check_mode(ctx, p.nn_mode, true))) return rc;
+    if ((rc = check_mode(ctx, p.nn_mode, SICP_POINT_TO_PLANE | SICP_INDEPENDENT, true))) return rc;
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
         return set_err(ctx, SICP_EINVAL, "non-finite input");
     DeviceScope ds(ctx->device);
     const bool plane = (p.nn_mode & SICP_POINT_TO_PLANE) != 0;
-    const int32_t nn_mode = p.nn_mode & ~SICP_POINT_TO_PLANE;
+    const bool indep = (p.nn_mode & SICP_INDEPENDENT) != 0;
+    const int32_t nn_mode = p.nn_mode & ~(SICP_POINT_TO_PLANE | SICP_INDEPENDENT);
     const bool surr = nn_mode == SICP_NN_SURROGATE;
+    if (surr && indep) return set_err(ctx, SICP_EINVAL, "independent runs use an exact search (grid, FP32, BF16)");
     if (surr && (int64_t)K * p.m > ((int64_t)1 << 24))
         return set_err(ctx, SICP_EINVAL, "surrogate mode needs K * m <= 2^24 queries per iteration");
     const bool bf = nn_mode == SICP_NN_BRUTE_BF16;
@@ -671,7 +677,9 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     // partial sums of the exhaustive kernel, or the surrogate's per-query terms
     const size_t partial_floats = 6 * (size_t)K * (size_t)((surr_T > 0 || bf) && p.m > chunks ? p.m : chunks);
     if ((rc = ensure(ctx, ctx->src4, sizeof(float4) * N))) return rc;
-    if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m))) return rc;
+    // one minibatch row per iteration, or one per iteration and independent run
+    if ((rc = ensure(ctx, ctx->mb, sizeof(int32_t) * (size_t)(p.T > 0 ? p.T : 1) * p.m * (indep ? (size_t)K : 1))))
+        return rc;
     if ((rc = ensure(ctx, ctx->theta, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->adam_m, b_th))) return rc;
     if ((rc = ensure(ctx, ctx->adam_v, b_th))) return rc;
@@ -754,7 +762,10 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
     const bool use_graph = getenv("SICP_NO_GRAPH") == nullptr;
     auto record = [&](GraphSlot* prof) -> int {
-        SICP_CUDA(launch_minibatch(p.seed, t0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
+        if (indep)
+            SICP_CUDA(launch_minibatch_runs(p.seed, t0, p.T, N, p.m, K, (int32_t*)ctx->mb.p, ctx->stream));
+        else
+            SICP_CUDA(launch_minibatch(p.seed, t0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
         GradArgs g;
         g.src = (const float4*)ctx->src4.p;
         g.m = p.m;
@@ -767,6 +778,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         g.done = (unsigned*)ctx->done.p;
         g.inv_m = 1.f / (float)p.m;
         g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
+        g.mb_stride = indep ? (int64_t)p.T * p.m : 0;   // run j's row of iteration t: mb[(j T + t) m]
         int np = 0;
         for (int32_t t = 0; t < p.T; ++t) {
             const bool timed = prof && stride > 0 && (t % stride) == 0;
@@ -778,7 +790,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
                                                 (int*)ctx->flags.p + 3));
             else if (bf)
                 SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, p.m, theta, K, (float*)ctx->partial.p, (float*)ctx->gbar.p,
-                                           nullptr, (int*)ctx->flags.p + 3, g.normals));
+                                           nullptr, (int*)ctx->flags.p + 3, g.normals, g.mb_stride));
             else
                 SICP_CUDA(launch_grad(ctx, exact_mode, g));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
@@ -792,7 +804,10 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
             a.arrive = (unsigned*)(med_state + 2);
             a.err = (int*)ctx->flags.p + 3;
             a.gen = (uint32_t)(t + 1);
-            SICP_CUDA(launch_stein_adam(a, ctx->stream));
+            if (indep)
+                SICP_CUDA(launch_adam_independent(a, ctx->stream));
+            else
+                SICP_CUDA(launch_stein_adam(a, ctx->stream));
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;
         }

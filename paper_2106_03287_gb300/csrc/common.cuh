@@ -228,6 +228,9 @@ cudaError_t kernel_attrs_init();
 
 cudaError_t launch_minibatch(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
                              int32_t* out, cudaStream_t s);
+// Independent runs: run j draws the stream of seed + j; out [R][T][m].
+cudaError_t launch_minibatch_runs(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m, int32_t R,
+                                  int32_t* out, cudaStream_t s);
 
 // Per-query search of the whole reference (fp32 exhaustive).
 cudaError_t launch_nn_brute(const float4* ref, int64_t M, const float* q, int64_t n,
@@ -259,6 +262,9 @@ struct GradArgs {
     // point-to-plane metric: unit normals by original reference index (w
     // unused); null: point-to-point
     const float4* normals;
+    // minibatch entries between consecutive particles' rows: 0, one row
+    // shared by all particles; else particle j reads mb[j * mb_stride + k]
+    int64_t mb_stride;
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
 
@@ -288,6 +294,9 @@ struct SteinArgs {
     uint32_t gen;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
+// Independent runs (no Stein coupling): Adam on g = -G_j for every particle j,
+// the K = 1 update of the same kernel for each particle.
+cudaError_t launch_adam_independent(const SteinArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s);
 cudaError_t launch_moments_circular(const float* theta, int32_t K, double* out42, cudaStream_t s);
 
@@ -318,7 +327,8 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
 // per-query gradient terms into qterms [K][m][6], then gbar [K][6]; out_nn [K][m] or null;
 // normals (unit, by original index) select the point-to-plane metric, null point-to-point
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
-                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals);
+                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals,
+                             int64_t mb_stride);
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kGradMaxThreads) k_grad_brute(GradArgs a, cons
     const bool valid = k < a.m;
     float3 s = make_float3(0.f, 0.f, 0.f);
     if (valid) {
-        float4 s4 = a.src[a.mb[k]];
+        float4 s4 = a.src[a.mb[(int64_t)j * a.mb_stride + k]];
         s = make_float3(s4.x, s4.y, s4.z);
     }
     const float3 q = apply_pose(P, s);

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, Grid
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
     const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
-    const float3 s = make_float3(s4.x, s4.y, s4.z);
+    float3 s = make_float3(s4.x, s4.y, s4.z);
     const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
     Work w;
     Best B;
@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, Grid
     for (int i = 0; i < kSeq; ++i) {
         const int jl = warp * kSeq + i, j = j0 + jl;
         if (j >= a.K) break;                        // warp-uniform
+        if (a.mb_stride) {                          // independent runs: particle j's own minibatch
+            const float4 sj = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
+            s = make_float3(sj.x, sj.y, sj.z);
+        }
         const float3 q = apply_pose(P[jl], s);
         bool seeded = false;
         if (B.i != kNone) {

@@ -105,6 +105,13 @@ __global__ void __launch_bounds__(kThreads) k_minibatch(uint64_t seed, int64_t t
     minibatch_row(seed, t0 + blockIdx.x, N, m, out + (int64_t)blockIdx.x * m);
 }
 
+// grid (T, R): independent run j uses seed + j; row [j][t] of iteration t0 + t.
+__global__ void __launch_bounds__(kThreads) k_minibatch_runs(uint64_t seed, int64_t t0, int32_t T, int64_t N,
+                                                             int32_t m, int32_t* __restrict__ out) {
+    const int j = blockIdx.y, t = blockIdx.x;
+    minibatch_row(seed + (uint64_t)j, t0 + t, N, m, out + ((int64_t)j * T + t) * m);
+}
+
 // grid (T, P): problem p uses seed + p, its own source size and row [p][t].
 __global__ void __launch_bounds__(kThreads) k_minibatch_batched(uint64_t seed, int32_t T, int32_t m,
                                                                 const int64_t* __restrict__ src_off,
@@ -119,6 +126,13 @@ cudaError_t launch_minibatch_batched(uint64_t seed, int32_t T, int32_t m, int32_
                                      int32_t* out, cudaStream_t s) {
     if (T <= 0 || P <= 0) return cudaSuccess;
     k_minibatch_batched<<<dim3(T, P), kThreads, 0, s>>>(seed, T, m, src_off, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minibatch_runs(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m, int32_t R,
+                                  int32_t* out, cudaStream_t s) {
+    if (T <= 0 || R <= 0) return cudaSuccess;
+    k_minibatch_runs<<<dim3(T, R), kThreads, 0, s>>>(seed, t0, T, N, m, out);
     return cudaGetLastError();
 }
 

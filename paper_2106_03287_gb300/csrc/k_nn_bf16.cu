@@ -142,6 +142,7 @@ struct BfArgs {
     float* qterms;             // grad = 1: [K][m][6]
     int* err;
     const float4* normals;     // grad = 1, point-to-plane: unit normals by original index; null: point-to-point
+    int64_t mb_stride;         // grad = 1: minibatch entries between particles' rows (0: one shared row)
 };
 
 // Wait for phase `parity` of the mbarrier; false (and the error flag set)
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs a) {
                     const int k = (int)(g / a.K), j = (int)(g % a.K);
                     Pose P;
                     make_pose(a.theta + 6 * j, P);
-                    const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+                    const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
                     q = apply_pose(P, make_float3(s4.x, s4.y, s4.z));
                 } else {
                     q = make_float3(a.q[3 * g], a.q[3 * g + 1], a.q[3 * g + 2]);
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs a) {
                     if (found) {
                         Pose P;
                         make_pose(a.theta + 6 * j, P);
-                        const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+                        const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
                         float3 dv = make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z);
                         if (a.normals) dv = plane_residual(__ldg(a.normals + bi), dv);
                         grad_terms(P, make_float3(s4.x, s4.y, s4.z), dv, t6);
@@ -471,9 +472,11 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
 }
 
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
-                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals) {
+                             float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals,
+                             int64_t mb_stride) {
     BfArgs a = bf_args(ctx, err);
     a.normals = normals;
+    a.mb_stride = mb_stride;
     a.grad = 1;
     a.src = src;
     a.mb = mb;

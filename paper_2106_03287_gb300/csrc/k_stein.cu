@@ -41,6 +41,48 @@ __global__ void __launch_bounds__(kThreads) k_stein_adam(SteinArgs a, int P) {
     stein_adam_one_block(a, blockIdx.x / P, blockIdx.x % P, P);
 }
 
+// Independent SGD-ICP runs: for every particle j and component c, G = -N gbar
+// + grad log prior and Adam on g = -phi with phi = G, computed as the Stein
+// kernel computes them for K = 1 (the same partial sums in the same order;
+// the K = 1 Stein sum adds +0 to G and multiplies by 1), so each particle
+// follows exactly the run it would follow alone.  chunks == 1: one thread per
+// component; else one warp per component, lanes over the chunks.
+__global__ void k_adam_independent(SteinArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = 6 * (int64_t)a.K;
+    const int64_t idx = a.chunks == 1 ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                                      : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (idx >= n) return;
+    const int j = (int)(idx / 6), c = (int)(idx % 6);
+    float gb;
+    if (a.chunks == 1) {
+        gb = a.partial[idx];
+    } else {
+        float s = 0.f;
+        for (int ch = lane; ch < a.chunks; ch += 32) s += a.partial[((int64_t)ch * a.K + j) * 6 + c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane != 0) return;
+        gb = s;
+    }
+    const float x = a.theta[idx];
+    float pr = 0.f;
+    if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
+    const float G = fmaf(-a.N, gb * a.inv_m, pr);
+    const float phi = (G + 0.f) * 1.f;
+    if (a.out_phi) a.out_phi[idx] = phi;
+    const float omb1 = 1.f - a.beta1, omb2 = 1.f - a.beta2;
+    const float c1 = -expm1f((float)a.t * log1pf(-omb1));
+    const float c2 = -expm1f((float)a.t * log1pf(-omb2));
+    const float g = -phi;
+    const float mo = fmaf(a.beta1, a.adam_m[idx], omb1 * g);
+    const float ve = fmaf(a.beta2, a.adam_v[idx], omb2 * g * g);
+    a.adam_m[idx] = mo;
+    a.adam_v[idx] = ve;
+    const float mh = mo / c1, vh = ve / c2;
+    a.theta[idx] = x - a.lr * mh / (sqrtf(vh) + a.eps);
+}
+
 __global__ void k_moments(const float* __restrict__ th, int K, double* __restrict__ out) {
     __shared__ double mean[6];
     const int tid = threadIdx.x;
@@ -125,6 +167,12 @@ cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_stein_adam, a, P);
+}
+
+cudaError_t launch_adam_independent(const SteinArgs& a, cudaStream_t s) {
+    const int64_t threads = a.chunks == 1 ? 6 * (int64_t)a.K : 32 * 6 * (int64_t)a.K;
+    k_adam_independent<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s) {
