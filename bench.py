@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="kinect", choices=["kinect", "box", "lidar", "batched", "surrogate"])
+    ap.add_argument("--workload", default="kinect", choices=["kinect", "box", "lidar", "batched", "surrogate", "mc"])
     ap.add_argument("--nn", default=None, choices=["grid", "bf16", "fp32", "surrogate"],
                     help="search of the registration loop (default: per workload)")
     ap.add_argument("--profile-stride", type=int, default=5,
@@ -93,6 +93,8 @@ def make_problem(workload: str, seed: int):
     from paper_2106_03287_gb300 import synth
     if workload == "batched":
         return synth.make_batched_problems(seed), dict(synth.WORKLOADS["batched"])
+    if workload == "mc":
+        return synth.make_kinect_problem(seed, K=synth.WORKLOADS["mc"]["runs"]), dict(synth.WORKLOADS["mc"])
     if workload in ("kinect", "surrogate"):
         d = synth.make_kinect_problem(seed)
     elif workload == "box":
@@ -232,12 +234,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     d, cfg = make_problem(args.workload, 1000)
+    if args.workload == "batched":
+        d = d[0]              # the oracle takes the batch's first problem (its runs are independent)
     import oracle as O
     ref, src = d["ref"], d["src"]
-    K = d["particles"].shape[0]
+    parts = d["particles"][:8] if args.workload == "mc" else d["particles"]   # mc: 8 of the independent runs
+    K = parts.shape[0]
     normals = O.normals(ref, NORMAL_K)[0] if args.metric == "plane" else None
-    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals)
-    th = d["particles"].astype(np.float64).copy()
+    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals, independent=args.workload == "mc")
+    th = parts.astype(np.float64).copy()
     mom, vel = np.zeros_like(th), np.zeros_like(th)
     t0 = time.perf_counter()
     O.step(ref, src, th, mom, vel, p, 0)
@@ -257,7 +262,9 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = K * cfg["m"] * per_step / (ms / 1e3)
-    sample = f"{per_step} SVGD iterations per step of the {args.workload} workload, exhaustive FP64 search"
+    sample = (f"{per_step} SVGD iterations per step of the {args.workload} workload"
+              + (" (problem 0 of the batch)" if args.workload == "batched" else "")
+              + (" (8 of the independent runs)" if args.workload == "mc" else "") + ", exhaustive FP64 search")
     line = {"impl": "reference", "metric": "particle_point_evals_per_sec", "value": value,
             "unit": "particle_point_evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -648,12 +655,153 @@ def run_ours_batched(args):
     return 0
 
 
+def run_ours_mc(args):
+    """The experiments' distribution-quality protocol on the kinect scene: a
+    Monte Carlo reference of 1000 independent SGD-ICP runs (each its own
+    minibatch stream) in one registration call, timed as the step; then Stein
+    ICP with 100 of the same initial poses, and the KL divergence and
+    overlapping coefficient between the two Gaussians."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2106_03287_gb300 as S
+    from paper_2106_03287_gb300 import build
+    if not os.path.exists(S.LIB_PATH):
+        build.build()
+    d, cfg = make_problem("mc", rank_seed(rank))
+    R, Ks = cfg["runs"], cfg["stein_K"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = S.sicp_create(local, stream)
+    p_mc = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0,
+                                 nn_mode=S.SICP_NN_GRID | S.SICP_INDEPENDENT)
+    p_st = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, nn_mode=S.SICP_NN_GRID)
+    ref_d = torch.from_numpy(d["ref"]).cuda()
+    src_d = torch.from_numpy(d["src"]).cuda()
+    par_d = torch.from_numpy(d["particles"]).cuda()
+
+    def step():
+        S.sicp_set_reference(ctx, ref_d)
+        return S.sicp_register(ctx, src_d, par_d, p_mc)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        step()
+    S.sicp_stats(ctx, True)
+    step()
+    st = S.sicp_stats(ctx, False).astype(np.float64)
+    queries = max(st[0], 1.0)
+    bytes_per_query = 16 + 4 + 8 * st[1] / queries + 8 * st[2] / queries + 16 * st[3] / queries
+    S.sicp_profile(ctx, 5)
+    step()
+    step()
+    S.sicp_profile(ctx, 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    out = None
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        out = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = S.sicp_profile(ctx, 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_max = slowest_rank_ms(statistics.mean(step_ms), world, "cuda")
+    evals = R * cfg["m"] * cfg["T"]
+    grad_ms = prof[0] / prof[1] if prof[1] else None
+    peak, peak_kind = measured_peak()
+    alg_bytes = bytes_per_query * R * cfg["m"]
+    achieved = alg_bytes / (grad_ms * 1e-3) / 1e9 if grad_ms else None
+    roofline = {"kernel": "k_grad_grid over 1000 independent runs, each with its own minibatch (one iteration)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_kind": f"{peak_kind} copy bandwidth", "frac": achieved / peak if achieved else None,
+                "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_us": grad_ms * 1e3 if grad_ms else None, "launches_timed": int(prof[1]),
+                "update_avg_launch_us": 1e3 * prof[2] / prof[3] if prof[3] else None}
+    # end to end: pinned host inputs, copies and the reference build inside the timed region
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    ref_h, src_h, par_h = pin(d["ref"]), pin(d["src"]), pin(d["particles"])
+    for _ in range(2):
+        S.sicp_set_reference(ctx, ref_h)
+        S.sicp_register(ctx, src_h, par_h, p_mc)
+    wall = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.sicp_set_reference(ctx, ref_h)
+        S.sicp_register(ctx, src_h, par_h, p_mc)
+        wall.append(time.perf_counter() - t0)
+    e2e = {"value": world * evals / statistics.mean(wall), "unit": "particle_point_evals/s",
+           "h2d_bytes_per_step": 12 * int(d["ref"].shape[0]) + 12 * int(d["src"].shape[0]) + 24 * R,
+           "d2h_bytes_per_step": 24 * R + 8 * 42, "ms_per_step": 1e3 * statistics.mean(wall)}
+    # quality: Stein ICP from the first stein_K initial poses against the Monte Carlo reference
+    S.sicp_set_reference(ctx, ref_d)
+    _, m_mc, c_mc = [np.asarray(x.cpu()) for x in out]
+    _, m_st, c_st = [np.asarray(x.cpu()) for x in S.sicp_register(ctx, src_d, par_d[:Ks].contiguous(), p_st)]
+    reg = 1e-12 * np.eye(6)
+    quality = {"reference": f"{R} independent SGD-ICP runs", "estimate": f"Stein ICP, {Ks} particles",
+               "kl_reference_to_estimate": S.sicp_gaussian_kl(m_mc, c_mc + reg, m_st, c_st + reg),
+               "kl_estimate_to_reference": S.sicp_gaussian_kl(m_st, c_st + reg, m_mc, c_mc + reg),
+               "ovl": S.sicp_gaussian_ovl(m_mc, c_mc + reg, m_st, c_st + reg, n=200_000, seed=0),
+               "sd_reference_mm_deg": (1e3 * np.sqrt(np.diag(c_mc)[:3])).tolist()
+               + np.degrees(np.sqrt(np.diag(c_mc)[3:])).tolist(),
+               "sd_estimate_mm_deg": (1e3 * np.sqrt(np.diag(c_st)[:3])).tolist()
+               + np.degrees(np.sqrt(np.diag(c_st)[3:])).tolist(),
+               "mean_diff_mm": (1e3 * np.abs(m_mc[:3] - m_st[:3])).tolist()}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        sub = 8   # a bounded sample: 8 of the runs, a few iterations
+        th = d["particles"][:sub].astype(np.float64).copy()
+        mom, vel = np.zeros_like(th), np.zeros_like(th)
+        po = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, independent=True)
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < 10.0 and n < cfg["T"]:
+            O.step(d["ref"], d["src"], th, mom, vel, po, n)
+            n += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": O.num_threads(),
+               "kind": "oracle", "sample": f"{sub} of the {R} runs, {n} iterations, exhaustive FP64 search, {dt:.1f} s"}
+    S.sicp_destroy(ctx)
+    if rank == 0:
+        line = {"metric": "particle_point_evals_per_sec", "value": job_value(evals, world, ms_max),
+                "unit": "particle_point_evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded generators; no dataset)",
+                "config": {"workload": "mc", "reference_points": int(d["ref"].shape[0]),
+                           "source_points": int(d["src"].shape[0]), "runs": R, "minibatch": cfg["m"],
+                           "iterations": cfg["T"], "adam_lr": cfg["lr"], "nn": "voxel grid (exact)",
+                           "l2": "256 MB buffer written between timed steps (outside the events)",
+                           "parallelism": f"independent problem per rank x{world}"},
+                "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),
+                "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": (SETREF_LAUNCHES + 4 + 3 * cfg["T"]) * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "quality": quality}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_ours_batched(args)
+    if args.workload == "mc":
+        return run_ours_mc(args)
     return run_ours(args)
 
 

@@ -396,4 +396,8 @@ WORKLOADS = {
     "lidar": dict(T=200, m=500, lr=0.01),
     "batched": dict(T=100, m=300, lr=0.01),
     "surrogate": dict(T=200, m=300, lr=0.03, surrogate_iters=150),
+    # the experiments' quality protocol on the kinect scene: a Monte Carlo reference of
+    # `runs` independent SGD-ICP runs, and Stein ICP with the first `stein_K` of the
+    # same initial poses
+    "mc": dict(T=150, m=300, lr=0.03, runs=1000, stein_K=100),
 }
