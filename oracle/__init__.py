@@ -426,3 +426,113 @@ def gaussian_ovl(m0, S0, m1, S1, z0, z1):
     a = np.minimum(1.0, np.exp(_gauss_logpdf(x0, m1, S1) - _gauss_logpdf(x0, m0, S0)))
     b = np.minimum(1.0, np.exp(_gauss_logpdf(x1, m0, S0) - _gauss_logpdf(x1, m1, S1)))
     return 0.5 * (a.mean() + b.mean())
+
+
+# ---------------------------------------------------------------- odometry chaining (reading R18)
+#
+# R18: the odometry experiment chains scan-to-scan estimates as
+# T_E = T^1_0 T^2_1 ... T^l_(l-1) of the mean transforms and combines their
+# covariances to fourth order (an approximation it cites, not prints).  Read
+# here: each scan pair's distribution is its particles' mean pose (where
+# their left perturbations average to zero) with the sample covariance of
+# those perturbations; two independent distributions compound to the mean
+# T1 T2 with S1 + Ad(T1) S2 Ad(T1)^T plus the published fourth-order terms.
+#
+# A pose is T = [[C, r], [0, 1]] with C = R(theta) and r = theta[:3]; a pose
+# distribution is a mean pose T_bar and the covariance of the left
+# perturbation xi = [rho; phi] in T = exp(xi^) T_bar.  Matrix exponential and
+# logarithm come from scipy.linalg (expm, logm), not from closed forms.
+
+def _hat(xi):
+    rho, phi = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    X = np.zeros((4, 4))
+    X[:3, :3] = [[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]]
+    X[:3, 3] = rho
+    return X
+
+
+def se3_exp(xi):
+    import scipy.linalg
+    return scipy.linalg.expm(_hat(xi))
+
+
+def se3_log(T):
+    import scipy.linalg
+    X = np.real(scipy.linalg.logm(np.asarray(T, np.float64)))
+    return np.r_[X[:3, 3], X[2, 1], X[0, 2], X[1, 0]]
+
+
+def pose_matrix(theta):
+    R, _ = rotation(theta)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = np.asarray(theta[:3], np.float64)
+    return T
+
+
+def adjoint(T):
+    C, r = T[:3, :3], T[:3, 3]
+    A = np.zeros((6, 6))
+    A[:3, :3] = C
+    A[3:, 3:] = C
+    A[:3, 3:] = _hat(np.r_[0, 0, 0, r])[:3, :3] @ C
+    return A
+
+
+def pose_distribution(particles, iters=50):
+    """Mean pose (the point where the left perturbations of the particles
+    average to zero, found by fixed-point iteration from the pose of the mean
+    parameters) and the covariance of those perturbations (divisor K - 1)."""
+    th = np.asarray(particles, np.float64).reshape(-1, 6)
+    Ts = [pose_matrix(t) for t in th]
+    Tb = pose_matrix(moments_circular(th)[0])
+    for _ in range(iters):
+        xis = np.array([se3_log(T @ np.linalg.inv(Tb)) for T in Ts])
+        step = xis.mean(0)
+        Tb = se3_exp(step) @ Tb
+        if np.abs(step).max() < 1e-15:
+            break
+    xis = np.array([se3_log(T @ np.linalg.inv(Tb)) for T in Ts])
+    K = th.shape[0]
+    cov = xis.T @ xis / (K - 1) if K > 1 else np.zeros((6, 6))
+    return Tb, cov
+
+
+def _angle3(M):
+    return -np.trace(M) * np.eye(3) + M
+
+
+def _angle6(S):
+    Spp, Spf = S[3:, 3:], S[:3, 3:]
+    A = np.zeros((6, 6))
+    A[:3, :3] = _angle3(Spp)
+    A[:3, 3:] = _angle3(Spf + Spf.T)
+    A[3:, 3:] = _angle3(Spp)
+    return A
+
+
+def _bb(A, B):
+    return _angle3(A) @ _angle3(B) + _angle3(B @ A)
+
+
+def compound(T1, S1, T2, S2, order=4):
+    """The distribution of T1 T2 for independent T1 = exp(xi1^) T1_bar,
+    T2 = exp(xi2^) T2_bar: mean T1_bar T2_bar and covariance to second order,
+    S1 + Ad(T1_bar) S2 Ad(T1_bar)^T, or with the fourth-order terms."""
+    T1, T2 = np.asarray(T1, np.float64), np.asarray(T2, np.float64)
+    S1, S2 = np.asarray(S1, np.float64), np.asarray(S2, np.float64)
+    A = adjoint(T1)
+    S2p = A @ S2 @ A.T
+    S = S1 + S2p
+    if order == 4:
+        a1, a2 = _angle6(S1), _angle6(S2p)
+        S = S + (a1 @ S2p + S2p @ a1.T + a2 @ S1 + S1 @ a2.T) / 12.0
+        s1rr, s1rp, s1pp = S1[:3, :3], S1[:3, 3:], S1[3:, 3:]
+        s2rr, s2rp, s2pp = S2p[:3, :3], S2p[:3, 3:], S2p[3:, 3:]
+        B = np.zeros((6, 6))
+        B[:3, :3] = _bb(s1pp, s2rr) + _bb(s1rp.T, s2rp) + _bb(s1rp, s2rp.T) + _bb(s1rr, s2pp)
+        B[:3, 3:] = _bb(s1pp, s2rp.T) + _bb(s1rp.T, s2pp)
+        B[3:, :3] = B[:3, 3:].T
+        B[3:, 3:] = _bb(s1pp, s2pp)
+        S = S + B / 4.0
+    return T1 @ T2, S

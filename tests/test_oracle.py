@@ -357,6 +357,97 @@ def test_gaussian_ovl_closed_forms():
     assert O.gaussian_ovl(m0, S, far, S, z0, z1) < 1e-6
 
 
+# ---------------------------------------------------------------- odometry chaining (R18)
+
+def _so3_exp_batch(phi):
+    """Rodrigues' formula, vectorised (independent of the oracle's scipy expm)."""
+    th = np.linalg.norm(phi, axis=1)[:, None, None]
+    K = np.zeros((phi.shape[0], 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -phi[:, 2], phi[:, 1], -phi[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = phi[:, 2], -phi[:, 1], phi[:, 0]
+    a = np.where(th > 1e-9, np.sin(th) / np.maximum(th, 1e-300), 1.0)
+    b = np.where(th > 1e-9, (1 - np.cos(th)) / np.maximum(th, 1e-300) ** 2, 0.5)
+    c = np.where(th > 1e-9, (th - np.sin(th)) / np.maximum(th, 1e-300) ** 3, 1.0 / 6)
+    K2 = K @ K
+    return np.eye(3) + a * K + b * K2, np.eye(3) + b * K + c * K2
+
+
+def _se3_exp_batch(xi):
+    C, V = _so3_exp_batch(xi[:, 3:])
+    T = np.tile(np.eye(4), (xi.shape[0], 1, 1))
+    T[:, :3, :3] = C
+    T[:, :3, 3] = np.einsum("nij,nj->ni", V, xi[:, :3])
+    return T
+
+
+def _se3_log_batch(T):
+    C = T[:, :3, :3]
+    cos = np.clip((np.trace(C, axis1=1, axis2=2) - 1) / 2, -1, 1)
+    th = np.arccos(cos)
+    w = np.stack([C[:, 2, 1] - C[:, 1, 2], C[:, 0, 2] - C[:, 2, 0], C[:, 1, 0] - C[:, 0, 1]], 1)
+    s = np.where(th > 1e-9, th / (2 * np.sin(np.maximum(th, 1e-300))), 0.5)
+    phi = s[:, None] * w
+    _, V = _so3_exp_batch(phi)
+    rho = np.linalg.solve(V, T[:, :3, 3][..., None])[..., 0]
+    return np.c_[rho, phi]
+
+
+def test_se3_exp_log_and_adjoint():
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        xi = np.r_[rng.normal(0, 1, 3), rng.normal(0, 0.8, 3)]
+        T = O.se3_exp(xi)
+        assert np.allclose(T, _se3_exp_batch(xi[None])[0], atol=1e-12)
+        assert np.allclose(O.se3_log(T), xi, atol=1e-10)
+        # T exp(xi^) T^-1 = exp((Ad(T) xi)^)
+        P = O.pose_matrix(np.r_[rng.normal(0, 1, 3), rng.uniform(-1, 1, 3)])
+        eps = xi * 1e-3
+        assert np.allclose(P @ O.se3_exp(eps) @ np.linalg.inv(P), O.se3_exp(O.adjoint(P) @ eps), atol=1e-12)
+    assert np.allclose(O.pose_matrix([1, 2, 3, 0, 0, 0]), np.r_[np.c_[np.eye(3), [1, 2, 3]], [[0, 0, 0, 1]]])
+
+
+def test_compounding_against_monte_carlo():
+    """Compound two uncertain poses by sampling (own vectorised exp/log) and
+    compare: the second-order covariance is good for small uncertainty, and
+    the fourth-order terms remove most of its error for large uncertainty."""
+    rng = np.random.default_rng(3)
+    T1 = O.pose_matrix([0.5, -0.2, 0.3, 0.3, -0.2, 0.5])
+    T2 = O.pose_matrix([1.0, 0.4, -0.2, -0.4, 0.1, 0.2])
+    n = 200_000
+    for sc, tol2, ratio in ((0.05, 0.02, None), (0.5, None, 0.4)):
+        S1 = np.diag([1, 2, 1, 1, 0.5, 2.0]) * sc ** 2
+        S2 = np.diag([2, 1, 1, 0.5, 1, 1.5]) * sc ** 2
+        x1 = rng.standard_normal((n, 6)) @ np.linalg.cholesky(S1).T
+        x2 = rng.standard_normal((n, 6)) @ np.linalg.cholesky(S2).T
+        Tm = T1 @ T2
+        T = _se3_exp_batch(x1) @ T1 @ _se3_exp_batch(x2) @ T2 @ np.linalg.inv(Tm)
+        S_mc = np.cov(_se3_log_batch(T).T)
+        Tc, S2nd = O.compound(T1, S1, T2, S2, order=2)
+        _, S4th = O.compound(T1, S1, T2, S2, order=4)
+        assert np.allclose(Tc, Tm, atol=1e-14)
+        e2 = np.linalg.norm(S2nd - S_mc) / np.linalg.norm(S_mc)
+        e4 = np.linalg.norm(S4th - S_mc) / np.linalg.norm(S_mc)
+        if tol2 is not None:
+            assert e2 < tol2 and e4 < tol2
+        else:
+            assert e4 < ratio * e2 and e4 < 0.03, (e2, e4)
+
+
+def test_pose_distribution_of_particles():
+    """Particles drawn as exp(xi^) T_bar around a known pose: the mean pose is
+    recovered and the covariance is the sample covariance of the xi."""
+    rng = np.random.default_rng(4)
+    Tb = O.pose_matrix([0.3, -0.1, 0.2, 0.2, 0.1, 3.0])      # yaw next to pi
+    xi = rng.normal(0, 1, (400, 6)) * [0.01, 0.02, 0.01, 0.02, 0.01, 0.03]
+    xi -= xi.mean(0)
+    Ts = _se3_exp_batch(xi) @ Tb
+    from scipy.spatial.transform import Rotation as Rot
+    th = np.c_[Ts[:, :3, 3], Rot.from_matrix(Ts[:, :3, :3]).as_euler("xyz")]
+    T_hat, S = O.pose_distribution(th)
+    assert np.allclose(T_hat, Tb, atol=1e-9)
+    assert np.allclose(S, np.cov(xi.T), atol=1e-12)
+
+
 def test_icp_gradient_single_point_closed_form():
     ref = np.array([[0.3, -0.2, 0.5]], np.float32)
     src = np.array([[0.1, 0.4, -0.2]], np.float32)
