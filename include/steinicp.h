@@ -270,6 +270,26 @@ int sicp_gaussian_kl(const double* mean0, const double* cov0, const double* mean
 int sicp_gaussian_ovl(const double* mean0, const double* cov0, const double* mean1, const double* cov1,
                       int32_t d, const double* z0, const double* z1, int64_t n, double* out);
 
+/* Odometry chaining (no context; host arrays; float64).  The paper's odometry
+ * experiment multiplies consecutive scan-to-scan mean transforms, T_E =
+ * T^1_0 T^2_1 ... T^l_(l-1), and combines their covariances to fourth order
+ * (an approximation it cites, not prints).  A pose distribution is a mean
+ * pose T (4 x 4 row-major, [C r; 0 1]) and the 6 x 6 row-major covariance of
+ * the left perturbation xi = [rho; phi] in exp(xi^) T.
+ * sicp_pose_distribution: the distribution of K particles [K][6] (x, y, z,
+ * roll, pitch, yaw; C = Rz Ry Rx): the mean pose where their perturbations
+ * average to zero (fixed-point iteration from the pose of the mean
+ * parameters, angles by circular mean) and the sample covariance of the
+ * perturbations (divisor K - 1; zero for K = 1).
+ * sicp_compound: the distribution of T1 T2 for independent distributions 1
+ * and 2: mean T1 T2; covariance S1 + Ad(T1) S2 Ad(T1)^T (order 2) plus the
+ * fourth-order terms (order 4).
+ * Errors: SICP_EINVAL (null pointer, K outside [1, 2^20], order not 2 or 4,
+ * a non-finite value, a T that is not a rigid transform to 1e-6). */
+int sicp_pose_distribution(const float* particles, int32_t K, double* T_mean, double* cov);
+int sicp_compound(const double* T1, const double* cov1, const double* T2, const double* cov2, int32_t order,
+                  double* T_out, double* cov_out);
+
 /* The same moments with circular statistics for the three angles, for
  * particle sets whose rotations straddle +-pi (the plain mean of angles near
  * pi and -pi lands near 0).  Mean of angle a: atan2(sum_j sin theta_j,a,

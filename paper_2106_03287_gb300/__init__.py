@@ -10,5 +10,5 @@ from .binding import (  # noqa: F401
     sicp_stats, sicp_stein_adam, sicp_icp_grad_noalloc, sicp_register_batched, sicp_autotune_batched, pack_batch,
     SURROGATE_NPARAM, sicp_surrogate_train, sicp_surrogate_params, sicp_surrogate_loss_grad, sicp_surrogate_infer,
     sicp_register_continue, sicp_surrogate_save, sicp_surrogate_load, sicp_reference_normals, SICP_POINT_TO_PLANE,
-    SICP_INDEPENDENT, sicp_gaussian_kl, sicp_gaussian_ovl,
+    SICP_INDEPENDENT, sicp_gaussian_kl, sicp_gaussian_ovl, sicp_pose_distribution, sicp_compound, chain_odometry,
 )

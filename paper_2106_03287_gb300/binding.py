@@ -41,7 +41,8 @@ _CODES = {-1: "EINVAL", -2: "ENOREF", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
 EXPORTS = (
     "sicp_default_params", "sicp_create", "sicp_destroy", "sicp_last_error", "sicp_set_reference",
     "sicp_register", "sicp_minibatch", "sicp_nn", "sicp_icp_grad", "sicp_stein_adam", "sicp_moments",
-    "sicp_moments_circular", "sicp_reference_normals", "sicp_gaussian_kl", "sicp_gaussian_ovl", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
+    "sicp_moments_circular", "sicp_reference_normals", "sicp_gaussian_kl", "sicp_gaussian_ovl",
+    "sicp_pose_distribution", "sicp_compound", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
 )
@@ -107,6 +108,8 @@ def lib() -> ctypes.CDLL:
             "sicp_reference_normals": (ctypes.c_int, [P, I32, P, ctypes.c_int]),
             "sicp_gaussian_kl": (ctypes.c_int, [P, P, P, P, I32, P]),
             "sicp_gaussian_ovl": (ctypes.c_int, [P, P, P, P, I32, P, P, ctypes.c_int64, P]),
+            "sicp_pose_distribution": (ctypes.c_int, [P, I32, P, P]),
+            "sicp_compound": (ctypes.c_int, [P, P, P, P, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -358,6 +361,40 @@ def sicp_gaussian_ovl(m0, S0, m1, S1, n: int = 100_000, seed: int = 0, z0=None, 
                                          z0.shape[0], ctypes.byref(out)),
                  "sicp_gaussian_ovl: bad sizes, non-finite values or a covariance that is not positive definite")
     return out.value
+
+
+def sicp_pose_distribution(particles):
+    """(mean pose 4 x 4, se(3) covariance 6 x 6) of particles [K][6] (host data)."""
+    th = np.ascontiguousarray(particles.cpu().numpy() if _is_torch(particles) else particles, np.float32).reshape(-1, 6)
+    T = np.empty((4, 4))
+    S = np.empty((6, 6))
+    _plain_check(lib().sicp_pose_distribution(_ptr(th, np.float32), th.shape[0], _ptr(T, np.float64),
+                                              _ptr(S, np.float64)),
+                 "sicp_pose_distribution: bad size or a non-finite value")
+    return T, S
+
+
+def sicp_compound(T1, S1, T2, S2, order: int = 4):
+    """(T1 T2, covariance) of two independent pose distributions."""
+    a = [np.ascontiguousarray(x, np.float64) for x in (T1, S1, T2, S2)]
+    T = np.empty((4, 4))
+    S = np.empty((6, 6))
+    _plain_check(lib().sicp_compound(*[_ptr(x, np.float64) for x in a], int(order), _ptr(T, np.float64),
+                                     _ptr(S, np.float64)),
+                 "sicp_compound: order must be 2 or 4, the poses rigid transforms, the values finite")
+    return T, S
+
+
+def chain_odometry(distributions, order: int = 4):
+    """Compound a sequence of scan-to-scan distributions (T, S) in order:
+    returns the list of accumulated (T_E, S_E) after each pair."""
+    out = []
+    T, S = distributions[0]
+    out.append((np.asarray(T, np.float64), np.asarray(S, np.float64)))
+    for T2, S2 in distributions[1:]:
+        T, S = sicp_compound(T, S, T2, S2, order)
+        out.append((T, S))
+    return out
 
 
 def sicp_moments_circular(ctx, particles):
