@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--nn", default=None, choices=["grid", "bf16", "fp32", "surrogate"],
                     help="search of the registration loop (default: per workload)")
     ap.add_argument("--profile-stride", type=int, default=5,
-                    help="time the gradient and Stein kernels of every s-th iteration with CUDA events")
+                    help="after the timed steps, time the gradient and Stein kernels of every s-th iteration "
+                         "with CUDA events in a separate pass (0: skip)")
     ap.add_argument("--metric", default="point", choices=["point", "plane"],
                     help="ICP error metric: point-to-point (the paper's Stein ICP) or point-to-plane")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -347,12 +348,6 @@ def run_ours(args):
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
     coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
     bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q + (16 if plane else 0)   # + the normal
-    if args.profile_stride > 0:
-        S.sicp_profile(ctx, args.profile_stride)
-        step()   # capture the profiling graphs outside the timed region
-        step()
-        S.sicp_profile(ctx, args.profile_stride)   # reset totals
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
@@ -368,8 +363,10 @@ def run_ours(args):
     clocks = sampler.stop()
     if world > 1:
         torch.distributed.barrier()
-    prof = S.sicp_profile(ctx, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # kernel durations for the roofline: a separate, untimed pass with CUDA events
+    # recorded around the kernels of every s-th iteration (they would slow the timed steps)
+    prof = kernel_profile(S, ctx, step, args.profile_stride)
     ms = statistics.mean(step_ms)
     ms_max = slowest_rank_ms(ms, world, "cuda")
     evals = K * cfg["m"] * cfg["T"]
@@ -477,6 +474,21 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def kernel_profile(S, ctx, step, stride, runs=3):
+    """Average kernel durations over `runs` untimed steps with profiling on
+    (the first captures the profiling graphs and is discarded)."""
+    if stride <= 0:
+        return [0.0, 0.0, 0.0, 0.0]
+    S.sicp_profile(ctx, stride)
+    step()
+    S.sicp_profile(ctx, stride)   # drop the capture run's totals
+    for _ in range(runs):
+        step()
+    prof = S.sicp_profile(ctx, 0)
+    step()                        # leave the context's unprofiled graph captured again
+    return prof
 
 
 def timed_runs(fn, flush, stream, steps):
@@ -695,10 +707,6 @@ def run_ours_mc(args):
     st = S.sicp_stats(ctx, False).astype(np.float64)
     queries = max(st[0], 1.0)
     bytes_per_query = 16 + 4 + 8 * st[1] / queries + 8 * st[2] / queries + 16 * st[3] / queries
-    S.sicp_profile(ctx, 5)
-    step()
-    step()
-    S.sicp_profile(ctx, 5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
@@ -713,9 +721,9 @@ def run_ours_mc(args):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    prof = S.sicp_profile(ctx, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_max = slowest_rank_ms(statistics.mean(step_ms), world, "cuda")
+    prof = kernel_profile(S, ctx, step, 5)
     evals = R * cfg["m"] * cfg["T"]
     grad_ms = prof[0] / prof[1] if prof[1] else None
     peak, peak_kind = measured_peak()

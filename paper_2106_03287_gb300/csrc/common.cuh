@@ -186,6 +186,8 @@ struct sicp_ctx {
     int bf16_R = 0;                      // reference tiles of 256 points
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
+    sicp::Buf search_dev;                // device copy of `search`, rewritten by every reference build
+    uint64_t ref_gen = 0;                // bumped by every sicp_set_reference
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
 };
@@ -335,6 +337,7 @@ int grid_build(sicp_ctx* ctx, float cell_size);
 int search_table_init(sicp_ctx* ctx);
 cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32_t* idx, float* d2,
                            unsigned long long* stats, cudaStream_t s);
-cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch& g, cudaStream_t s);
+// d_search: the device copy of the context's GridSearch (sicp_ctx::search_dev)
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s);
 
 }  // namespace sicp

@@ -76,7 +76,10 @@ constexpr int kSeq = 2;                                   // particles per warp
 constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
 constexpr float kReuse = 2.f;
 
-__global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, GridSearch S) {
+// The search description is read from device memory (the reference build
+// rewrites it there), so a captured graph of these launches stays valid when
+// the reference changes.  (Staging it in shared memory was slower.)
+__global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd) {
     __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x;
@@ -84,6 +87,7 @@ __global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, Grid
     for (int i = threadIdx.x; i < kPart; i += blockDim.x)
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
+    const GridSearch& S = *Sd;
     const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
     float3 s = make_float3(s4.x, s4.y, s4.z);
     const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
@@ -405,6 +409,9 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
     ctx->search.coarse = ctx->grid2.v;
     ctx->search.ref4 = ctx->ref4;
     ctx->search.M = (int)M;
+    // the device copy the captured gradient launches read
+    if ((rc = ensure(ctx, ctx->search_dev, sizeof(GridSearch)))) return rc;
+    SICP_CUDA(cudaMemcpyAsync(ctx->search_dev.p, &ctx->search, sizeof(GridSearch), cudaMemcpyHostToDevice, s));
     return SICP_OK;
 }
 
@@ -422,9 +429,9 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch& g, cudaStream_t s) {
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s) {
     dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
-    k_grad_grid<<<grid, kGradThreads, 0, s>>>(a, g);
+    k_grad_grid<<<grid, kGradThreads, 0, s>>>(a, d_search);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
