@@ -61,7 +61,6 @@ struct LoopKey {
     uint64_t seed;
     int64_t t0;             // first iteration of the run
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
-    uint64_t ref_gen;       // BF16 graphs: the reference build they were captured after
     const void* ptrs[13];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -329,7 +328,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done,
-                   &c->bf16_tiles, &c->normals, &c->search_dev};
+                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -383,7 +382,7 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
         ctx->M = 0;
         return rc;
     }
-    ++ctx->ref_gen;   // captured loops stay valid: they read the search description from device memory
+    // captured loops stay valid: their kernels read the reference's description from device memory
     return sync(ctx);
 }
 
@@ -746,10 +745,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.surr_gen = surr ? ctx->surr_gen : 0;
     key.seed = p.seed;
     key.t0 = t0;
-    key.ref_M = ctx->M;
-    // the grid kernels read the search description from device memory; the BF16
-    // kernel takes the tiles' centre by value, so its graphs follow the reference
-    key.ref_gen = bf ? ctx->ref_gen : 0;
+    key.ref_M = ctx->M;   // (the grid and BF16 kernels read the reference's description from device memory)
     key.ptrs[0] = ctx->src4.p;
     key.ptrs[1] = ctx->mb.p;
     key.ptrs[2] = ctx->theta.p;

@@ -184,10 +184,10 @@ struct sicp_ctx {
     bool bf16_ready = false;             // bf16_tiles hold the current reference
     float3 bf16_centre = {0, 0, 0};
     int bf16_R = 0;                      // reference tiles of 256 points
+    sicp::Buf bf16_ref;                  // device copy of what the tensor-core search reads of the reference
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
     sicp::Buf search_dev;                // device copy of `search`, rewritten by every reference build
-    uint64_t ref_gen = 0;                // bumped by every sicp_set_reference
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
 };

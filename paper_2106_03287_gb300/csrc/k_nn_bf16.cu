@@ -122,7 +122,19 @@ __global__ void k_bf16_btiles(const float4* __restrict__ sorted, int M, float3 c
     store_row16(out + (size_t)tile * kTileBytes, row, v);
 }
 
+// What the search reads of the current reference, kept in device memory and
+// rewritten by every tile build (bf16_prepare), so a captured graph of the
+// search stays valid when the reference changes.
+struct BfRef {
+    float3 c;                  // centre of the bounding box, subtracted before the split
+    int M, R;                  // points, tiles of 256
+    const unsigned char* btiles;
+    const float* nmax;         // [R]
+    GridView grid;             // the fine grid: where each cell's points start in `sorted`
+};
+
 struct BfArgs {
+    const BfRef* ref;          // the reference description (device memory); fills the fields below
     int grad;                  // 0: queries given; 1: queries R_j s_k + u_j of a registration iteration
     const float* q;            // grad = 0: [n][3]
     int64_t n;
@@ -191,7 +203,18 @@ __device__ __forceinline__ bool better_u(float d, unsigned i, float bd, unsigned
     return d < bd || (d == bd && i < bi);
 }
 
-__global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs a) {
+__global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
+    BfArgs a = args;
+    {
+        const BfRef* r = args.ref;
+        a.c = r->c;
+        a.M = r->M;
+        a.R = r->R;
+        a.btiles = r->btiles;
+        a.nmax = r->nmax;
+        a.grid = r->grid;
+        a.sorted = r->grid.sorted;
+    }
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t tfull[2];
     __shared__ uint32_t tbase;
@@ -438,19 +461,22 @@ int bf16_prepare(sicp_ctx* ctx) {
     SICP_CUDA(cudaGetLastError());
     ctx->bf16_centre = c;
     ctx->bf16_R = R;
+    BfRef h;
+    h.c = c;
+    h.M = (int)ctx->M;
+    h.R = R;
+    h.btiles = (const unsigned char*)ctx->bf16_tiles.p;
+    h.nmax = (const float*)nmax;
+    h.grid = ctx->grid.v;
+    if ((rc = ensure(ctx, ctx->bf16_ref, sizeof(BfRef)))) return rc;
+    SICP_CUDA(cudaMemcpyAsync(ctx->bf16_ref.p, &h, sizeof(BfRef), cudaMemcpyHostToDevice, ctx->stream));
     ctx->bf16_ready = true;
     return SICP_OK;
 }
 
 static BfArgs bf_args(sicp_ctx* ctx, int* err) {
     BfArgs a{};
-    a.c = ctx->bf16_centre;
-    a.btiles = (const unsigned char*)ctx->bf16_tiles.p;
-    a.nmax = (const float*)((const char*)ctx->bf16_tiles.p + (size_t)ctx->bf16_R * kTileBytes);
-    a.sorted = ctx->grid.v.sorted;
-    a.grid = ctx->grid.v;
-    a.M = (int)ctx->M;
-    a.R = ctx->bf16_R;
+    a.ref = (const BfRef*)ctx->bf16_ref.p;   // the kernel fills the reference fields from it
     a.err = err;
     return a;
 }
