@@ -106,7 +106,10 @@ def make_problem(workload: str, seed: int):
 
 
 NORMAL_K = 10   # neighbours of the reference normals of the point-to-plane metric
-SETREF_LAUNCHES = 22   # kernels of one sicp_set_reference on the kinect-sized grid (7 seed-flooding steps)
+# kernels of one sicp_set_reference per workload, counted in ncu launch lists: pack, bbox, the fine
+# level (cell assignment, 3-kernel scan, scatter, cell sort, seed init, seed-flooding steps) and the
+# coarse level; the number of flooding steps follows the grid's size
+SETREF_LAUNCHES = {"kinect": 22, "box": 21, "lidar": 23, "mc": 22, "surrogate": 22}
 
 
 def metric_name(metric):
@@ -450,7 +453,8 @@ def run_ours(args):
         # reference build (pack, bbox, two grid levels, seed map: 22 launches on the kinect grid, counted
         # in an ncu launch list), the run's pack / finite check / minibatch / moments, and per iteration
         # the gradient kernel(s) and the Stein kernel; point-to-plane adds the normals kernel
-        launches_per_step = SETREF_LAUNCHES + 4 + per_iter * cfg["T"] + (1 if plane else 0)
+        launches_per_step = (SETREF_LAUNCHES[args.workload] + 4 + per_iter * cfg["T"] + (1 if plane else 0)
+                             + (1 if nn == "bf16" else 0))   # the bf16 tile build follows each new reference
     else:   # surrogate, fallback, reduction and Stein for the surrogate iterations; grid, reduction and Stein after
         si = min(cfg.get("surrogate_iters", 0), cfg["T"])
         launches_per_step = 4 + 4 * si + 3 * (cfg["T"] - si)
@@ -794,7 +798,7 @@ def run_ours_mc(args):
                            "parallelism": f"independent problem per rank x{world}"},
                 "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-                "clocks": clocks, "e2e": e2e, "gpu_launches": (SETREF_LAUNCHES + 4 + 3 * cfg["T"]) * args.steps,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": (SETREF_LAUNCHES["mc"] + 4 + 3 * cfg["T"]) * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "quality": quality}
         print(json.dumps(line), flush=True)
     if world > 1:
