@@ -109,7 +109,7 @@ NORMAL_K = 10   # neighbours of the reference normals of the point-to-plane metr
 # kernels of one sicp_set_reference per workload, counted in ncu launch lists: pack, bbox, the fine
 # level (cell assignment, 3-kernel scan, scatter, cell sort, seed init, seed-flooding steps) and the
 # coarse level; the number of flooding steps follows the grid's size
-SETREF_LAUNCHES = {"kinect": 22, "box": 21, "lidar": 23, "mc": 22, "surrogate": 22}
+SETREF_LAUNCHES = {"kinect": 22, "box": 21, "lidar": 24, "mc": 22, "surrogate": 22}
 
 
 def metric_name(metric):

@@ -179,18 +179,27 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t r[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Minimum of 64 accumulator values (a tree, for instruction-level parallelism).
+// min(a, b, c) in one instruction (three-input min.f32 of sm_100 and later).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Minimum of 64 accumulator values: a tree of three-input minimums (32
+// instructions instead of 63; a minimum is exact in any order).
 __device__ __forceinline__ float min64(const uint32_t r[64]) {
-    float t[16];
+    float t[22];
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        t[i] = fminf(fminf(__uint_as_float(r[i]), __uint_as_float(r[i + 16])),
-                     fminf(__uint_as_float(r[i + 32]), __uint_as_float(r[i + 48])));
+    for (int i = 0; i < 21; ++i)
+        t[i] = min3f(__uint_as_float(r[i]), __uint_as_float(r[i + 21]), __uint_as_float(r[i + 42]));
+    t[21] = __uint_as_float(r[63]);
+    float u[8];
 #pragma unroll
-    for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-        for (int i = 0; i < w; ++i) t[i] = fminf(t[i], t[i + w]);
-    return t[0];
+    for (int i = 0; i < 7; ++i) u[i] = min3f(t[i], t[i + 7], t[i + 14]);
+    u[7] = t[21];
+    const float v0 = min3f(u[0], u[1], u[2]), v1 = min3f(u[3], u[4], u[5]);
+    return min3f(v0, v1, fminf(u[6], u[7]));
 }
 
 // Reference tile swept at step t (all R tiles, from `rot` on).
