@@ -61,7 +61,7 @@ struct LoopKey {
     uint64_t seed;
     int64_t t0;             // first iteration of the run
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
-    const void* ptrs[13];
+    const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -327,7 +327,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->batch) batch_destroy(c->batch);
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
-                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar, &c->done,
+                   &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar,
                    &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
@@ -525,9 +525,6 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.inv_m = 1.f / (float)m;
     g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
     g.mb_stride = 0;
-    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
-    g.done = (unsigned*)ctx->done.p;
-    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
     if (surr) {
         SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, m, g.theta, K, kSurrogateIcpGradConf, (float*)ctx->partial.p,
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
@@ -687,7 +684,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if ((rc = ensure(ctx, ctx->partial, sizeof(float) * partial_floats))) return rc;
     if ((rc = ensure(ctx, ctx->moments, 42 * sizeof(double)))) return rc;
     if ((rc = ensure(ctx, ctx->gbar, b_th + 4 * sizeof(float)))) return rc;   // + the two blocks' medians
-    if ((rc = ensure(ctx, ctx->done, sizeof(unsigned) * (size_t)K))) return rc;
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
 
@@ -712,7 +708,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
         SICP_CUDA(cudaMemsetAsync(ctx->adam_v.p, 0, b_th, ctx->stream));
     }
-    SICP_CUDA(cudaMemsetAsync(ctx->done.p, 0, sizeof(unsigned) * (size_t)K, ctx->stream));
     // after gbar: the two blocks' previous medians, then their Stein arrival counters
     float* med_state = (float*)ctx->gbar.p + 6 * (size_t)K;
     SICP_CUDA(cudaMemsetAsync(med_state, 0, 4 * sizeof(float), ctx->stream));
@@ -757,8 +752,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.ptrs[8] = ctx->ref4;
     key.ptrs[9] = stats_ptr(ctx);
     key.ptrs[10] = ctx->gbar.p;
-    key.ptrs[11] = ctx->done.p;
-    key.ptrs[12] = plane ? ctx->normals.p : nullptr;
+    key.ptrs[11] = plane ? ctx->normals.p : nullptr;
 
     GraphCache& gc = *ctx->graphs;
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
@@ -777,7 +771,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         g.out_nn = nullptr;
         g.stats = stats_ptr(ctx);
         g.gbar = (float*)ctx->gbar.p;
-        g.done = (unsigned*)ctx->done.p;
         g.inv_m = 1.f / (float)p.m;
         g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
         g.mb_stride = indep ? (int64_t)p.T * p.m : 0;   // run j's row of iteration t: mb[(j T + t) m]

@@ -174,7 +174,7 @@ struct sicp_ctx {
 
     // per-problem and scratch buffers (grow-only)
     sicp::Buf src4, mb, theta, adam_m, adam_v, partial, moments, flags, tmp_in, tmp_out, tmp_aux;
-    sicp::Buf bbox, stats, gbar, done;
+    sicp::Buf bbox, stats, gbar;
     bool stats_on = false;
     int prof_stride = 0;
     double prof[4] = {0, 0, 0, 0};   // gradient ms, gradient launches, Stein ms, Stein launches
@@ -259,7 +259,6 @@ struct GradArgs {
     // grid search only: gbar = inv_m * (sum over the minibatch of the terms),
     // reduced in a fixed order after the search kernel.
     float* gbar;           // K x 6
-    unsigned* done;        // K arrival counters (unused by the grid search)
     float inv_m;
     // point-to-plane metric: unit normals by original reference index (w
     // unused); null: point-to-point
