@@ -186,20 +186,19 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return r;
 }
 
-// Minimum of 64 accumulator values: a tree of three-input minimums (32
-// instructions instead of 63; a minimum is exact in any order).
-__device__ __forceinline__ float min64(const uint32_t r[64]) {
-    float t[22];
+// Minimum of 64 accumulator values and of each run of 8 (g[i] over columns
+// 8i .. 8i + 7): a tree of three-input minimums, 36 instructions (a minimum is
+// exact in any order).  The run minimums let the candidate scan skip the runs
+// that hold no candidate.
+__device__ __forceinline__ float min64_runs(const uint32_t r[64], float g[8]) {
 #pragma unroll
-    for (int i = 0; i < 21; ++i)
-        t[i] = min3f(__uint_as_float(r[i]), __uint_as_float(r[i + 21]), __uint_as_float(r[i + 42]));
-    t[21] = __uint_as_float(r[63]);
-    float u[8];
-#pragma unroll
-    for (int i = 0; i < 7; ++i) u[i] = min3f(t[i], t[i + 7], t[i + 14]);
-    u[7] = t[21];
-    const float v0 = min3f(u[0], u[1], u[2]), v1 = min3f(u[3], u[4], u[5]);
-    return min3f(v0, v1, fminf(u[6], u[7]));
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t* x = r + 8 * i;
+        const float a = min3f(__uint_as_float(x[0]), __uint_as_float(x[1]), __uint_as_float(x[2]));
+        const float b = min3f(__uint_as_float(x[3]), __uint_as_float(x[4]), __uint_as_float(x[5]));
+        g[i] = min3f(a, b, fminf(__uint_as_float(x[6]), __uint_as_float(x[7])));
+    }
+    return min3f(min3f(g[0], g[1], g[2]), min3f(g[3], g[4], g[5]), fminf(g[6], g[7]));
 }
 
 // Reference tile swept at step t (all R tiles, from `rot` on).
@@ -372,23 +371,30 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             const int rt = ref_tile(t, a.R, rot);
             const float nt = __ldg(a.nmax + rt);
             const float E = fmaf(aq, nt, fmaf(kEpsRR * nt, nt, eq));
-            const float cm = min64(r);
+            float g[8];
+            const float cm = min64_runs(r, g);
             u = fminf(u, cm + E);
             const float thr = u + E;   // lower bound v - E <= u
             if (cm <= thr) {
                 const int col0 = qtr * kQuarter;
+                const int lim = a.M - rt * kRCols - col0;   // columns from lim on are padding
                 const float4* pts =
                     reinterpret_cast<const float4*>(sm + sRing + (t % kSlots) * kSlotBytes + kTileBytes);
 #pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    if (__uint_as_float(r[j]) <= thr && rt * kRCols + col0 + j < a.M) {
-                        const float4 r4 = pts[col0 + j];
-                        const float d = dist2(r4, q);
-                        const unsigned id = __float_as_uint(r4.w);
-                        if (better_u(d, id, bd, bi)) {
-                            bd = d;
-                            bi = id;
-                            bp = r4;
+                for (int i = 0; i < 8; ++i) {
+                    if (g[i] > thr) continue;   // no candidate in this run
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = 8 * i + jj;
+                        if (__uint_as_float(r[j]) <= thr && j < lim) {
+                            const float4 r4 = pts[col0 + j];
+                            const float d = dist2(r4, q);
+                            const unsigned id = __float_as_uint(r4.w);
+                            if (better_u(d, id, bd, bi)) {
+                                bd = d;
+                                bi = id;
+                                bp = r4;
+                            }
                         }
                     }
                 }
