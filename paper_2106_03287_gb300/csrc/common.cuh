@@ -23,6 +23,18 @@ __host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t s, uint64_t k) {
     return sm64_mix(s + k * 0x9e3779b97f4a7c15ULL);
 }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while its predecessor in the stream still runs: pdl_wait() blocks
+// until the predecessor grid has completed and its writes are visible (at once
+// when there is no programmatic predecessor), and pdl_trigger() lets the
+// successor be scheduled once every CTA of this grid has called it or exited.
+// The registration loop chains gradient -> reduction -> Stein step -> next
+// gradient this way.  The gradient kernels trigger only after their own wait,
+// so a Stein step is never scheduled before the previous Stein step has
+// completed, which lets it read the particles before its own wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Rotation R = Rz(yaw) Ry(pitch) Rx(roll) and its partials with respect to
 // roll, pitch and yaw: 36 floats, R row-major then dR_roll, dR_pitch, dR_yaw.
 struct Pose {
@@ -142,10 +154,29 @@ struct GridSearch {
     int M;
 };
 
+bool pdl_enabled();   // false when the environment sets SICP_NO_PDL
+
 struct Buf {
     void* p = nullptr;
     size_t cap = 0;
 };
+
+// Launch `k` with programmatic stream serialisation (see pdl_wait); plain
+// stream order when SICP_NO_PDL is set.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
 
 struct GraphCache;
 struct BatchState;

@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x;
     const int j0 = blockIdx.y * kPart;
+    pdl_wait();      // the particles of the previous Stein step
+    pdl_trigger();   // only after the wait: see pdl_wait
     for (int i = threadIdx.x; i < kPart; i += blockDim.x)
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
@@ -431,8 +433,7 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
 
 cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s) {
     dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
-    k_grad_grid<<<grid, kGradThreads, 0, s>>>(a, d_search);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_grad_grid, grid, dim3(kGradThreads), 0, s, a, d_search);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
 }

@@ -151,22 +151,13 @@ cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s) {
     const size_t pairs = (size_t)a.K * (a.K - 1) / 2;
     const size_t smem = sizeof(float) * (18 * (size_t)a.K + (pairs <= (size_t)kCacheFloats ? pairs : 0));
     const int P = (a.arrive && a.err) ? stein_ctas_per_block(a.K) : 1;
-    if (P == 1) {
-        k_stein_adam<<<2, kThreads, smem, s>>>(a, 1);
-        return cudaGetLastError();
-    }
-    // the CTAs of a block wait for one another: all must be resident at once
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * P);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_stein_adam, a, P);
+    // With P > 1 the CTAs of a block wait for one another, so all 2P <= 64 of
+    // them must be resident together.  They are: everything before them in the
+    // stream completes without waiting for them, and the next kernel is
+    // scheduled only once every one of them has passed its pdl_wait.  (A
+    // cooperative launch would state it; it is not combined with the
+    // programmatic serialisation here.)  The wait is bounded all the same.
+    return launch_pdl(k_stein_adam, dim3(2 * P), dim3(kThreads), smem, s, a, P);
 }
 
 cudaError_t launch_adam_independent(const SteinArgs& a, cudaStream_t s) {

@@ -1,6 +1,7 @@
 // Small utility kernels: input packing and checks, the chunk reduction that
 // turns partial gradient sums into gbar, a bounding box and an exclusive scan
 // used by the grid build.
+#include <stdlib.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -162,6 +163,8 @@ __global__ void __launch_bounds__(kGbarThreads) k_qterms_to_gbar(const float* __
                                                                  float inv_m, float* __restrict__ gbar, int* fb_count) {
     __shared__ float part[6][33];
     const int j = blockIdx.x, t = threadIdx.x;
+    pdl_trigger();   // the Stein step may be scheduled now (it waits for this grid)
+    pdl_wait();
     if (j == 0 && t == 0 && fb_count) *fb_count = 0;
     const int e = t / 6, c = t % 6;
     const float* row = qterms + (int64_t)j * m * 6;
@@ -180,6 +183,11 @@ __global__ void __launch_bounds__(kGbarThreads) k_qterms_to_gbar(const float* __
 }
 
 }  // namespace
+
+bool pdl_enabled() {
+    static const bool on = getenv("SICP_NO_PDL") == nullptr;
+    return on;
+}
 
 cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* flags, cudaStream_t s) {
     k_pack_points<<<grid_1d(n, 256), 256, 0, s>>>(xyz, n, out, flags);
@@ -205,8 +213,7 @@ cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, 
 cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
                                   cudaStream_t s) {
     if (K <= 0) return cudaSuccess;
-    k_qterms_to_gbar<<<K, kGbarThreads, 0, s>>>(qterms, K, m, inv_m, gbar, fb_count);
-    return cudaGetLastError();
+    return launch_pdl(k_qterms_to_gbar, dim3(K), dim3(kGbarThreads), 0, s, qterms, K, m, inv_m, gbar, fb_count);
 }
 
 cudaError_t launch_bbox(const float4* p, int64_t n, unsigned* lohi, cudaStream_t s) {

@@ -473,13 +473,25 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     const int c0 = 3 * b;
     const int Kq = (K + P - 1) / P, i0 = min(K, q * Kq), i1 = min(K, i0 + Kq);
 
-    const float m_prev = a.med_state ? a.med_state[b] : 0.f;   // read before the arrival below
+    // The particles and the previous median come from the previous Stein step,
+    // which has completed before this grid is scheduled (see pdl_wait), so the
+    // bandwidth is found before the wait for the gradients, overlapping the
+    // end of the gradient kernel.  (Loads through L2: nothing stale from L1.)
+    const float m_prev = a.med_state ? __ldcg(a.med_state + b) : 0.f;   // read before the arrival below
     if (tid == 0) s_fail = 0;
-    for (int idx = tid; idx < 6 * K; idx += blockDim.x) th[idx] = a.theta[idx];
+    for (int idx = tid; idx < 6 * K; idx += blockDim.x) th[idx] = __ldcg(a.theta + idx);
+    __syncthreads();
+    const Team T = {0, (int)blockDim.x, 1};
+    float med = 0.f;
+    const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum, m_prev, bracket, &med);
+    const float inv_h = 1.f / h, two_h = 2.f / h;
+
+    pdl_wait();      // the gradients of this iteration
+    pdl_trigger();   // the next gradient kernel may be scheduled (it waits for this grid)
     if (a.chunks == 1) {
         for (int e = tid; e < 3 * K; e += blockDim.x) {
             const int j = e / 3, c = c0 + e % 3, idx = 6 * j + c;
-            const float x = a.theta[idx], gb = a.partial[idx];
+            const float x = th[idx], gb = a.partial[idx];
             float pr = 0.f;
             if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
             G[idx] = fmaf(-a.N, gb * a.inv_m, pr);
@@ -493,7 +505,7 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (lane == 0) {
-                const float x = a.theta[idx];
+                const float x = th[idx];
                 float pr = 0.f;
                 if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
                 G[idx] = fmaf(-a.N, s * a.inv_m, pr);
@@ -502,11 +514,6 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     }
     __syncthreads();
     if (P > 1 && tid == 0) atomicAdd(a.arrive + b, 1u);   // this CTA has read theta
-
-    const Team T = {0, (int)blockDim.x, 1};
-    float med = 0.f;
-    const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum, m_prev, bracket, &med);
-    const float inv_h = 1.f / h, two_h = 2.f / h;
 
     // S lanes per particle (power of two <= 32), each summing over j = lane (mod S)
     int S = 32;
