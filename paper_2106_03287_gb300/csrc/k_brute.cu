@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(kGradMaxThreads) k_grad_brute(GradArgs a, cons
     __shared__ float red[kGradMaxThreads / 32][6];
     const int j = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_wait();      // the particles of the previous Stein step
+    pdl_trigger();   // only after the wait: see pdl_wait
     if (threadIdx.x == 0) make_pose(a.theta + 6 * j, P);
     __syncthreads();
     const bool valid = k < a.m;
@@ -137,8 +139,7 @@ cudaError_t launch_nn_brute(const float4* ref, int64_t M, const float* q, int64_
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s) {
     const GradLayout L = grad_layout(a.m);
     dim3 grid(L.chunks, a.K);
-    k_grad_brute<<<grid, L.threads, 0, s>>>(a, ref, (int)M);
-    return cudaGetLastError();
+    return launch_pdl(k_grad_brute, grid, dim3(L.threads), 0, s, a, ref, (int)M);
 }
 
 }  // namespace sicp

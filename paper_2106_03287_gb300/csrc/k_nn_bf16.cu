@@ -212,6 +212,8 @@ __device__ __forceinline__ bool better_u(float d, unsigned i, float bd, unsigned
 }
 
 __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
+    pdl_wait();      // the particles of the previous Stein step (and the reference description)
+    pdl_trigger();   // only after the wait: see pdl_wait
     BfArgs a = args;
     {
         const BfRef* r = args.ref;
@@ -508,8 +510,7 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
     a.n = n;
     a.out_idx = idx;
     a.out_d2 = d2;
-    k_nn_bf16<<<bf_grid(ctx, n), kBfThreads, kBfSmem, ctx->stream>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_nn_bf16, dim3(bf_grid(ctx, n)), dim3(kBfThreads), kBfSmem, ctx->stream, a);
 }
 
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
@@ -526,8 +527,7 @@ cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb
     a.K = K;
     a.qterms = qterms;
     a.out_idx = out_nn;
-    k_nn_bf16<<<bf_grid(ctx, (int64_t)K * m), kBfThreads, kBfSmem, ctx->stream>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_nn_bf16, dim3(bf_grid(ctx, (int64_t)K * m)), dim3(kBfThreads), kBfSmem, ctx->stream, a);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, nullptr, ctx->stream);
 }
