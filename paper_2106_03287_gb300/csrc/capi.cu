@@ -339,7 +339,7 @@ void sicp_destroy(sicp_ctx* c) {
             if (p) cudaFree(p);
     }
     if (c->tab_off) cudaFree(c->tab_off);
-    if (c->tab_lb2) cudaFree(c->tab_lb2);
+    if (c->tab_lb) cudaFree(c->tab_lb);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -136,12 +136,12 @@ struct Grid {
 
 // Row offsets (dy, dz) in cell units, in increasing order of a lower bound on
 // the distance from a query (mirrored into the upper half of its cell) to the
-// row; lb2 holds that bound squared, in cell units squared.
+// row; lb holds that bound, in cell units.
 struct SearchTable {
     const short2* off;
-    const float* lb2;
+    const float* lb;
     int n;
-    int upto[8];   // upto[k]: number of entries with lb2 <= (1.5 * 2^k)^2
+    int upto[8];   // upto[k]: number of entries with lb <= 1.5 * 2^k
 };
 
 // Everything an exact grid search reads: a fine and a coarse level over the
@@ -200,7 +200,7 @@ struct sicp_ctx {
     sicp::Grid grid, grid2;           // fine and coarse levels
     sicp::GridSearch search{};
     short2* tab_off = nullptr;
-    float* tab_lb2 = nullptr;
+    float* tab_lb = nullptr;
     float3 ref_lo = {0, 0, 0}, ref_hi = {0, 0, 0};
 
     // per-problem and scratch buffers (grow-only)

@@ -45,6 +45,15 @@ __device__ __forceinline__ float slab(float v, float o, float c, int i, float to
     return fmaxf(d - tol, 0.f);
 }
 
+// At least sqrt(x), for x >= 0: the hardware approximation widened by 1e-5
+// relative, far above its error.  Used for a search range, where a wider
+// range only adds candidates.
+__device__ __forceinline__ float sqrt_up(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 1.00001f;
+}
+
 // Squared pruning radius: best widened by kSlack, kept finite.
 __device__ __forceinline__ float bound2(float best) { return fminf(best * kSlack, FLT_MAX); }
 
@@ -87,7 +96,7 @@ __device__ __forceinline__ void warp_min(Best& B) {
 
 // Every row from table entry e on is farther than the current best.
 __device__ __forceinline__ bool cleared(const GridView& g, const SearchTable& tab, int e, float best) {
-    const float lbd = sqrtf(__ldg(tab.lb2 + e)) * g.cell - g.tol;
+    const float lbd = __ldg(tab.lb + e) * g.cell - g.tol;
     return lbd > 0.f && lbd * lbd > bound2(best);
 }
 
@@ -105,7 +114,7 @@ __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, 
             w.rows += 1;
             // the row's cells within reach along x; cell_start bounds their points (empty cells add none)
             const int rowi = z * g.dims.y + y;
-            const float r = sqrtf(rem) + g.tol;
+            const float r = sqrt_up(rem) + g.tol;
             const int x0 = max(max(cell_floor_clamped(q.x - r, g.origin.x, g.inv_cell, g.dims.x), 0), xlo);
             const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), g.dims.x - 1), xhi);
             if (x0 <= x1) {
@@ -170,7 +179,8 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
     const int lane = threadIdx.x & 31;
     const QueryCell c = query_cell(g, q);
     for (int base = 0; base < n;) {
-        if (cleared(g, tab, base, B.d)) return bound2(B.d) <= cap2;
+        // (entry 0 is the query's own row, bound 0: never cleared)
+        if (base > 0 && cleared(g, tab, base, B.d)) return bound2(B.d) <= cap2;
         const int e = base + lane;
         const bool has = e < n;
         int y = 0, z = 0;

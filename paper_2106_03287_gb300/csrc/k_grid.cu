@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -347,21 +348,22 @@ int search_table_init(sicp_ctx* ctx) {
         return abs(a.dy) + abs(a.dz) < abs(b.dy) + abs(b.dz);
     });
     std::vector<short2> off(es.size());
-    std::vector<float> lb2(es.size());
+    std::vector<float> lb2(es.size()), lb(es.size());
     for (size_t i = 0; i < es.size(); ++i) {
         off[i] = make_short2(es[i].dy, es[i].dz);
         lb2[i] = es[i].lb2;
+        lb[i] = std::sqrt(es[i].lb2);   // correctly rounded, as sqrtf on the device
     }
     if (cudaMalloc(&ctx->tab_off, sizeof(short2) * off.size()) != cudaSuccess ||
-        cudaMalloc(&ctx->tab_lb2, sizeof(float) * lb2.size()) != cudaSuccess) {
+        cudaMalloc(&ctx->tab_lb, sizeof(float) * lb.size()) != cudaSuccess) {
         cudaGetLastError();
         return set_err(ctx, SICP_ENOMEM, "search table allocation failed");
     }
     SICP_CUDA(cudaMemcpy(ctx->tab_off, off.data(), sizeof(short2) * off.size(), cudaMemcpyHostToDevice));
-    SICP_CUDA(cudaMemcpy(ctx->tab_lb2, lb2.data(), sizeof(float) * lb2.size(), cudaMemcpyHostToDevice));
+    SICP_CUDA(cudaMemcpy(ctx->tab_lb, lb.data(), sizeof(float) * lb.size(), cudaMemcpyHostToDevice));
     SearchTable& t = ctx->search.tab;
     t.off = ctx->tab_off;
-    t.lb2 = ctx->tab_lb2;
+    t.lb = ctx->tab_lb;
     t.n = (int)off.size();
     for (int k = 0; k < 8; ++k) {
         const float cap = 1.5f * (float)(1 << k);
