@@ -15,9 +15,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;  // queries in flight per CTA, one warp each
-constexpr int kGradThreads = 64;       // gradient kernel CTA: one warp per particle
-constexpr int kPb = kGradThreads / 32;  // particles per CTA in the gradient kernel
-constexpr int kKc = 4;                 // minibatch entries per warp in the gradient kernel
+constexpr int kGradThreads = 128;      // gradient kernel CTA: one warp per particle
 constexpr int kCoarseFactor = 4;
 constexpr float kFineReach = 6.f;      // the far phase proves on the fine level below this many cells
 constexpr int kTableRadius = 48;

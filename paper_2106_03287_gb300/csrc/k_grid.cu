@@ -72,15 +72,18 @@ __global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float*
 // under a neighbouring particle, so the previous answer is a starting bound
 // (kept when it lies within kReuse cells, else the seed map is used).  Lane 0
 // writes the query's gradient terms to qterms[j][k]; a fixed-order reduction
-// over k follows (launch_qterms_to_gbar).
-constexpr int kSeq = 2;                                   // particles per warp
+// over k follows (launch_qterms_to_gbar).  One particle per warp is fastest
+// on the kinect scene: the seed map gives a tighter start than a neighbouring
+// particle's answer (45.2 against 46.6 candidates per query), and 128-thread
+// CTAs at 40 registers hold 48 warps per SM.
+constexpr int kSeq = 1;                                   // particles per warp
 constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
 constexpr float kReuse = 2.f;
 
 // The search description is read from device memory (the reference build
 // rewrites it there), so a captured graph of these launches stays valid when
 // the reference changes.  (Staging it in shared memory was slower.)
-__global__ void __launch_bounds__(kGradThreads, 20) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd) {
+__global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd) {
     __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x;
