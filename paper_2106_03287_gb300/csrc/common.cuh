@@ -87,6 +87,16 @@ __device__ __forceinline__ void grad_terms(const Pose& P, float3 s, float3 e, fl
     }
 }
 
+// Term c (0..5) of grad_terms, by the same arithmetic, for a lane of its own.
+__device__ __forceinline__ float grad_term(const Pose& P, float3 s, float3 e, int c) {
+    if (c < 3) return c == 0 ? e.x : (c == 1 ? e.y : e.z);
+    const float* D = P.dR + 9 * (c - 3);
+    const float jx = fmaf(D[0], s.x, fmaf(D[1], s.y, D[2] * s.z));
+    const float jy = fmaf(D[3], s.x, fmaf(D[4], s.y, D[5] * s.z));
+    const float jz = fmaf(D[6], s.x, fmaf(D[7], s.y, D[8] * s.z));
+    return fmaf(e.x, jx, fmaf(e.y, jy, e.z * jz));
+}
+
 // Point-to-plane: the residual vector d = s' - r replaced by (n . d) n, n the
 // unit normal at r (xyz of n4), so that grad_terms gives the gradient of
 // (n . d)^2 / 2.

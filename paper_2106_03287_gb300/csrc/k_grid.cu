@@ -119,19 +119,12 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
             }
         }
         if (!seeded) grid_search(S, q, B, w);
-        if (lane == 0) {
-            float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool found = B.i != kNone;   // false only for a non-finite distance
-            if (found) {
-                float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
-                if (a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
-                grad_terms(P[jl], s, d, t);
-            }
-            float* dst = a.partial + ((int64_t)j * a.m + k) * 6;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) dst[c] = t[c];
-            if (a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
-        }
+        // the six gradient terms, one per lane (B, q and s are the same in every lane)
+        const bool found = B.i != kNone;   // false only for a non-finite distance
+        float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
+        if (found && a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
+        if (lane < 6) a.partial[((int64_t)j * a.m + k) * 6 + lane] = found ? grad_term(P[jl], s, d, lane) : 0.f;
+        if (lane == 0 && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
     }
     if (a.stats) add_stats(a.stats, w);
 }
