@@ -334,7 +334,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->ref4) cudaFree(c->ref4);
     for (Grid* g : {&c->grid, &c->grid2}) {
         void* gp[] = {g->sorted, g->cell_start, g->cell_of, g->counts, g->scan_sums, g->seed,
-                      g->seed_tmp};
+                      g->seed_tmp, g->seed4};
         for (void* p : gp)
             if (p) cudaFree(p);
     }

@@ -128,6 +128,7 @@ struct GridView {
     const float4* sorted;           // M, w = original index bits
     const int32_t* cell_start;      // ncells + 1
     const int32_t* seed;            // ncells: position in `sorted` of a point near the cell centre (fine level)
+    const float4* seed4;            // ncells: that point itself (single-problem fine level; null elsewhere)
 };
 
 struct Grid {
@@ -140,6 +141,8 @@ struct Grid {
     int32_t* scan_sums = nullptr;   // build scratch
     int32_t* seed = nullptr;        // ncells (fine level only)
     int32_t* seed_tmp = nullptr;    // ncells (build scratch)
+    float4* seed4 = nullptr;        // ncells (fine level only)
+    size_t cap_seed4 = 0;
     size_t cap_points = 0, cap_cellof = 0, cap_cells = 0, cap_counts = 0, cap_sums = 0,
            cap_seed = 0, cap_seed_tmp = 0;
 };

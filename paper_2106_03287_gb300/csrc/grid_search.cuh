@@ -206,10 +206,16 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
     const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
     const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
     const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
-    const int s = __ldg(F.seed + ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx);
-    if (s >= 0) {
-        const float4 r = __ldg(F.sorted + s);
+    const int64_t cell = ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx;
+    if (F.seed4) {   // the seed point itself: one load
+        const float4 r = __ldg(F.seed4 + cell);
         take(B, r, q, __float_as_int(r.w));
+    } else {
+        const int s = __ldg(F.seed + cell);
+        if (s >= 0) {
+            const float4 r = __ldg(F.sorted + s);
+            take(B, r, q, __float_as_int(r.w));
+        }
     }
     prove(S, q, B, w);
 }

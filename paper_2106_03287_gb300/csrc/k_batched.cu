@@ -481,6 +481,7 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
             v.sorted = (const float4*)L.sorted.p;
             v.cell_start = (const int32_t*)L.cell_start.p + L.h_cell_off[p];
             v.seed = l == 0 ? (const int32_t*)L.seed.p + L.h_cell_off[p] : nullptr;
+            v.seed4 = nullptr;
         }
         SICP_CUDA(cudaMemcpyAsync(L.views.p, L.hv.data(), sizeof(GridView) * P, cudaMemcpyHostToDevice, s));
         SICP_CUDA(cudaMemcpyAsync(L.cell_off.p, L.h_cell_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));

@@ -230,6 +230,16 @@ __global__ void k_seed_step(GridView g, int64_t ncells, int k, const int32_t* __
     }
 }
 
+// The seed points themselves, so that a query's first candidate is one load
+// (none: an infinitely far point, never taken).
+__global__ void k_seed_points(const float4* __restrict__ sorted, const int32_t* __restrict__ seed, int64_t ncells,
+                              float4* __restrict__ seed4) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = seed[c];
+        seed4[c] = s >= 0 ? sorted[s] : make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(-1));
+    }
+}
+
 unsigned blocks_for(int64_t n, int threads, int cap = 8192) {
     int64_t b = (n + threads - 1) / threads;
     return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
@@ -278,6 +288,7 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     if (seeds) {
         if ((rc = grow(ctx, G.seed, G.cap_seed, (size_t)ncells))) return rc;
         if ((rc = grow(ctx, G.seed_tmp, G.cap_seed_tmp, (size_t)ncells))) return rc;
+        if ((rc = grow(ctx, G.seed4, G.cap_seed4, (size_t)ncells))) return rc;
     }
     // the scatter target doubles as the unsorted staging area of the per-cell sort
     float4* staging = (float4*)ctx->tmp_aux.p;
@@ -292,6 +303,7 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     v.sorted = G.sorted;
     v.cell_start = G.cell_start;
     v.seed = seeds ? G.seed : nullptr;
+    v.seed4 = seeds ? G.seed4 : nullptr;
     G.ncells = ncells;
     SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
     k_cell_assign<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, v, G.cell_of, G.counts);
@@ -318,6 +330,8 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
             std::swap(a, b);
         }
         if (a != G.seed) SICP_CUDA(cudaMemcpyAsync(G.seed, a, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, s));
+        k_seed_points<<<blocks_for(ncells, 256), 256, 0, s>>>(G.sorted, G.seed, ncells, G.seed4);
+        SICP_CUDA(cudaGetLastError());
     }
     return SICP_OK;
 }
