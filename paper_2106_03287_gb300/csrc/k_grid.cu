@@ -83,6 +83,9 @@ constexpr float kReuse = 2.f;
 // The search description is read from device memory (the reference build
 // rewrites it there), so a captured graph of these launches stays valid when
 // the reference changes.  (Staging it in shared memory was slower.)
+// kStats: the work counters are kept (sicp_stats on); otherwise they are dead
+// code and the compiler drops them.
+template <bool kStats>
 __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd) {
     __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
         if (lane < 6) a.partial[((int64_t)j * a.m + k) * 6 + lane] = found ? grad_term(P[jl], s, d, lane) : 0.f;
         if (lane == 0 && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
     }
-    if (a.stats) add_stats(a.stats, w);
+    if (kStats) add_stats(a.stats, w);
 }
 
 // ---------------------------------------------------------------- build kernels
@@ -445,7 +448,8 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
 
 cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s) {
     dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
-    cudaError_t e = launch_pdl(k_grad_grid, grid, dim3(kGradThreads), 0, s, a, d_search);
+    cudaError_t e = a.stats ? launch_pdl(k_grad_grid<true>, grid, dim3(kGradThreads), 0, s, a, d_search)
+                            : launch_pdl(k_grad_grid<false>, grid, dim3(kGradThreads), 0, s, a, d_search);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
 }
