@@ -262,7 +262,8 @@ void collect_profile(sicp_ctx* ctx, GraphSlot& s) {
 }
 
 cudaError_t launch_grad(sicp_ctx* ctx, int32_t mode, const GradArgs& g) {
-    if (mode == SICP_NN_GRID) return launch_grad_grid(g, (const GridSearch*)ctx->search_dev.p, ctx->stream);
+    if (mode == SICP_NN_GRID)
+        return launch_grad_grid(g, (const GridSearch*)ctx->search_dev.p, ctx->search_slot, ctx->stream);
     return launch_grad_brute(g, ctx->ref4, ctx->M, ctx->stream);
 }
 
@@ -324,6 +325,7 @@ void sicp_destroy(sicp_ctx* c) {
     DeviceScope ds(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     delete c->graphs;
+    search_slot_release(c->search_slot);
     if (c->batch) batch_destroy(c->batch);
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,

@@ -232,6 +232,7 @@ struct sicp_ctx {
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
     sicp::Buf search_dev;                // device copy of `search`, rewritten by every reference build
+    int search_slot = -2;                // constant-memory copy of `search` (-2: none yet, -1: none free)
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
 };
@@ -380,7 +381,10 @@ int grid_build(sicp_ctx* ctx, float cell_size);
 int search_table_init(sicp_ctx* ctx);
 cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32_t* idx, float* d2,
                            unsigned long long* stats, cudaStream_t s);
-// d_search: the device copy of the context's GridSearch (sicp_ctx::search_dev)
-cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s);
+// d_search: the device copy of the context's GridSearch (sicp_ctx::search_dev);
+// slot: the context's constant-memory copy (sicp_ctx::search_slot), or < 0
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s);
+int search_slot_acquire();   // a free constant-memory slot, or -1
+void search_slot_release(int slot);
 
 }  // namespace sicp

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -44,6 +45,16 @@
 
 namespace sicp {
 namespace {
+
+// Search descriptions in constant memory, one slot per context (uniform reads
+// through the constant cache, as fast as kernel parameters).  A reference
+// build rewrites its context's slot in stream order, so a captured loop stays
+// valid when the reference changes.  Contexts beyond kSearchSlots read the
+// device-memory copy instead.
+constexpr int kSearchSlots = 32;
+__constant__ GridSearch c_search[kSearchSlots];
+std::mutex g_slot_mu;
+bool g_slot_used[kSearchSlots];
 
 using namespace gs;
 
@@ -85,8 +96,9 @@ constexpr float kReuse = 2.f;
 // the reference changes.  (Staging it in shared memory was slower.)
 // kStats: the work counters are kept (sicp_stats on); otherwise they are dead
 // code and the compiler drops them.
-template <bool kStats>
-__global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd) {
+template <bool kStats, bool kConst>
+__global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd,
+                                                                int slot) {
     __shared__ Pose P[kPart];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x;
@@ -96,7 +108,7 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
     for (int i = threadIdx.x; i < kPart; i += blockDim.x)
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
-    const GridSearch& S = *Sd;
+    const GridSearch& S = kConst ? c_search[slot] : *Sd;
     const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
     float3 s = make_float3(s4.x, s4.y, s4.z);
     const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
@@ -429,6 +441,10 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
     // the device copy the captured gradient launches read
     if ((rc = ensure(ctx, ctx->search_dev, sizeof(GridSearch)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->search_dev.p, &ctx->search, sizeof(GridSearch), cudaMemcpyHostToDevice, s));
+    if (ctx->search_slot == -2) ctx->search_slot = search_slot_acquire();
+    if (ctx->search_slot >= 0)
+        SICP_CUDA(cudaMemcpyToSymbolAsync(c_search, &ctx->search, sizeof(GridSearch),
+                                          sizeof(GridSearch) * (size_t)ctx->search_slot, cudaMemcpyHostToDevice, s));
     return SICP_OK;
 }
 
@@ -446,10 +462,32 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, cudaStream_t s) {
+int search_slot_acquire() {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int i = 0; i < kSearchSlots; ++i)
+        if (!g_slot_used[i]) {
+            g_slot_used[i] = true;
+            return i;
+        }
+    return -1;
+}
+
+void search_slot_release(int slot) {
+    if (slot < 0 || slot >= kSearchSlots) return;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    g_slot_used[slot] = false;
+}
+
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s) {
     dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
-    cudaError_t e = a.stats ? launch_pdl(k_grad_grid<true>, grid, dim3(kGradThreads), 0, s, a, d_search)
-                            : launch_pdl(k_grad_grid<false>, grid, dim3(kGradThreads), 0, s, a, d_search);
+    const dim3 blk(kGradThreads);
+    cudaError_t e;
+    if (slot >= 0)
+        e = a.stats ? launch_pdl(k_grad_grid<true, true>, grid, blk, 0, s, a, d_search, slot)
+                    : launch_pdl(k_grad_grid<false, true>, grid, blk, 0, s, a, d_search, slot);
+    else
+        e = a.stats ? launch_pdl(k_grad_grid<true, false>, grid, blk, 0, s, a, d_search, slot)
+                    : launch_pdl(k_grad_grid<false, false>, grid, blk, 0, s, a, d_search, slot);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
 }
