@@ -91,9 +91,10 @@ constexpr int kSeq = 1;                                   // particles per warp
 constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
 constexpr float kReuse = 2.f;
 
-// The search description is read from device memory (the reference build
-// rewrites it there), so a captured graph of these launches stays valid when
-// the reference changes.  (Staging it in shared memory was slower.)
+// The search description is read from memory that the reference build
+// rewrites, so a captured graph of these launches stays valid when the
+// reference changes: kConst, the context's constant-memory slot c_search[slot];
+// else the device copy Sd.  (Staging it in shared memory was slower.)
 // kStats: the work counters are kept (sicp_stats on); otherwise they are dead
 // code and the compiler drops them.
 template <bool kStats, bool kConst>
