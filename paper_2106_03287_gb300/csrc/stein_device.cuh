@@ -454,8 +454,7 @@ constexpr long long kArriveSpins = 1ll << 22;   // ~0.3 s of 64 ns polls
 // nothing but one arrival: a CTA writes theta only after all P CTAs of its
 // block have read it (a.arrive[b] counts arrivals, a.gen * P of them by the end
 // of update a.gen; bounded wait, a.err set on timeout, and then nothing is
-// written).  P > 1 needs all CTAs co-resident
-// (cooperative launch).
+// written).  P > 1 needs all CTAs co-resident (see launch_stein_adam).
 __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, int q, int P) {
     extern __shared__ float sm[];
     float* th = sm;               // K x 6 (all components: pair_d2 indexes the full rows)
