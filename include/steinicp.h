@@ -149,6 +149,33 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
 int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float* state, int32_t K,
                            int64_t t0, const sicp_params* p, double* mean6, double* cov36, int on_device);
 
+/* The context's run state as bytes, for checkpoints that outlive the
+ * context or the process.  After a finished sicp_register,
+ * sicp_register_continue or sicp_resume, the context holds that run's K,
+ * iterations done t, minibatch seed, particles and Adam moments.
+ * sicp_export_state writes them to buf (host memory): "SICPRUN1", u32
+ * version 1, i32 K, i64 t, u64 seed, float32 state [3][K][6] (particles,
+ * first moments, second moments), u32 CRC-32 (IEEE polynomial, reflected)
+ * of all bytes before it; host byte order; 36 + 72 K bytes.  With buf NULL
+ * only *len is set to that size.  Errors: SICP_EINVAL (no finished run in
+ * the context; *len smaller than needed, then *len is set to the size),
+ * SICP_ECUDA.
+ * sicp_import_state makes such bytes the context's run state (checked:
+ * magic, version, size, checksum, 1 <= K <= 2048, finite values); errors
+ * SICP_EINVAL, SICP_ENOMEM, SICP_ECUDA.  A failed call leaves the context
+ * without a run state. */
+int sicp_export_state(sicp_ctx* ctx, void* buf, size_t* len);
+int sicp_import_state(sicp_ctx* ctx, const void* buf, size_t len);
+
+/* T = p->T more iterations of the context's run state (previous run, or
+ * sicp_import_state): the same as sicp_register_continue with that state
+ * and t0.  p->seed must be the run's seed.  particles_out [K][6] (may be
+ * NULL), mean6, cov36 as sicp_register; the context's state moves on to
+ * t0 + T.  Errors as sicp_register, plus SICP_EINVAL when the context has
+ * no run state or the seed differs. */
+int sicp_resume(sicp_ctx* ctx, const float* src_xyz, int64_t N, const sicp_params* p, float* particles_out,
+                double* mean6, double* cov36, int on_device);
+
 /* ---- many problems at once ---- */
 
 /* P independent runs of sicp_register (Sec. IV summary) in one persistent

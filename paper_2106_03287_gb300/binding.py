@@ -45,6 +45,7 @@ EXPORTS = (
     "sicp_pose_distribution", "sicp_compound", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
+    "sicp_export_state", "sicp_import_state", "sicp_resume",
 )
 
 SURROGATE_NPARAM = 33040
@@ -103,6 +104,9 @@ def lib() -> ctypes.CDLL:
             "sicp_surrogate_loss_grad": (ctypes.c_int, [P, P, P, P, I64, F32, F32, P, P]),
             "sicp_surrogate_infer": (ctypes.c_int, [P, P, I64, P, P, ctypes.c_int]),
             "sicp_register_continue": (ctypes.c_int, [P, P, I64, P, I32, I64, pp, P, P, ctypes.c_int]),
+            "sicp_export_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
+            "sicp_import_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+            "sicp_resume": (ctypes.c_int, [P, P, I64, pp, P, P, P, ctypes.c_int]),
             "sicp_surrogate_save": (ctypes.c_int, [P, ctypes.c_char_p]),
             "sicp_surrogate_load": (ctypes.c_int, [P, ctypes.c_char_p]),
             "sicp_reference_normals": (ctypes.c_int, [P, I32, P, ctypes.c_int]),
@@ -243,6 +247,39 @@ def sicp_register_continue(ctx, src_xyz, state, t0: int, params: sicp_params):
                                              K, int(t0), ctypes.byref(params), _ptr(mean, np.float64),
                                              _ptr(cov, np.float64), _on_device(src_xyz, state)))
     return mean, cov
+
+
+def sicp_export_state(ctx) -> bytes:
+    """The context's run state (K, iterations done, seed, particles and Adam
+    moments, checksummed) as bytes."""
+    n = ctypes.c_size_t(0)
+    _check(ctx, lib().sicp_export_state(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, lib().sicp_export_state(ctx, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def sicp_import_state(ctx, data: bytes):
+    """Make bytes from sicp_export_state the context's run state."""
+    data = bytes(data)
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check(ctx, lib().sicp_import_state(ctx, buf, len(data)))
+
+
+def sicp_resume(ctx, src_xyz, params: sicp_params):
+    """params.T more iterations of the context's run state.  Returns
+    (particles [K][6], mean [6], cov [6][6])."""
+    n = ctypes.c_size_t(0)
+    _check(ctx, lib().sicp_export_state(ctx, None, ctypes.byref(n)))   # 36 + 72 K bytes
+    K = (n.value - 36) // 72
+    src_xyz = _host(src_xyz, np.float32)
+    out = _empty(src_xyz, (K, 6), np.float32)
+    mean = _empty(src_xyz, (6,), np.float64)
+    cov = _empty(src_xyz, (6, 6), np.float64)
+    _check(ctx, lib().sicp_resume(ctx, _ptr(src_xyz, np.float32), src_xyz.shape[0], ctypes.byref(params),
+                                  _ptr(out, np.float32), _ptr(mean, np.float64), _ptr(cov, np.float64),
+                                  _on_device(src_xyz)))
+    return out, mean, cov
 
 
 def sicp_minibatch(ctx, seed: int, t0: int, T: int, N: int, m: int, device=None):

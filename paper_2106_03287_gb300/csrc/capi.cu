@@ -330,7 +330,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar,
-                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref};
+                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -645,6 +645,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
                  int64_t t0, const float* adam_in, float* adam_out) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
+    ctx->run_valid = false;   // set again once this run has finished
     if (!src_xyz || !particles_in || !particles_out || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
     if (t0 < 0 || t0 > ((int64_t)1 << 40)) return set_err(ctx, SICP_EINVAL, "t0 must lie in [0, 2^40]");
     const sicp_params p = normalise(p_in);
@@ -861,8 +862,36 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         if ((rc = copy_out(ctx, adam_out, ctx->adam_m.p, b_th, on_device))) return rc;
         if ((rc = copy_out(ctx, adam_out + 6 * (size_t)K, ctx->adam_v.p, b_th, on_device))) return rc;
     }
-    return sync(ctx);
+    if ((rc = sync(ctx))) return rc;
+    ctx->run_valid = true;
+    ctx->run_K = K;
+    ctx->run_t = t0 + p.T;
+    ctx->run_seed = p.seed;
+    return SICP_OK;
 }
+
+}  // namespace
+
+// ---- the context's run state as a byte string
+//   "SICPRUN1" | u32 version (1) | i32 K | i64 t | u64 seed | f32 state[3][K][6] | u32 CRC-32
+// in host byte order; the CRC (IEEE 802.3 polynomial, reflected, as in zlib)
+// covers every byte before it.
+
+namespace {
+
+constexpr char kStateMagic[8] = {'S', 'I', 'C', 'P', 'R', 'U', 'N', '1'};
+constexpr size_t kStateHead = 8 + 4 + 4 + 8 + 8;
+
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+    uint32_t c = 0xffffffffu;
+    for (size_t i = 0; i < n; ++i) {
+        c ^= p[i];
+        for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xedb88320u & (0u - (c & 1u)));
+    }
+    return ~c;
+}
+
+size_t state_bytes(int32_t K) { return kStateHead + sizeof(float) * 18 * (size_t)K + 4; }
 
 }  // namespace
 
@@ -882,6 +911,128 @@ int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float
     // the particles are read before they are overwritten (staged into the context first)
     return register_run(ctx, src_xyz, N, state, K, p, state, mean6, cov36, on_device, t0, state + 6 * (size_t)K,
                         state + 6 * (size_t)K);
+}
+
+int sicp_export_state(sicp_ctx* ctx, void* buf, size_t* len) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!len) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (!ctx->run_valid) return set_err(ctx, SICP_EINVAL, "no finished run in this context");
+    const int32_t K = ctx->run_K;
+    const size_t need = state_bytes(K);
+    if (!buf) {
+        *len = need;
+        return SICP_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return set_err(ctx, SICP_EINVAL, "buffer too small: %zu bytes needed", need);
+    }
+    DeviceScope ds(ctx->device);
+    unsigned char* o = (unsigned char*)buf;
+    const uint32_t version = 1;
+    const int64_t t = ctx->run_t;
+    const uint64_t seed = ctx->run_seed;
+    memcpy(o, kStateMagic, 8);
+    memcpy(o + 8, &version, 4);
+    memcpy(o + 12, &K, 4);
+    memcpy(o + 16, &t, 8);
+    memcpy(o + 24, &seed, 8);
+    const size_t b = sizeof(float) * 6 * (size_t)K;
+    std::vector<float> h(18 * (size_t)K);
+    SICP_CUDA(cudaMemcpyAsync(h.data(), ctx->theta.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(h.data() + 6 * (size_t)K, ctx->adam_m.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(h.data() + 12 * (size_t)K, ctx->adam_v.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+    int rc = sync(ctx);
+    if (rc) return rc;
+    memcpy(o + kStateHead, h.data(), 3 * b);
+    const uint32_t crc = crc32_ieee(o, need - 4);
+    memcpy(o + need - 4, &crc, 4);
+    *len = need;
+    return SICP_OK;
+}
+
+int sicp_import_state(sicp_ctx* ctx, const void* buf, size_t len) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!buf) return set_err(ctx, SICP_EINVAL, "null pointer");
+    const unsigned char* in = (const unsigned char*)buf;
+    if (len < kStateHead + 4 || memcmp(in, kStateMagic, 8) != 0) return set_err(ctx, SICP_EINVAL, "not a run state");
+    uint32_t version, crc;
+    int32_t K;
+    int64_t t;
+    uint64_t seed;
+    memcpy(&version, in + 8, 4);
+    memcpy(&K, in + 12, 4);
+    memcpy(&t, in + 16, 8);
+    memcpy(&seed, in + 24, 8);
+    if (version != 1) return set_err(ctx, SICP_EINVAL, "run state version %u not supported", version);
+    if (K < 1 || K > kMaxK) return set_err(ctx, SICP_EINVAL, "particle count must be in [1, %d]", kMaxK);
+    if (len != state_bytes(K)) return set_err(ctx, SICP_EINVAL, "run state of %zu bytes, %zu expected", len, state_bytes(K));
+    memcpy(&crc, in + len - 4, 4);
+    if (crc != crc32_ieee(in, len - 4)) return set_err(ctx, SICP_EINVAL, "run state checksum mismatch");
+    if (t < 0 || t > ((int64_t)1 << 40)) return set_err(ctx, SICP_EINVAL, "t must lie in [0, 2^40]");
+    std::vector<float> h(18 * (size_t)K);
+    memcpy(h.data(), in + kStateHead, sizeof(float) * h.size());
+    if (!host_finite(h.data(), (int64_t)h.size())) return set_err(ctx, SICP_EINVAL, "non-finite state");
+    DeviceScope ds(ctx->device);
+    const size_t b = sizeof(float) * 6 * (size_t)K;
+    int rc;
+    ctx->run_valid = false;
+    if ((rc = ensure(ctx, ctx->theta, b)) || (rc = ensure(ctx, ctx->adam_m, b)) || (rc = ensure(ctx, ctx->adam_v, b)))
+        return rc;
+    SICP_CUDA(cudaMemcpyAsync(ctx->theta.p, h.data(), b, cudaMemcpyHostToDevice, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(ctx->adam_m.p, h.data() + 6 * (size_t)K, b, cudaMemcpyHostToDevice, ctx->stream));
+    SICP_CUDA(cudaMemcpyAsync(ctx->adam_v.p, h.data() + 12 * (size_t)K, b, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = sync(ctx))) return rc;
+    ctx->run_valid = true;
+    ctx->run_K = K;
+    ctx->run_t = t;
+    ctx->run_seed = seed;
+    return SICP_OK;
+}
+
+int sicp_resume(sicp_ctx* ctx, const float* src_xyz, int64_t N, const sicp_params* p, float* particles_out,
+                double* mean6, double* cov36, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!p) return set_err(ctx, SICP_EINVAL, "null pointer");
+    if (!ctx->run_valid) return set_err(ctx, SICP_EINVAL, "no run to resume in this context");
+    if (p->seed != ctx->run_seed)
+        return set_err(ctx, SICP_EINVAL, "the run draws its minibatches with seed %llu",
+                       (unsigned long long)ctx->run_seed);
+    DeviceScope ds(ctx->device);
+    const int32_t K = ctx->run_K;
+    const int64_t t0 = ctx->run_t;
+    const size_t b = sizeof(float) * 6 * (size_t)K;
+    std::vector<float> h;
+    float* st;
+    int rc;
+    if (on_device) {   // the state as register_run reads it: [3][K][6] in one device buffer
+        if ((rc = ensure(ctx, ctx->resume, 3 * b))) return rc;
+        st = (float*)ctx->resume.p;
+        SICP_CUDA(cudaMemcpyAsync(st, ctx->theta.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(st + 6 * (size_t)K, ctx->adam_m.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(st + 12 * (size_t)K, ctx->adam_v.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        h.resize(18 * (size_t)K);
+        st = h.data();
+        SICP_CUDA(cudaMemcpyAsync(st, ctx->theta.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(st + 6 * (size_t)K, ctx->adam_m.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+        SICP_CUDA(cudaMemcpyAsync(st + 12 * (size_t)K, ctx->adam_v.p, b, cudaMemcpyDeviceToHost, ctx->stream));
+        if ((rc = sync(ctx))) return rc;
+    }
+    rc = register_run(ctx, src_xyz, N, st, K, p, st, mean6, cov36, on_device, t0, st + 6 * (size_t)K,
+                      st + 6 * (size_t)K);
+    if (rc) return rc;
+    if (particles_out) {
+        if (on_device) {
+            SICP_CUDA(cudaMemcpyAsync(particles_out, st, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            return sync(ctx);
+        }
+        memcpy(particles_out, st, b);
+    }
+    return SICP_OK;
 }
 
 int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8) {

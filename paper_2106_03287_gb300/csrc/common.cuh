@@ -233,6 +233,13 @@ struct sicp_ctx {
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
     sicp::Buf search_dev;                // device copy of `search`, rewritten by every reference build
     int search_slot = -2;                // constant-memory copy of `search` (-2: none yet, -1: none free)
+    // the last registration run: its particles and Adam moments stay in theta,
+    // adam_m, adam_v (sicp_export_state, sicp_import_state, sicp_resume)
+    bool run_valid = false;
+    int32_t run_K = 0;
+    int64_t run_t = 0;                   // iterations done
+    uint64_t run_seed = 0;               // its minibatch stream
+    sicp::Buf resume;                    // device staging of that state for sicp_resume
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
 };
