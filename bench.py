@@ -209,7 +209,7 @@ def ncu_traffic_per_query():
     return rec["dram_bytes"] / rec["queries"]
 
 
-def cpu_baseline(d, cfg, budget_s=15.0, metric="point"):
+def cpu_baseline(d, cfg, budget_s=15.0, metric="point", single_budget_s=6.0):
     """The oracle as it stands, on a bounded number of iterations of the same workload
     (point-to-plane: the reference normals are computed before the timed sample)."""
     import oracle as O
@@ -227,10 +227,25 @@ def cpu_baseline(d, cfg, budget_s=15.0, metric="point"):
     for t in range(1, 1 + n):
         O.step(ref, src, th, mom, vel, p, t)
     dt = time.perf_counter() - t0
-    return {"value": K * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": f"{n} SVGD iterations (iterations 1..{n}) of the same workload, exhaustive FP64 search, "
-                      f"{dt:.1f} s", "iters_per_sec": n / dt}
+    cores = O.num_threads()
+    out = {"value": K * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": cores,
+           "kind": "oracle",
+           "sample": f"{n} SVGD iterations (iterations 1..{n}) of the same workload, exhaustive FP64 search, "
+                     f"{dt:.1f} s", "iters_per_sec": n / dt}
+    # the same oracle on one thread, for the next few iterations (a shorter bounded sample)
+    n1 = min(cfg["T"] - 1 - n, max(1, int(single_budget_s * n / max(dt, 1e-6) / max(cores, 1))))
+    if n1 >= 1:
+        O.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            for t in range(1 + n, 1 + n + n1):
+                O.step(ref, src, th, mom, vel, p, t)
+            dt1 = time.perf_counter() - t0
+        finally:
+            O.set_threads(cores)
+        out["single_thread"] = {"value": K * cfg["m"] * n1 / dt1, "cores": 1,
+                                "sample": f"{n1} SVGD iterations (iterations {1 + n}..{n + n1}), {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):

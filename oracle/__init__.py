@@ -86,6 +86,7 @@ def _setup(L):
         "or_step": (None, [_p, _i64, _p, _i64, _p, _p, _p, _i32, _p, _i64, _p, _p, _p, _p]),
         "or_register": (ctypes.c_int, [_p, _i64, _p, _i64, _p, _i32, _p, _p, _p, _p]),
         "or_num_threads": (ctypes.c_int, []),
+        "or_set_threads": (None, [ctypes.c_int]),
         "or_mlp_nparam": (ctypes.c_int, []),
         "or_bf16": (_f64, [_f64]),
         "or_mlp_features": (None, [_p, _p]),
@@ -144,6 +145,11 @@ class Params:
 
 def num_threads() -> int:
     return _L().or_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (timing only; results do not depend on it)."""
+    _L().or_set_threads(int(n))
 
 
 def splitmix64_at(state: int, k: int) -> int:

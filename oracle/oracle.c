@@ -577,6 +577,16 @@ OR_EXPORT int or_num_threads(void) {
 #endif
 }
 
+/* Threads for the parallel loops that follow (n >= 1); timing only, the
+ * results do not depend on it. */
+OR_EXPORT void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Learned closest-point field (the surrogate of the correspondence search)  */
 /* ------------------------------------------------------------------------ */
