@@ -108,8 +108,8 @@ def make_problem(workload: str, seed: int):
 NORMAL_K = 10   # neighbours of the reference normals of the point-to-plane metric
 # kernels of one sicp_set_reference per workload, counted in ncu launch lists: pack, bbox, the fine
 # level (cell assignment, 3-kernel scan, scatter, cell sort, seed init, seed-flooding steps) and the
-# coarse level; the number of flooding steps follows the grid's size
-SETREF_LAUNCHES = {"kinect": 22, "box": 21, "lidar": 24, "mc": 22, "surrogate": 22}
+# coarse level, plus the seed points; the number of flooding steps follows the grid's size
+SETREF_LAUNCHES = {"kinect": 23, "box": 22, "lidar": 25, "mc": 23, "surrogate": 23}
 
 
 def metric_name(metric):
@@ -465,7 +465,7 @@ def run_ours(args):
     S.sicp_destroy(ctx)
     per_iter = {"grid": 3, "fp32": 2, "bf16": 3}.get(nn)
     if per_iter is not None:
-        # reference build (pack, bbox, two grid levels, seed map: 22 launches on the kinect grid, counted
+        # reference build (pack, bbox, two grid levels, seed map: 23 launches on the kinect grid, counted
         # in an ncu launch list), the run's pack / finite check / minibatch / moments, and per iteration
         # the gradient kernel(s) and the Stein kernel; point-to-plane adds the normals kernel
         launches_per_step = (SETREF_LAUNCHES[args.workload] + 4 + per_iter * cfg["T"] + (1 if plane else 0)
