@@ -33,10 +33,11 @@
  *    written (all argument checks), and sicp_last_error() describes it.  No
  *    error path traps the GPU.
  *  - A context is not thread-safe: one host thread at a time per context.
- *  - Environment (read once, for diagnosis; results do not change):
+ *  - Environment (for diagnosis; results do not change):
  *    SICP_NO_GRAPH runs the registration loop as plain launches instead of a
  *    captured CUDA graph; SICP_NO_PDL launches its kernels in plain stream
- *    order instead of with programmatic dependent launch.
+ *    order instead of with programmatic dependent launch (read once per
+ *    process).
  */
 #ifndef STEINICP_H
 #define STEINICP_H
