@@ -10,12 +10,17 @@ Parity status of each function (what pins it in `tests/test_oracle.py`):
   minibatch       selection invariants and per-index frequency
   rotation        scipy's rotation from fixed-axis angles; orthogonality;
                   central differences for the partial derivatives
-  nn / nn2        scipy cKDTree; exact duplicates and self-queries
+  nn / nn2        scipy cKDTree (nearest and second-nearest distances);
+                  exact duplicates and self-queries
+  KDTree          identical indices and distances to the exhaustive nn on
+                  random, clustered, lattice (many exact ties) and
+                  duplicated clouds, queries near and far
   icp_grad        central differences of L/2; single-point closed form
   bandwidths      numpy.median; two-particle closed form
   stein_phi       two-particle closed form (incl. wrap across +-pi);
                   SVGD on a Gaussian target; K = 1 reduces to G
-  adam            closed form under a constant gradient
+  adam            closed form under a constant gradient; three steps under a
+                  varying gradient worked out by hand (exact fractions)
   register        K = 1 recovery of a known pose on noise-free data
 """
 from __future__ import annotations
@@ -61,7 +66,8 @@ _i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes
 class _Params(ctypes.Structure):
     _fields_ = [("T", _i32), ("m", _i32), ("lr", _f64), ("beta1", _f64), ("beta2", _f64),
                 ("eps", _f64), ("seed", _u64), ("prior", _i32), ("mu", _f64 * 6),
-                ("sigma", _f64 * 3), ("kappa", _f64 * 3), ("normals", _p), ("independent", _i32)]
+                ("sigma", _f64 * 3), ("kappa", _f64 * 3), ("normals", _p), ("independent", _i32),
+                ("tree", _p)]
 
 
 def _setup(L):
@@ -74,7 +80,11 @@ def _setup(L):
         "or_nn2": (None, [_p, _i64, _p, _i64, _p, _p, _p]),
         "or_icp_grad": (None, [_p, _i64, _p, _p, _i32, _p, _i32, _p, _p, _p, _p]),
         "or_icp_grad_given_nn": (None, [_p, _p, _p, _i32, _p, _i32, _p, _p, _p]),
-        "or_knn": (None, [_p, _i64, _i32, _p]),
+        "or_knn": (None, [_p, _i64, _i32, _p, _p]),
+        "or_kd_build": (_p, [_p, _i64]),
+        "or_kd_free": (None, [_p]),
+        "or_kd_nn": (None, [_p, _p, _i64, _p, _p]),
+        "or_icp_grad_kd": (None, [_p, _p, _p, _i32, _p, _i32, _p, _p, _p, _p]),
         "or_neighbourhood_cov": (None, [_p, _i64, _i32, _p, _p]),
         "or_log_post_grad": (None, [_p, _p, _i32, _f64, _i32, _p, _p, _p, _p]),
         "or_median": (_f64, [_p, _i64]),
@@ -128,6 +138,7 @@ class Params:
     kappa: tuple = (1.0,) * 3
     normals: object = None     # None: point-to-point; M x 3 unit normals: point-to-plane (R16)
     independent: bool = False  # independent SGD-ICP runs, no Stein coupling (R17)
+    tree: object = None        # None: exhaustive search; a KDTree of the reference: the same answers, faster
 
     def c(self) -> _Params:
         p = _Params()
@@ -140,6 +151,8 @@ class Params:
         if self.normals is not None:
             self._normals64 = _f64a(self.normals)     # kept alive with the parameters
             p.normals = _ptr(self._normals64)
+        if self.tree is not None:
+            p.tree = self.tree.handle
         return p
 
 
@@ -195,6 +208,50 @@ def nn2(ref, q):
     return idx, d2, d2b
 
 
+class KDTree:
+    """k-d tree of a reference cloud (oracle.c, or_kd_build): nearest
+    neighbours identical to the exhaustive search `nn`, lowest index on ties,
+    in far fewer distance evaluations.  Pass it as Params(tree=...) to make
+    `step` and `register` search through it."""
+
+    def __init__(self, ref):
+        self.ref = _f32(ref).copy()          # the tree points into this array
+        self.handle = _L().or_kd_build(_ptr(self.ref), self.ref.shape[0])
+        if not self.handle:
+            raise ValueError("or_kd_build failed")
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.or_kd_free(h)
+
+    def nn(self, q):
+        q = _f64a(q).reshape(-1, 3)
+        n = q.shape[0]
+        idx = np.empty(n, np.int64)
+        d2 = np.empty(n)
+        _L().or_kd_nn(self.handle, _ptr(q), n, _ptr(idx), _ptr(d2))
+        return idx, d2
+
+    def icp_grad(self, src, mb, theta, normals=None):
+        """icp_grad of the tree's reference, searching through the tree."""
+        src = _f32(src)
+        mb = np.ascontiguousarray(mb, np.int32)
+        th = _f64a(theta).reshape(-1, 6)
+        K, m = th.shape[0], mb.shape[0]
+        g = np.empty((K, 6))
+        nnk = np.empty((K, m), np.int64)
+        loss = np.empty(K)
+        keep, np_ = _normals_ptr(normals, self.ref.shape[0])
+        _L().or_icp_grad_kd(self.handle, _ptr(src), _ptr(mb), m, _ptr(th), K, np_, _ptr(g), _ptr(nnk), _ptr(loss))
+        return g, nnk, loss
+
+
+def _check_tree(ref, params):
+    if params.tree is not None and not (params.tree.ref.shape == ref.shape and np.array_equal(params.tree.ref, ref)):
+        raise ValueError("Params.tree was built on another reference cloud")
+
+
 def transform(theta, pts):
     """R(theta) p + u for each row of pts (float64 result)."""
     R, _ = rotation(theta)
@@ -236,16 +293,17 @@ def icp_grad_given_nn(ref, src, mb, theta, nnk, normals=None):
     return g
 
 
-def knn(ref, k: int):
+def knn(ref, k: int, with_d2: bool = False):
     """The k nearest reference points of every reference point (itself
-    included), nearest first, ranked by fp32 squared distance with ties to
-    the lower index: M x k indices."""
+    included), nearest first, ranked by exact fp64 squared distance with ties
+    to the lower index: M x k indices (and the M x k squared distances)."""
     ref = _f32(ref)
     if not 1 <= k <= min(64, ref.shape[0]):
         raise ValueError("knn needs 1 <= k <= min(64, M)")
     idx = np.empty((ref.shape[0], k), np.int64)
-    _L().or_knn(_ptr(ref), ref.shape[0], k, _ptr(idx))
-    return idx
+    d2 = np.empty((ref.shape[0], k))
+    _L().or_knn(_ptr(ref), ref.shape[0], k, _ptr(idx), _ptr(d2))
+    return (idx, d2) if with_d2 else idx
 
 
 def neighbourhood_cov(ref, idx):
@@ -326,6 +384,7 @@ def step(ref, src, th, mom, vel, params: Params, t: int):
     """Iteration t in place on th, mom, vel (float64 K x 6); returns the
     iteration's gbar, G, phi and (h_t, h_r)."""
     ref, src = _f32(ref), _f32(src)
+    _check_tree(ref, params)
     for a in (th, mom, vel):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     K = th.shape[0]
@@ -338,6 +397,7 @@ def step(ref, src, th, mom, vel, params: Params, t: int):
 
 def register(ref, src, theta0, params: Params):
     ref, src, th0 = _f32(ref), _f32(src), _f32(theta0).reshape(-1, 6)
+    _check_tree(ref, params)
     K = th0.shape[0]
     th = np.empty((K, 6))
     mean = np.empty(6)

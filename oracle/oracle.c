@@ -43,9 +43,10 @@
  *      terms with the residual vector replaced by e n.  The normal at a
  *      reference point is the eigenvector of the smallest eigenvalue of the
  *      covariance of its k nearest reference points (itself included), the
- *      neighbours ranked by the fp32 squared distance fmaf(dx, dx, fmaf(dy,
- *      dy, dz * dz)) with dx = r_x - q_x in fp32, ties to the lower index (the
- *      decision is taken in the kernel's precision); the covariance in fp64.
+ *      neighbours ranked by their exact fp64 squared distance, ties to the
+ *      lower index; the covariance in fp64.  Where the k-th and (k+1)-th
+ *      distances tie to within fp32 rounding the neighbourhood, and so the
+ *      normal, is not unique, and a float32 ranking may pick either set.
  *  R17 Monte Carlo ground truth (the experiments' reference distribution:
  *      many SGD-ICP runs from spread initial poses): with `independent` set,
  *      every particle j is its own SGD-ICP run (Sec. III-B): its own
@@ -217,6 +218,164 @@ OR_EXPORT void or_nn2(const float* ref, int64_t M, const double* q, int64_t nq,
 }
 
 /* ------------------------------------------------------------------------ */
+/* The same argmin through a k-d tree (a faster route to or_nn's answer)     */
+/* ------------------------------------------------------------------------ */
+/*
+ * A k-d tree over the reference points: each node holds a contiguous range
+ * of a permutation of the point indices and the tight bounding box of its
+ * points; an inner node splits its range at the median of the box's longest
+ * axis.  A query walks the tree depth first, nearer child first, and skips a
+ * node only when the squared distance from the query to the node's box is
+ * strictly larger than the best squared distance found so far.  The box
+ * distance is summed over the axes in the same order (x, y, z) as a point's
+ * squared distance, and floating-point subtraction, squaring and addition are
+ * monotone, so no point of a skipped box can be nearer than or tie with the
+ * best: the walk returns exactly or_nn's answer, lowest index on ties (R12).
+ */
+#define OR_KD_LEAF 8
+
+typedef struct {
+    int64_t lo, hi;          /* range [lo, hi) of perm */
+    int64_t left, right;     /* children (-1 for a leaf) */
+    double bmin[3], bmax[3]; /* bounding box of the node's points */
+} or_kdnode;
+
+typedef struct or_kdtree {
+    const float* ref;
+    int64_t M;
+    int64_t* perm;
+    or_kdnode* node;
+    int64_t n_nodes, cap;
+} or_kdtree;
+
+static double or_kd_coord(const or_kdtree* t, int64_t i, int a) { return (double)t->ref[3 * t->perm[i] + a]; }
+
+static void or_kd_swap(int64_t* p, int64_t a, int64_t b) { int64_t x = p[a]; p[a] = p[b]; p[b] = x; }
+
+/* Reorder perm[lo, hi) so that perm[k] holds the point of rank k - lo along
+ * axis a (ties by index), smaller ranks before it, larger after (quickselect). */
+static void or_kd_select(or_kdtree* t, int64_t lo, int64_t hi, int64_t k, int a) {
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        or_kd_swap(t->perm, mid, hi - 1);
+        const double pv = or_kd_coord(t, hi - 1, a);
+        const int64_t pi = t->perm[hi - 1];
+        int64_t store = lo;
+        for (int64_t i = lo; i < hi - 1; ++i) {
+            const double v = or_kd_coord(t, i, a);
+            if (v < pv || (v == pv && t->perm[i] < pi)) or_kd_swap(t->perm, i, store++);
+        }
+        or_kd_swap(t->perm, store, hi - 1);
+        if (store == k) return;
+        if (k < store) hi = store; else lo = store + 1;
+    }
+}
+
+static int64_t or_kd_new_node(or_kdtree* t, int64_t lo, int64_t hi) {
+    if (t->n_nodes == t->cap) {
+        t->cap = t->cap ? 2 * t->cap : 64;
+        t->node = (or_kdnode*)realloc(t->node, sizeof(or_kdnode) * (size_t)t->cap);
+    }
+    or_kdnode* n = &t->node[t->n_nodes];
+    n->lo = lo; n->hi = hi; n->left = n->right = -1;
+    for (int a = 0; a < 3; ++a) { n->bmin[a] = INFINITY; n->bmax[a] = -INFINITY; }
+    for (int64_t i = lo; i < hi; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const double v = or_kd_coord(t, i, a);
+            if (v < n->bmin[a]) n->bmin[a] = v;
+            if (v > n->bmax[a]) n->bmax[a] = v;
+        }
+    return t->n_nodes++;
+}
+
+static int64_t or_kd_build_node(or_kdtree* t, int64_t lo, int64_t hi) {
+    const int64_t id = or_kd_new_node(t, lo, hi);
+    if (hi - lo <= OR_KD_LEAF) return id;
+    int axis = 0;
+    double best = -1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double ext = t->node[id].bmax[a] - t->node[id].bmin[a];
+        if (ext > best) { best = ext; axis = a; }
+    }
+    const int64_t mid = lo + (hi - lo) / 2;
+    or_kd_select(t, lo, hi, mid, axis);
+    const int64_t l = or_kd_build_node(t, lo, mid);
+    const int64_t r = or_kd_build_node(t, mid, hi);
+    t->node[id].left = l;       /* (t->node may have moved while the children were built) */
+    t->node[id].right = r;
+    return id;
+}
+
+/* Build a tree over ref (M x 3 floats; the caller keeps ref alive while the
+ * tree is used).  NULL on bad arguments or when memory runs out. */
+OR_EXPORT or_kdtree* or_kd_build(const float* ref, int64_t M) {
+    if (!ref || M < 1) return NULL;
+    or_kdtree* t = (or_kdtree*)calloc(1, sizeof(or_kdtree));
+    if (!t) return NULL;
+    t->ref = ref;
+    t->M = M;
+    t->perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
+    if (!t->perm) { free(t); return NULL; }
+    for (int64_t i = 0; i < M; ++i) t->perm[i] = i;
+    or_kd_build_node(t, 0, M);
+    return t;
+}
+
+OR_EXPORT void or_kd_free(or_kdtree* t) {
+    if (!t) return;
+    free(t->perm);
+    free(t->node);
+    free(t);
+}
+
+/* Squared distance from q to a node's box, summed in the order of a point's. */
+static double or_kd_box_d2(const or_kdnode* n, const double q[3]) {
+    double g[3];
+    for (int a = 0; a < 3; ++a) {
+        if (q[a] < n->bmin[a]) g[a] = n->bmin[a] - q[a];
+        else if (q[a] > n->bmax[a]) g[a] = q[a] - n->bmax[a];
+        else g[a] = 0.0;
+    }
+    return g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+}
+
+static int64_t or_kd_nn_one(const or_kdtree* t, const double q[3], double* d2_out) {
+    int64_t stack[128];
+    int sp = 0;
+    int64_t best = -1;
+    double bd = INFINITY;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const or_kdnode* n = &t->node[stack[--sp]];
+        if (or_kd_box_d2(n, q) > bd) continue;
+        if (n->left < 0) {
+            for (int64_t i = n->lo; i < n->hi; ++i) {
+                const int64_t r = t->perm[i];
+                const double dx = (double)t->ref[3 * r] - q[0];
+                const double dy = (double)t->ref[3 * r + 1] - q[1];
+                const double dz = (double)t->ref[3 * r + 2] - q[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < bd || (d2 == bd && r < best)) { bd = d2; best = r; }
+            }
+            continue;
+        }
+        const double dl = or_kd_box_d2(&t->node[n->left], q);
+        const double dr = or_kd_box_d2(&t->node[n->right], q);
+        /* push the farther child first so that the nearer one is walked first */
+        if (dl <= dr) { stack[sp++] = n->right; stack[sp++] = n->left; }
+        else { stack[sp++] = n->left; stack[sp++] = n->right; }
+    }
+    *d2_out = bd;
+    return best;
+}
+
+/* or_nn through the tree: the same indices and distances. */
+OR_EXPORT void or_kd_nn(const or_kdtree* t, const double* q, int64_t nq, int64_t* idx, double* d2) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nq; ++i) idx[i] = or_kd_nn_one(t, q + 3 * i, d2 + i);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Mean ICP gradient, Eqs. (trans_gradient) and (rotation_gradient), R3      */
 /* ------------------------------------------------------------------------ */
 
@@ -267,9 +426,9 @@ static double or_grad_given_nn_one(const float* ref, const float* src, const int
  * minibatch (nn_out: K x m, may be NULL) and gbar (K x 6).  loss_out (K, may be
  * NULL) receives L/2 over the minibatch.  normals (M x 3, may be NULL): the
  * point-to-plane metric (R16). */
-OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const int32_t* mb,
-                           int32_t m, const double* th, int32_t K, const double* normals, double* gbar,
-                           int64_t* nn_out, double* loss_out) {
+static void or_icp_grad_tree(const float* ref, int64_t M, const or_kdtree* tree, const float* src,
+                             const int32_t* mb, int32_t m, const double* th, int32_t K, const double* normals,
+                             double* gbar, int64_t* nn_out, double* loss_out) {
     int64_t* nn = (int64_t*)malloc(sizeof(int64_t) * (size_t)K * (size_t)m);
     double* qs = (double*)malloc(sizeof(double) * 3 * (size_t)K * (size_t)m);
     for (int32_t j = 0; j < K; ++j) {
@@ -281,7 +440,7 @@ OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const 
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t q = 0; q < (int64_t)K * m; ++q) {
         double d2;
-        nn[q] = or_nn_one(ref, M, qs + 3 * q, &d2);
+        nn[q] = tree ? or_kd_nn_one(tree, qs + 3 * q, &d2) : or_nn_one(ref, M, qs + 3 * q, &d2);
     }
     for (int32_t j = 0; j < K; ++j) {
         double l = or_grad_given_nn_one(ref, src, mb, m, th + 6 * j, nn + (int64_t)j * m, normals, gbar + 6 * j);
@@ -290,6 +449,19 @@ OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const 
     if (nn_out) memcpy(nn_out, nn, sizeof(int64_t) * (size_t)K * (size_t)m);
     free(nn);
     free(qs);
+}
+
+OR_EXPORT void or_icp_grad(const float* ref, int64_t M, const float* src, const int32_t* mb,
+                           int32_t m, const double* th, int32_t K, const double* normals, double* gbar,
+                           int64_t* nn_out, double* loss_out) {
+    or_icp_grad_tree(ref, M, NULL, src, mb, m, th, K, normals, gbar, nn_out, loss_out);
+}
+
+/* The same through a k-d tree of ref (or_kd_build): identical results. */
+OR_EXPORT void or_icp_grad_kd(const or_kdtree* tree, const float* src, const int32_t* mb, int32_t m,
+                              const double* th, int32_t K, const double* normals, double* gbar,
+                              int64_t* nn_out, double* loss_out) {
+    or_icp_grad_tree(tree->ref, tree->M, tree, src, mb, m, th, K, normals, gbar, nn_out, loss_out);
 }
 
 /* Same gradient with the correspondences given (K x m reference indices). */
@@ -305,18 +477,18 @@ OR_EXPORT void or_icp_grad_given_nn(const float* ref, const float* src, const in
 /* ------------------------------------------------------------------------ */
 
 /* The k nearest reference points of every reference point (itself included),
- * nearest first: exhaustive, fp32 squared distances, ties to the lower index.
- * idx: M x k. */
-OR_EXPORT void or_knn(const float* ref, int64_t M, int32_t k, int64_t* idx) {
+ * nearest first: exhaustive, exact fp64 squared distances, ties to the lower
+ * index.  idx: M x k; d2 (M x k, may be NULL) the squared distances. */
+OR_EXPORT void or_knn(const float* ref, int64_t M, int32_t k, int64_t* idx, double* d2_out) {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < M; ++i) {
-        float bd[64];
+        double bd[64];
         int64_t bi[64];
         int32_t n = 0;
-        const float qx = ref[3 * i], qy = ref[3 * i + 1], qz = ref[3 * i + 2];
+        const double qx = ref[3 * i], qy = ref[3 * i + 1], qz = ref[3 * i + 2];
         for (int64_t r = 0; r < M; ++r) {
-            const float dx = ref[3 * r] - qx, dy = ref[3 * r + 1] - qy, dz = ref[3 * r + 2] - qz;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const double dx = (double)ref[3 * r] - qx, dy = (double)ref[3 * r + 1] - qy, dz = (double)ref[3 * r + 2] - qz;
+            const double d2 = dx * dx + dy * dy + dz * dz;
             if (n == k && !(d2 < bd[k - 1])) continue;      /* r > every kept index: equal loses */
             int32_t p = n < k ? n++ : k - 1;                /* insertion position from the end */
             while (p > 0 && d2 < bd[p - 1]) {
@@ -327,7 +499,10 @@ OR_EXPORT void or_knn(const float* ref, int64_t M, int32_t k, int64_t* idx) {
             bd[p] = d2;
             bi[p] = r;
         }
-        for (int32_t c = 0; c < k; ++c) idx[i * k + c] = c < n ? bi[c] : -1;
+        for (int32_t c = 0; c < k; ++c) {
+            idx[i * k + c] = c < n ? bi[c] : -1;
+            if (d2_out) d2_out[i * k + c] = c < n ? bd[c] : INFINITY;
+        }
     }
 }
 
@@ -514,6 +689,7 @@ typedef struct {
     double mu[6], sigma[3], kappa[3];
     const double* normals;   /* NULL: point-to-point; else M x 3: point-to-plane (R16) */
     int32_t independent;     /* 1: independent SGD-ICP runs, phi_j = G_j (R17) */
+    const or_kdtree* tree;   /* NULL: exhaustive search; else a k-d tree of ref (same answers, faster) */
 } or_params;
 
 /* Iteration t (0-based) in place on th, mom, vel (each K x 6).  Optional
@@ -530,11 +706,11 @@ OR_EXPORT void or_step(const float* ref, int64_t M, const float* src, int64_t N,
     if (p->independent) {
         for (int32_t j = 0; j < K; ++j) {
             or_minibatch(p->seed + (uint64_t)j, t, N, p->m, mb);
-            or_icp_grad(ref, M, src, mb, p->m, th + 6 * j, 1, p->normals, gbar + 6 * j, NULL, NULL);
+            or_icp_grad_tree(ref, M, p->tree, src, mb, p->m, th + 6 * j, 1, p->normals, gbar + 6 * j, NULL, NULL);
         }
     } else {
         or_minibatch(p->seed, t, N, p->m, mb);
-        or_icp_grad(ref, M, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
+        or_icp_grad_tree(ref, M, p->tree, src, mb, p->m, th, K, p->normals, gbar, NULL, NULL);
     }
     or_log_post_grad(th, gbar, K, (double)N, p->prior, p->mu, p->sigma, p->kappa, G);
     double h_t = 1.0, h_r = 1.0;

@@ -136,6 +136,76 @@ def test_nn_ties_go_to_lowest_index_and_self_queries_are_exact():
         assert idx[r] == same.min()
 
 
+def test_nn2_second_distance_matches_kdtree():
+    rng = np.random.default_rng(5)
+    base = rng.uniform(-1, 1, (1500, 3)).astype(np.float32)
+    ref = np.concatenate([base, base[:20]])          # duplicates: their second distance is 0
+    q = np.concatenate([rng.uniform(-1.3, 1.3, (600, 3)), base[:20].astype(np.float64)])
+    idx, d2, d2b = O.nn2(ref, q)
+    dd, ii = cKDTree(ref.astype(np.float64)).query(q, k=2)
+    assert np.allclose(d2, dd[:, 0] ** 2, rtol=1e-12, atol=1e-15)
+    assert np.allclose(d2b, dd[:, 1] ** 2, rtol=1e-12, atol=1e-15)
+    assert np.all(d2b[-20:] == 0.0) and np.all(d2b >= d2)
+    i1, _ = O.nn(ref, q)
+    assert np.array_equal(idx, i1)
+
+
+def _kd_clouds():
+    rng = np.random.default_rng(21)
+    c = rng.uniform(-1, 1, (12, 3))
+    lat = np.stack(np.meshgrid(*[np.arange(8)] * 3, indexing="ij"), -1).reshape(-1, 3) * 0.25
+    base = rng.uniform(-1, 1, (700, 3))
+    return {
+        "uniform": rng.uniform(-1, 1, (5000, 3)),
+        "clustered": c[rng.integers(0, 12, 4000)] + rng.normal(0, 1e-3, (4000, 3)),
+        "lattice": lat[rng.permutation(lat.shape[0])],                 # many exact ties
+        "duplicates": np.concatenate([base, base[:300], base[:300], base[:5]])[rng.permutation(1305)],
+        "box": synth.make_box_problem(2)["ref"],
+        "planar": np.c_[rng.uniform(-1, 1, (3000, 2)), np.zeros(3000)],
+        "one": np.array([[0.1, -0.2, 0.3]]),
+        "two": np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0]]),
+    }
+
+
+@pytest.mark.parametrize("name", ["uniform", "clustered", "lattice", "duplicates", "box", "planar", "one", "two"])
+def test_kdtree_equals_exhaustive_search(name):
+    """The k-d tree returns exactly the exhaustive argmin, lowest index on ties."""
+    ref = _kd_clouds()[name].astype(np.float32)
+    rng = np.random.default_rng(len(name))
+    ext = float(np.abs(ref).max()) + 1e-3
+    q = np.concatenate([
+        rng.uniform(-1.2 * ext, 1.2 * ext, (1500, 3)),                        # inside and around
+        rng.uniform(-50 * ext, 50 * ext, (200, 3)),                           # far away
+        ref[rng.integers(0, ref.shape[0], 300)].astype(np.float64),           # on reference points
+        (ref[rng.integers(0, ref.shape[0], 200)] + 0.125).astype(np.float64),  # lattice midpoints: ties
+    ])
+    i_b, d_b = O.nn(ref, q)
+    i_k, d_k = O.KDTree(ref).nn(q)
+    assert np.array_equal(i_b, i_k)
+    assert np.array_equal(d_b, d_k)
+    if name == "lattice":     # the tie rule was exercised: some queries have several nearest points
+        dd, _ = cKDTree(ref.astype(np.float64)).query(q, k=2)
+        assert np.sum(dd[:, 1] == dd[:, 0]) > 50
+
+
+def test_kdtree_gradient_and_run_equal_exhaustive():
+    d = synth.make_box_problem(4, K=6)
+    tree = O.KDTree(d["ref"])
+    mb = O.minibatch(3, 0, d["src"].shape[0], 100)
+    th = d["particles"].astype(np.float64)
+    g_b, nn_b, l_b = O.icp_grad(d["ref"], d["src"], mb, th)
+    g_k, nn_k, l_k = tree.icp_grad(d["src"], mb, th)
+    assert np.array_equal(nn_b, nn_k) and np.array_equal(g_b, g_k) and np.array_equal(l_b, l_k)
+    p = O.Params(T=15, m=60, lr=0.01, seed=5)
+    a = O.register(d["ref"], d["src"], d["particles"], p)
+    p.tree = tree
+    b = O.register(d["ref"], d["src"], d["particles"], p)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    with pytest.raises(ValueError):
+        O.register(d["ref"][:-1], d["src"], d["particles"], p)        # a tree of another cloud
+
+
 # ---------------------------------------------------------------- ICP gradient
 
 def _half_loss(theta, ref, src_mb):
@@ -248,13 +318,18 @@ def test_point_to_plane_gradient_closed_form():
 def test_knn_matches_kdtree(k):
     rng = np.random.default_rng(k)
     ref = rng.uniform(-1, 1, (3000, 3)).astype(np.float32)
-    idx = O.knn(ref, k)
+    idx, d2 = O.knn(ref, k, with_d2=True)
     d, i = cKDTree(ref.astype(np.float64)).query(ref.astype(np.float64), k + 1)
     assert np.array_equal(idx[:, 0], np.arange(3000))             # each point is its own nearest
     same = np.array([set(idx[r]) == set(i[r, :k]) for r in range(3000)])
-    # a set may differ only where the k-th and (k+1)-th fp64 distances tie to fp32 rounding
-    near_tie = np.abs(d[:, k] - d[:, k - 1]) <= 1e-6 * d[:, k]
-    assert np.all(same | near_tie) and same.mean() > 0.99
+    # ranked by the exact fp64 distance: a set may differ only at an exact tie of the k-th and
+    # (k+1)-th distances (to the rounding of scipy's own distance sum)
+    near_tie = np.abs(d[:, k] - d[:, k - 1]) <= 1e-12 * d[:, k]
+    assert np.all(same | near_tie) and same.mean() > 0.999
+    assert np.allclose(d2, d[:, :k] ** 2, rtol=1e-12, atol=1e-15)
+    assert np.all(np.diff(d2, axis=1) >= 0)
+    exact = ((ref[idx].astype(np.float64) - ref[:, None, :].astype(np.float64)) ** 2).sum(-1)
+    assert np.allclose(d2, exact, rtol=1e-15, atol=0)
     # ties go to the lower index: duplicates of point 7 follow it in index order
     dup = np.concatenate([ref[:100], ref[7:8], ref[7:8]])
     di = O.knn(dup, 3)
@@ -611,6 +686,44 @@ def test_adam_constant_gradient_closed_form():
     for t in range(1, 11):
         O.adam(x, mom, vel, g, t, 0.01)
         assert np.allclose(x, -t * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-18)
+
+
+def test_adam_three_steps_varying_gradient_by_hand():
+    """beta1 = 1/2, beta2 = 3/4, eps = 0, gradients 1, -1, 2 (worked by hand):
+    m = 1/2, -1/4, 7/8 and v = 1/4, 7/16, 85/64; bias corrections 1/2, 3/4, 7/8
+    and 1/4, 7/16, 37/64 give mhat = 1, -1/3, 1 and vhat = 1, 1, 85/37, so the
+    steps are lr, -lr/3, lr sqrt(37/85).  Swapping the betas gives another
+    third step (the second case below), and dropping the bias correction
+    another first step (m1 / sqrt(v1) = 1 only with both corrections)."""
+    lr = 0.1
+    x, mom, vel = np.zeros(1), np.zeros(1), np.zeros(1)
+    steps = []
+    for t, g in enumerate([1.0, -1.0, 2.0], start=1):
+        x0 = x.copy()
+        O.adam(x, mom, vel, np.array([g]), t, lr, 0.5, 0.75, 0.0)
+        steps.append(float(x0[0] - x[0]))
+        if t == 2:
+            assert mom[0] == -0.25 and vel[0] == 7.0 / 16.0
+    assert steps[0] == pytest.approx(lr, rel=1e-15)
+    assert steps[1] == pytest.approx(-lr / 3.0, rel=1e-15)
+    assert steps[2] == pytest.approx(lr * math.sqrt(37.0 / 85.0), rel=1e-15)
+    assert mom[0] == 0.875 and vel[0] == 85.0 / 64.0
+    # betas swapped (beta1 = 3/4, beta2 = 1/2): m = 1/4, -1/16, 29/64; v = 1/2, 3/4, 19/8;
+    # corrections 1/4, 7/16, 37/64 and 1/2, 3/4, 7/8: mhat_3 = 29/37, vhat_3 = 19/7
+    x, mom, vel = np.zeros(1), np.zeros(1), np.zeros(1)
+    for t, g in enumerate([1.0, -1.0, 2.0], start=1):
+        x0 = x.copy()
+        O.adam(x, mom, vel, np.array([g]), t, lr, 0.75, 0.5, 0.0)
+    assert float(x0[0] - x[0]) == pytest.approx(lr * (29.0 / 37.0) / math.sqrt(19.0 / 7.0), rel=1e-14)
+    assert mom[0] == 29.0 / 64.0 and vel[0] == 19.0 / 8.0
+    # the defaults (0.9, 0.999, eps 1e-8) with gradients 1, 0: mhat_2 = 0.09 / 0.19,
+    # vhat_2 = 0.000999 / 0.001999, second step lr * mhat_2 / (sqrt(vhat_2) + 1e-8)
+    x, mom, vel = np.zeros(1), np.zeros(1), np.zeros(1)
+    O.adam(x, mom, vel, np.array([1.0]), 1, lr)
+    x1 = x.copy()
+    O.adam(x, mom, vel, np.array([0.0]), 2, lr)
+    want = lr * (0.09 / 0.19) / (math.sqrt(0.000999 / 0.001999) + 1e-8)
+    assert float(x1[0] - x[0]) == pytest.approx(want, rel=1e-12)
 
 
 # ---------------------------------------------------------------- moments & whole run
