@@ -248,6 +248,29 @@ def cpu_baseline(d, cfg, budget_s=15.0, metric="point", single_budget_s=6.0):
     return out
 
 
+def pose_gate(name, d, mean, cov, metric="point"):
+    """The run's final pose mean and spread against the FP64 oracle run of the
+    same inputs stored by tests/golden/make_pose_gate.py ("at fixed pose
+    error": within 1 mm and 0.05 deg), with the oracle's own spread under a
+    one-ulp change of its initial particles beside it."""
+    from paper_2106_03287_gb300 import gate
+    path = os.path.join(ROOT, "tests", "golden", "pose_gate.json")
+    if metric != "point" or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f).get(name)
+    if g is None:
+        return None
+    same = g["inputs_sha256_16"] == gate.inputs_hash(d)
+    err = gate.pose_errors(mean, cov, np.array(g["mean"]), np.array(g["cov"]).reshape(6, 6))
+    fl = g["floor"]
+    return {"reference": f"FP64 oracle run {name}, tests/golden/pose_gate.json", "same_inputs": same, **err,
+            "gate_mm": gate.GATE_MM, "gate_deg": gate.GATE_DEG, "met": bool(same and gate.within(err)),
+            "oracle_ulp_floor": fl,
+            "within_2x_floor": bool(same and gate.within(err, max(gate.GATE_MM, 2 * max(fl["dmean_mm"], fl["dsd_mm"])),
+                                                        max(gate.GATE_DEG, 2 * max(fl["dmean_deg"], fl["dsd_deg"]))))}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -455,6 +478,11 @@ def run_ours(args):
                "h2d_bytes_per_step": (12 * M if with_ref else 0) + 12 * N + 24 * K,
                "d2h_bytes_per_step": 24 * K + 8 * 42, "ms_per_step": 1e3 * statistics.mean(wall)}
 
+    gate_rec = None
+    if rank == 0 and nn != "surrogate" and args.workload != "mc":
+        _, mean_f, cov_f = step()
+        gate_rec = pose_gate(args.workload, d, np.asarray(mean_f.cpu()), np.asarray(cov_f.cpu()), args.metric)
+
     comparison = None
     if nn in ("bf16", "surrogate"):
         comparison = compare_paths(S, ctx, nn, p, lambda: set_ref(ref_d), src_d, par_d, cfg, K, flush, stream,
@@ -485,6 +513,8 @@ def run_ours(args):
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu}
+        if gate_rec:
+            line["pose_gate"] = gate_rec
         if training:
             line["surrogate_training"] = training
         if comparison:

@@ -150,7 +150,9 @@ int sicp_register(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* p
  * p->seed and takes Adam step t + 1 whether the run is done in one call or
  * several, so continuing with t0 += T gives the particles of one longer call.
  * mean6, cov36 as sicp_register.  Errors as sicp_register, plus SICP_EINVAL
- * for t0 < 0 or t0 > 2^40. */
+ * for t0 < 0 or t0 > 2^40 or a negative second moment.  A call rejected by
+ * its argument checks leaves the context's run state (sicp_export_state)
+ * as it was. */
 int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float* state, int32_t K,
                            int64_t t0, const sicp_params* p, double* mean6, double* cov36, int on_device);
 
@@ -166,7 +168,8 @@ int sicp_register_continue(sicp_ctx* ctx, const float* src_xyz, int64_t N, float
  * the context; *len smaller than needed, then *len is set to the size),
  * SICP_ECUDA.
  * sicp_import_state makes such bytes the context's run state (checked:
- * magic, version, size, checksum, 1 <= K <= 2048, finite values); errors
+ * magic, version, size, checksum, 1 <= K <= 2048, finite values, second
+ * moments >= 0); errors
  * SICP_EINVAL, SICP_ENOMEM, SICP_ECUDA.  A failed call leaves the context
  * without a run state. */
 int sicp_export_state(sicp_ctx* ctx, void* buf, size_t* len);
@@ -346,15 +349,21 @@ int sicp_moments_circular(sicp_ctx* ctx, const float* particles, int32_t K, doub
  *
  * No context is needed and nothing is allocated.  All array arguments are
  * device pointers on the current device: reference ref_xyz [M][3], source
- * src_xyz [N][3], minibatch mb [m] (indices into the source), particles [K][6];
- * the result goes to out_gbar [K][6].  The work is queued on `cuda_stream`
- * (NULL: the legacy default stream) and the call returns without waiting.
+ * src_xyz [N][3], minibatch mb [m] (indices into the source; the device
+ * values are not checked on the host, and an entry outside [0, N) reads
+ * nothing and adds nothing to the sum, which is still divided by m),
+ * particles [K][6]; the result goes to out_gbar [K][6].  The work is queued
+ * on `cuda_stream` (NULL: the legacy default stream) and the call returns
+ * without waiting.
  *
  * Scratch: the kernel's partial sums and arrival counters live in one
  * file-scope device array of 25,600 bytes that every GPU loading this library
  * holds until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) for that device; make that
- * first call before any stream capture.  Each call clears the counters itself.
+ * array's device address (cudaGetSymbolAddress) for that device and keeps it
+ * for the life of the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset, or the primary context torn
+ * down and created again) invalidates the kept address and is not supported
+ * while the library is loaded.  Each call clears the counters itself.
  * Calls share the array, so calls that overlap on the GPU (on two streams,
  * or from two threads) race and must be serialised by the caller.
  *
@@ -459,6 +468,34 @@ int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8);
  * before it and the moments after it) to the gradient-kernel totals.
  * Synchronises the context's stream. */
 int sicp_profile(sicp_ctx* ctx, int stride, double* out4);
+
+/* ---- resource limits and failure detection (no counterpart in the paper) ---- */
+
+/* Device memory budget of a context: from now on an allocation that would
+ * take the bytes the context holds in its growable buffers (reference and
+ * its search structures, per-run state, scratch of every path) above `bytes`
+ * fails, and the call that needed it returns SICP_ENOMEM before it launches
+ * anything or writes any output.  0 removes the budget.  Buffers already
+ * held are kept and counted.  *held (may be NULL) receives the bytes held
+ * now.  A failed allocation can leave the context without its reference or
+ * run state (it frees the smaller buffer it was replacing first); set the
+ * reference again.  Never fails for a valid context. */
+int sicp_set_memory_limit(sicp_ctx* ctx, size_t bytes, size_t* held);
+
+/* Failure-detection check of the device waits.  Several kernels wait on the
+ * GPU for other CTAs (the CTAs of one Stein update, the grid barrier of the
+ * persistent batched kernel) or for the tensor cores (the mbarrier of the
+ * tensor-core search), and every such wait is bounded: it gives up after a
+ * number of polls, sets an error flag that the host reads, and the call
+ * returns SICP_ETIMEOUT with its outputs untouched, the GPU still usable.
+ * With on = 1 every such wait of the context's later calls waits for an
+ * event that never happens (one arrival more than there are CTAs; an
+ * mbarrier nothing arrives on, before any copy or MMA is issued) and gives
+ * up after `polls` polls (0: each wait's default limit, up to seconds), so
+ * the give-up path can be exercised on purpose.  on = 0 restores normal
+ * operation; polls then still caps the waits (0: the defaults).  Errors:
+ * SICP_EINVAL (polls outside [0, 2^30]). */
+int sicp_set_wait_check(sicp_ctx* ctx, int on, int64_t polls);
 
 #ifdef __cplusplus
 }

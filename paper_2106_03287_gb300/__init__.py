@@ -11,5 +11,5 @@ from .binding import (  # noqa: F401
     SURROGATE_NPARAM, sicp_surrogate_train, sicp_surrogate_params, sicp_surrogate_loss_grad, sicp_surrogate_infer,
     sicp_register_continue, sicp_surrogate_save, sicp_surrogate_load, sicp_reference_normals, SICP_POINT_TO_PLANE,
     SICP_INDEPENDENT, sicp_gaussian_kl, sicp_gaussian_ovl, sicp_pose_distribution, sicp_compound, chain_odometry,
-    sicp_export_state, sicp_import_state, sicp_resume,
+    sicp_export_state, sicp_import_state, sicp_resume, sicp_set_memory_limit, sicp_set_wait_check,
 )

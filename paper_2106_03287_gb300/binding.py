@@ -45,7 +45,7 @@ EXPORTS = (
     "sicp_pose_distribution", "sicp_compound", "sicp_stats", "sicp_profile", "sicp_icp_grad_noalloc", "sicp_register_batched", "sicp_autotune_batched",
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
-    "sicp_export_state", "sicp_import_state", "sicp_resume",
+    "sicp_export_state", "sicp_import_state", "sicp_resume", "sicp_set_memory_limit", "sicp_set_wait_check",
 )
 
 SURROGATE_NPARAM = 33040
@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
             "sicp_gaussian_ovl": (ctypes.c_int, [P, P, P, P, I32, P, P, ctypes.c_int64, P]),
             "sicp_pose_distribution": (ctypes.c_int, [P, I32, P, P]),
             "sicp_compound": (ctypes.c_int, [P, P, P, P, I32, P, P]),
+            "sicp_set_memory_limit": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+            "sicp_set_wait_check": (ctypes.c_int, [P, ctypes.c_int, I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -452,6 +454,19 @@ def sicp_stats(ctx, enable: bool = True):
     out = np.zeros(8, np.uint64)
     _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def sicp_set_memory_limit(ctx, nbytes: int) -> int:
+    """Cap the context's device memory at nbytes (0: no cap); returns the bytes it holds now."""
+    held = ctypes.c_size_t(0)
+    _check(ctx, lib().sicp_set_memory_limit(ctx, int(nbytes), ctypes.byref(held)))
+    return int(held.value)
+
+
+def sicp_set_wait_check(ctx, on: bool, polls: int = 0):
+    """Make every bounded device wait of later calls wait for an event that never comes (on = True),
+    giving up after `polls` polls (0: the defaults)."""
+    _check(ctx, lib().sicp_set_wait_check(ctx, int(bool(on)), int(polls)))
 
 
 def sicp_profile(ctx, stride: int = 0):

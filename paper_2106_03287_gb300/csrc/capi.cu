@@ -32,19 +32,31 @@ int cuda_err(sicp_ctx* c, cudaError_t e, const char* what) {
     return SICP_ECUDA;
 }
 
+int budget_malloc(sicp_ctx* c, void** p, size_t bytes, size_t held) {
+    *p = nullptr;
+    c->mem_used -= held < c->mem_used ? held : c->mem_used;
+    if (c->mem_limit && c->mem_used + bytes > c->mem_limit)
+        return set_err(c, SICP_ENOMEM, "device allocation of %zu bytes would pass the context's budget of %zu bytes "
+                       "(%zu held)", bytes, c->mem_limit, c->mem_used);
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_err(c, SICP_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    c->mem_used += bytes;
+    return SICP_OK;
+}
+
 int ensure(sicp_ctx* c, Buf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return SICP_OK;
+    const size_t held = b.cap;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
     const size_t want = bytes + bytes / 4;   // headroom so nearby sizes reuse the buffer
-    cudaError_t e = cudaMalloc(&b.p, want);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        cudaGetLastError();
-        return set_err(c, SICP_ENOMEM, "device allocation of %zu bytes failed", want);
-    }
+    int rc = budget_malloc(c, &b.p, want, held);
+    if (rc) return rc;
     b.cap = want;
     return SICP_OK;
 }
@@ -61,6 +73,8 @@ struct LoopKey {
     uint64_t seed;
     int64_t t0;             // first iteration of the run
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
+    int64_t wait_polls;     // failure-detection check settings (the kernels take them by value)
+    int32_t wait_never, pad2;
     const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -236,6 +250,8 @@ SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, c
     a.arrive = nullptr;
     a.err = nullptr;
     a.gen = 0;
+    a.max_spins = 0;
+    a.extra = 0;
     return a;
 }
 
@@ -359,13 +375,12 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
     int rc = stage_in(ctx, xyz, sizeof(float) * 3 * M, on_device, ctx->tmp_in, &d_xyz);
     if (rc) return rc;
     if ((size_t)M > ctx->ref_cap) {
+        const size_t held = sizeof(float4) * ctx->ref_cap;
         if (ctx->ref4) cudaFree(ctx->ref4);
         ctx->ref4 = nullptr;
         ctx->ref_cap = 0;
-        if (cudaMalloc(&ctx->ref4, sizeof(float4) * M) != cudaSuccess) {
-            cudaGetLastError();
-            return set_err(ctx, SICP_ENOMEM, "reference allocation failed");
-        }
+        ctx->M = 0;   // the old reference is gone
+        if ((rc = budget_malloc(ctx, (void**)&ctx->ref4, sizeof(float4) * M, held))) return rc;
         ctx->ref_cap = M;
     }
     ctx->M = 0;
@@ -583,6 +598,8 @@ int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_
     a.arrive = (unsigned*)(hh + 2);
     a.err = (int*)ctx->flags.p + 3;
     a.gen = 1;
+    a.max_spins = ctx->wait_polls;
+    a.extra = ctx->wait_never ? 1u : 0u;
     SICP_CUDA(cudaMemsetAsync(a.arrive, 0, 2 * sizeof(unsigned), ctx->stream));
     SICP_CUDA(launch_stein_adam(a, ctx->stream));
     if ((rc = read_flags(ctx, flags))) return rc;
@@ -645,7 +662,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
                  int64_t t0, const float* adam_in, float* adam_out) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
-    ctx->run_valid = false;   // set again once this run has finished
     if (!src_xyz || !particles_in || !particles_out || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
     if (t0 < 0 || t0 > ((int64_t)1 << 40)) return set_err(ctx, SICP_EINVAL, "t0 must lie in [0, 2^40]");
     const sicp_params p = normalise(p_in);
@@ -659,6 +675,11 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     if (!on_device && (!host_finite(src_xyz, 3 * N) || !host_finite(particles_in, 6 * (int64_t)K)))
         return set_err(ctx, SICP_EINVAL, "non-finite input");
+    if (adam_in && !on_device) {
+        if (!host_finite(adam_in, 12 * (int64_t)K)) return set_err(ctx, SICP_EINVAL, "non-finite input");
+        for (int64_t i = 6 * (int64_t)K; i < 12 * (int64_t)K; ++i)
+            if (adam_in[i] < 0.f) return set_err(ctx, SICP_EINVAL, "negative Adam second moment");
+    }
     DeviceScope ds(ctx->device);
     const bool plane = (p.nn_mode & SICP_POINT_TO_PLANE) != 0;
     const bool indep = (p.nn_mode & SICP_INDEPENDENT) != 0;
@@ -670,6 +691,9 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     const bool bf = nn_mode == SICP_NN_BRUTE_BF16;
     if (bf && (int64_t)K * p.m > ((int64_t)1 << 26))
         return set_err(ctx, SICP_EINVAL, "the tensor-core search needs K * m <= 2^26");
+    // every argument is valid: from here the run replaces the context's run state (the buffers
+    // below may be reallocated), which is valid again once the run has finished
+    ctx->run_valid = false;
     const bool grid = nn_mode == SICP_NN_GRID || surr;   // the surrogate's exact iterations use the grid
     const int32_t exact_mode = surr ? SICP_NN_GRID : nn_mode;
     const int chunks = (grid ? grad_layout_grid(p.m) : grad_layout(p.m)).chunks;
@@ -700,12 +724,11 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
     if (adam_in) {
         const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        if (!on_device && !host_finite(adam_in, 12 * (int64_t)K)) return set_err(ctx, SICP_EINVAL, "non-finite input");
         SICP_CUDA(cudaMemcpyAsync(ctx->adam_m.p, adam_in, b_th, kin, ctx->stream));
         SICP_CUDA(cudaMemcpyAsync(ctx->adam_v.p, adam_in + 6 * (size_t)K, b_th, kin, ctx->stream));
         if (on_device) {
             SICP_CUDA(launch_check_finite((const float*)ctx->adam_m.p, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
-            SICP_CUDA(launch_check_finite((const float*)ctx->adam_v.p, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
+            SICP_CUDA(launch_check_nonneg((const float*)ctx->adam_v.p, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
         }
     } else {
         SICP_CUDA(cudaMemsetAsync(ctx->adam_m.p, 0, b_th, ctx->stream));
@@ -744,6 +767,8 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.seed = p.seed;
     key.t0 = t0;
     key.ref_M = ctx->M;   // (the grid and BF16 kernels read the reference's description from device memory)
+    key.wait_polls = ctx->wait_polls;
+    key.wait_never = ctx->wait_never;
     key.ptrs[0] = ctx->src4.p;
     key.ptrs[1] = ctx->mb.p;
     key.ptrs[2] = ctx->theta.p;
@@ -802,6 +827,8 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
             a.arrive = (unsigned*)(med_state + 2);
             a.err = (int*)ctx->flags.p + 3;
             a.gen = (uint32_t)(t + 1);
+            a.max_spins = ctx->wait_polls;
+            a.extra = ctx->wait_never ? 1u : 0u;
             if (indep)
                 SICP_CUDA(launch_adam_independent(a, ctx->stream));
             else
@@ -852,7 +879,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     }
     int flags[4];
     if ((rc = read_flags(ctx, flags))) return rc;
-    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input");
+    if (flags[0]) return set_err(ctx, SICP_EINVAL, "non-finite input (or a negative Adam second moment)");
     if (flags[3])
         return set_err(ctx, SICP_ETIMEOUT, "a bounded wait on the GPU gave up (tensor-core search or Stein update)");
     if ((rc = copy_out(ctx, particles_out, theta, b_th, on_device))) return rc;
@@ -975,6 +1002,8 @@ int sicp_import_state(sicp_ctx* ctx, const void* buf, size_t len) {
     std::vector<float> h(18 * (size_t)K);
     memcpy(h.data(), in + kStateHead, sizeof(float) * h.size());
     if (!host_finite(h.data(), (int64_t)h.size())) return set_err(ctx, SICP_EINVAL, "non-finite state");
+    for (size_t i = 12 * (size_t)K; i < h.size(); ++i)
+        if (h[i] < 0.f) return set_err(ctx, SICP_EINVAL, "negative Adam second moment in the state");
     DeviceScope ds(ctx->device);
     const size_t b = sizeof(float) * 6 * (size_t)K;
     int rc;
@@ -1052,6 +1081,23 @@ int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8) {
     SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), ctx->stream));
     ctx->stats_on = enable != 0;
     return sync(ctx);
+}
+
+int sicp_set_wait_check(sicp_ctx* ctx, int on, int64_t polls) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (polls < 0 || polls > ((int64_t)1 << 30)) return set_err(ctx, SICP_EINVAL, "polls must lie in [0, 2^30]");
+    ctx->wait_never = on ? 1 : 0;
+    ctx->wait_polls = (long long)polls;
+    return SICP_OK;
+}
+
+int sicp_set_memory_limit(sicp_ctx* ctx, size_t bytes, size_t* held) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    ctx->mem_limit = bytes;
+    if (held) *held = ctx->mem_used;
+    return SICP_OK;
 }
 
 int sicp_profile(sicp_ctx* ctx, int stride, double* out4) {

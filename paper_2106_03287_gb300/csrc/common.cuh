@@ -242,6 +242,14 @@ struct sicp_ctx {
     sicp::Buf resume;                    // device staging of that state for sicp_resume
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
+    // failure-detection check (sicp_set_wait_check): when set, every bounded device wait of the
+    // context's kernels waits for an event that never comes, polling at most wait_polls times
+    // (0: each wait's default limit)
+    int wait_never = 0;
+    long long wait_polls = 0;
+    // device memory budget (sicp_set_memory_limit; 0: none) and the bytes the context holds in
+    // buffers that can grow (references, grids, run state, scratch)
+    size_t mem_limit = 0, mem_used = 0;
 };
 
 namespace sicp {
@@ -249,6 +257,9 @@ namespace sicp {
 int set_err(sicp_ctx* c, int code, const char* fmt, ...);
 int cuda_err(sicp_ctx* c, cudaError_t e, const char* what);
 int ensure(sicp_ctx* c, Buf& b, size_t bytes);
+// cudaMalloc of `bytes` counted against the context's budget (SICP_ENOMEM past it);
+// `held` bytes are freed by the caller first and no longer count
+int budget_malloc(sicp_ctx* c, void** p, size_t bytes, size_t held);
 
 #define SICP_CUDA(call)                                     \
     do {                                                    \
@@ -262,6 +273,8 @@ int ensure(sicp_ctx* c, Buf& b, size_t bytes);
 // points [n][3] -> float4 (w = index bits); flags[0] |= 1 on a non-finite value
 cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* flags, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, int64_t n, int* flags, cudaStream_t s);
+// flags[0] |= 1 on a non-finite or negative value (Adam second moments)
+cudaError_t launch_check_nonneg(const float* x, int64_t n, int* flags, cudaStream_t s);
 // flags[1] |= 1 if any index is outside [0, N)
 cudaError_t launch_check_index(const int32_t* idx, int64_t n, int64_t N, int* flags, cudaStream_t s);
 // gbar[j][c] = inv_m * sum over chunks of partial[chunk][j][c]
@@ -345,6 +358,10 @@ struct SteinArgs {
     unsigned* arrive;
     int* err;
     uint32_t gen;
+    // the arrival wait: at most max_spins polls (0: the default), for gen * P + extra arrivals
+    // (extra = 1 only in the failure-detection check, where the wait must give up)
+    long long max_spins;
+    uint32_t extra;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 // Independent runs (no Stein coupling): Adam on g = -G_j for every particle j,

@@ -232,23 +232,27 @@ struct BatchArgs {
     unsigned* bar;                       // arrival count, generation
     int* err;
     unsigned long long* stats;           // search work counters or null
+    long long max_spins;                 // polls of a barrier wait before it gives up (0: kMaxSpins)
+    unsigned extra;                      // arrivals a barrier waits for beyond the grid's CTAs (1 only in
+                                         // the failure-detection check, where every wait must give up)
 };
 
 // Grid-wide barrier with a bounded wait; false if any CTA gave up waiting.
-__device__ bool grid_barrier(unsigned* bar, int* err) {
+__device__ bool grid_barrier(unsigned* bar, int* err, long long max_spins, unsigned extra) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* gen = bar + 1;
         const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x + extra) {
             bar[0] = 0u;
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
+            const long long limit = max_spins > 0 ? max_spins : kMaxSpins;
             long long spins = 0;
             while (*gen == g) {
-                if (++spins > kMaxSpins || *(volatile int*)err) {
+                if (++spins > limit || *(volatile int*)err) {
                     atomicOr(err, 1);
                     break;
                 }
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
             if (b.stats) add_stats(b.stats, w);
             __syncwarp();
         }
-        if (!grid_barrier(b.bar, b.err)) return;
+        if (!grid_barrier(b.bar, b.err, b.max_spins, b.extra)) return;
         // Stein phase: whole problems per CTA
         for (int p = blockIdx.x; p < b.P; p += gridDim.x) {
             const int off = b.part_off[p];
@@ -330,10 +334,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
             a.out_phi = nullptr;
             a.out_h = nullptr;
             a.med_state = nullptr;
+            a.arrive = nullptr;
+            a.err = nullptr;
+            a.gen = 0;
+            a.max_spins = 0;
+            a.extra = 0;
             sd::stein_adam_block(a);
             __syncthreads();
         }
-        if (!grid_barrier(b.bar, b.err)) return;
+        if (!grid_barrier(b.bar, b.err, b.max_spins, b.extra)) return;
     }
 }
 
@@ -667,6 +676,8 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
         a.kappa[q] = p.prior_kappa[q];
     }
     a.bar = (unsigned*)B.bar.p;
+    a.max_spins = ctx->wait_polls;
+    a.extra = ctx->wait_never ? 1u : 0u;
     a.err = (int*)B.flags.p + 2;
     a.stats = ctx->stats_on ? (unsigned long long*)ctx->stats.p : nullptr;
 

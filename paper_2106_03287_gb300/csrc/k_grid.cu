@@ -264,14 +264,15 @@ unsigned blocks_for(int64_t n, int threads, int cap = 8192) {
 template <typename T>
 int grow(sicp_ctx* ctx, T*& p, size_t& cap, size_t n) {
     if (n <= cap && p) return SICP_OK;
+    const size_t held = sizeof(T) * cap;
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
     const size_t want = n + n / 4 + 16;
-    if (cudaMalloc(&p, sizeof(T) * want) != cudaSuccess) {
-        cudaGetLastError();
-        return set_err(ctx, SICP_ENOMEM, "grid allocation of %zu elements failed", want);
-    }
+    void* q = nullptr;
+    int rc = budget_malloc(ctx, &q, sizeof(T) * want, held);
+    if (rc) return rc;
+    p = (T*)q;
     cap = want;
     return SICP_OK;
 }

@@ -155,12 +155,14 @@ struct BfArgs {
     int* err;
     const float4* normals;     // grad = 1, point-to-plane: unit normals by original index; null: point-to-point
     int64_t mb_stride;         // grad = 1: minibatch entries between particles' rows (0: one shared row)
+    long long polls;           // polls of an mbarrier wait before it gives up (0: kPolls)
+    int never;                 // failure-detection check: first wait on an mbarrier nothing arrives on
 };
 
 // Wait for phase `parity` of the mbarrier; false (and the error flag set)
-// after kPolls polls.
-__device__ __forceinline__ bool bwait(uint64_t* mb, uint32_t parity, int* err) {
-    if (tc::mbar_wait(mb, parity, kPolls)) return true;
+// after `polls` polls (0: kPolls).
+__device__ __forceinline__ bool bwait(uint64_t* mb, uint32_t parity, int* err, long long polls) {
+    if (tc::mbar_wait(mb, parity, polls > 0 ? polls : kPolls)) return true;
     atomicOr(err, 1);
     return false;
 }
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         a.sorted = r->grid.sorted;
     }
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t tfull[2];
+    __shared__ uint64_t tfull[2], tnever;
     __shared__ uint32_t tbase;
     __shared__ int s_fail, s_rot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
@@ -242,12 +244,21 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     if (tid == 0) {
         tc::mbar_init(&tfull[0], 1);
         tc::mbar_init(&tfull[1], 1);
+        tc::mbar_init(&tnever, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    // Failure-detection check: a wait on an mbarrier that nothing arrives on, before any copy or
+    // MMA is issued.  It gives up after a.polls polls, sets the error flag, and the CTA then skips
+    // all work (nothing in flight), frees its tensor memory and returns.
+    if (a.never) {
+        if (tid == 0 && !bwait(&tnever, 0u, a.err, a.polls)) s_fail = 1;
+        __syncthreads();
+    }
+    const bool skip = s_fail != 0;
     const uint32_t tmem = tbase;
     const uint32_t idesc = tc::idesc_bf16(kQRows, kRCols);
     const uint64_t adesc = tc::smem_desc(tc::smem_u32(sm + sA), 128, kKDim * 16, false);
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         }
     };
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < ntiles && !skip; tile += gridDim.x) {
         // ---- A operand and the fp32 queries of this tile.  In a registration
         // iteration the rows go minibatch-major (the K particles' images of one
         // source point are neighbours), which keeps a tile's queries close.
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             const int64_t N = N0 + t;
             const int b = (int)(N & 1);
             int ok = 1;
-            if (lane == 0) ok = s_fail ? 0 : bwait(&tfull[b], (uint32_t)((N >> 1) & 1), a.err);
+            if (lane == 0) ok = s_fail ? 0 : bwait(&tfull[b], (uint32_t)((N >> 1) & 1), a.err, a.polls);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             tc::fence_after_sync();
             if (!ok) {
@@ -495,6 +506,8 @@ static BfArgs bf_args(sicp_ctx* ctx, int* err) {
     BfArgs a{};
     a.ref = (const BfRef*)ctx->bf16_ref.p;   // the kernel fills the reference fields from it
     a.err = err;
+    a.polls = ctx->wait_polls;
+    a.never = ctx->wait_never;
     return a;
 }
 

@@ -34,7 +34,8 @@ struct NaArgs {
     const float* ref;       // M x 3
     int M;
     const float* src;       // N x 3
-    const int32_t* mb;      // m
+    int64_t N;
+    const int32_t* mb;      // m (an entry outside [0, N) contributes nothing)
     int m;
     const float* theta;     // K x 6
     int K;
@@ -77,12 +78,10 @@ __global__ void __launch_bounds__(kNaMaxThreads) k_grad_brute_noalloc(NaArgs a) 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (threadIdx.x == 0) make_pose(a.theta + 6 * j, P);
     __syncthreads();
-    const bool valid = k < a.m;
+    const int i = k < a.m ? a.mb[k] : -1;
+    const bool valid = i >= 0 && (int64_t)i < a.N;   // an index outside the source reads nothing
     float3 s = make_float3(0.f, 0.f, 0.f);
-    if (valid) {
-        const int i = a.mb[k];
-        s = make_float3(a.src[3 * (int64_t)i], a.src[3 * (int64_t)i + 1], a.src[3 * (int64_t)i + 2]);
-    }
+    if (valid) s = make_float3(a.src[3 * (int64_t)i], a.src[3 * (int64_t)i + 1], a.src[3 * (int64_t)i + 2]);
     const float3 q = apply_pose(P, s);
     float best = FLT_MAX;
     int bi = 0x7fffffff;
@@ -158,6 +157,7 @@ extern "C" int sicp_icp_grad_noalloc(const float* ref_xyz, int64_t M, const floa
     a.ref = ref_xyz;
     a.M = (int)M;
     a.src = src_xyz;
+    a.N = N;
     a.mb = mb;
     a.m = m;
     a.theta = particles;

@@ -27,6 +27,14 @@ __global__ void k_check_finite(const float* __restrict__ x, int64_t n, int* __re
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
 }
 
+// flags[0] |= 1 on a value that is non-finite or negative
+__global__ void k_check_nonneg(const float* __restrict__ x, int64_t n, int* __restrict__ flags) {
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !(isfinite(x[i]) && x[i] >= 0.f);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+}
+
 __global__ void k_check_index(const int32_t* __restrict__ idx, int64_t n, int64_t N, int* __restrict__ flags) {
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -196,6 +204,11 @@ cudaError_t launch_pack_points(const float* xyz, int64_t n, float4* out, int* fl
 
 cudaError_t launch_check_finite(const float* x, int64_t n, int* flags, cudaStream_t s) {
     k_check_finite<<<grid_1d(n, 256), 256, 0, s>>>(x, n, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_nonneg(const float* x, int64_t n, int* flags, cudaStream_t s) {
+    k_check_nonneg<<<grid_1d(n, 256), 256, 0, s>>>(x, n, flags);
     return cudaGetLastError();
 }
 

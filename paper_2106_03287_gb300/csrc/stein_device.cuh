@@ -556,13 +556,15 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     if (P > 1) {
         // every CTA of the block has read theta (and the previous median) once all have arrived
         if (tid == 0) {
-            const unsigned target = a.gen * (unsigned)P;
+            const unsigned target = a.gen * (unsigned)P + a.extra;
+            const long long limit = a.max_spins > 0 ? a.max_spins : kArriveSpins;
             long long spins = 0;
             for (;;) {
                 unsigned now;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(a.arrive + b) : "memory");
                 if ((int)(now - target) >= 0) break;
-                if (++spins > kArriveSpins) {
+                // give up after the limit, or at once when another wait of this call already gave up
+                if (++spins > limit || *(volatile int*)a.err) {
                     s_fail = 1;
                     atomicExch(a.err, 1);
                     break;

@@ -283,24 +283,6 @@ def test_teacher_forced_kinect_grid(ctx):
     assert wp <= 1e-4
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_free_run_box_against_oracle(ctx, mode):
-    d = synth.make_box_problem(0)
-    S.sicp_set_reference(ctx, d["ref"])
-    p = S.sicp_default_params(T=100, m=100, lr=0.01, seed=7, nn_mode=mode)
-    th, mean, cov = S.sicp_register(ctx, d["src"], d["particles"], p)
-    th_o, mean_o, cov_o = O.register(d["ref"], d["src"], d["particles"],
-                                     O.Params(T=100, m=100, lr=float(np.float32(0.01)), seed=7))
-    dm = np.abs(mean - mean_o)
-    rel = np.abs(th - th_o).max() / np.abs(th_o).max()
-    print(f"box free run mode={mode}: particle rel err {rel:.2e}, mean err t {dm[:3].max():.2e} m, "
-          f"r {math.degrees(dm[3:].max()):.2e} deg")
-    # the moments the library returns are those of the particles it returns
-    mo, co = O.moments(th.astype(np.float64))
-    assert np.allclose(mean, mo, atol=1e-12) and np.allclose(cov, co, atol=1e-12)
-    assert np.all(np.isfinite(th))
-
-
 def test_register_special_cases_and_residency(ctx):
     d = synth.make_box_problem(5, K=8)
     S.sicp_set_reference(ctx, d["ref"])
