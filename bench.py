@@ -209,7 +209,7 @@ def ncu_traffic_per_query():
     return rec["dram_bytes"] / rec["queries"]
 
 
-def cpu_baseline(d, cfg, budget_s=15.0, metric="point", single_budget_s=6.0):
+def cpu_baseline(d, cfg, budget_s=10.0, metric="point", single_budget_s=5.0):
     """The oracle as it stands, on a bounded number of iterations of the same workload
     (point-to-plane: the reference normals are computed before the timed sample)."""
     import oracle as O
@@ -217,7 +217,10 @@ def cpu_baseline(d, cfg, budget_s=15.0, metric="point", single_budget_s=6.0):
     th = d["particles"].astype(np.float64).copy()
     mom, vel = np.zeros_like(th), np.zeros_like(th)
     normals = O.normals(ref, NORMAL_K)[0] if metric == "plane" else None
-    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals)
+    t0 = time.perf_counter()
+    tree = O.KDTree(ref)
+    build_s = time.perf_counter() - t0
+    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals, tree=tree)
     K = th.shape[0]
     t0 = time.perf_counter()
     O.step(ref, src, th, mom, vel, p, 0)
@@ -230,8 +233,8 @@ def cpu_baseline(d, cfg, budget_s=15.0, metric="point", single_budget_s=6.0):
     cores = O.num_threads()
     out = {"value": K * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": cores,
            "kind": "oracle",
-           "sample": f"{n} SVGD iterations (iterations 1..{n}) of the same workload, exhaustive FP64 search, "
-                     f"{dt:.1f} s", "iters_per_sec": n / dt}
+           "sample": f"{n} SVGD iterations (iterations 1..{n}) of the same workload, FP64, exact k-d tree search "
+                     f"(tree built once in {build_s * 1e3:.0f} ms, not timed), {dt:.1f} s", "iters_per_sec": n / dt}
     # the same oracle on one thread, for the next few iterations (a shorter bounded sample)
     n1 = min(cfg["T"] - 1 - n, max(1, int(single_budget_s * n / max(dt, 1e-6) / max(cores, 1))))
     if n1 >= 1:
@@ -280,10 +283,11 @@ def run_reference(args):
         d = d[0]              # the oracle takes the batch's first problem (its runs are independent)
     import oracle as O
     ref, src = d["ref"], d["src"]
-    parts = d["particles"][:8] if args.workload == "mc" else d["particles"]   # mc: 8 of the independent runs
+    parts = d["particles"][:100] if args.workload == "mc" else d["particles"]   # mc: 100 of the independent runs
     K = parts.shape[0]
     normals = O.normals(ref, NORMAL_K)[0] if args.metric == "plane" else None
-    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals, independent=args.workload == "mc")
+    p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals, independent=args.workload == "mc",
+                 tree=O.KDTree(ref))
     th = parts.astype(np.float64).copy()
     mom, vel = np.zeros_like(th), np.zeros_like(th)
     t0 = time.perf_counter()
@@ -306,12 +310,12 @@ def run_reference(args):
     value = K * cfg["m"] * per_step / (ms / 1e3)
     sample = (f"{per_step} SVGD iterations per step of the {args.workload} workload"
               + (" (problem 0 of the batch)" if args.workload == "batched" else "")
-              + (" (8 of the independent runs)" if args.workload == "mc" else "") + ", exhaustive FP64 search")
+              + (" (100 of the independent runs)" if args.workload == "mc" else "") + ", FP64, exact k-d tree search")
     line = {"impl": "reference", "metric": "particle_point_evals_per_sec", "value": value,
             "unit": "particle_point_evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, d, cfg, "exhaustive", args.metric),
+            "config": workload_config(args.workload, d, cfg, "exact k-d tree (FP64)", args.metric),
             "iters_per_sec": per_step / (ms / 1e3),
             "cpu_baseline": {"value": value, "unit": "particle_point_evals/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
@@ -388,6 +392,7 @@ def run_ours(args):
     queries = max(st[0], 1.0)   # grid-search counters (zero in the exhaustive modes)
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
     coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
+    queued_frac = st[10] / queries   # grid gradient queries the neighbourhood lists did not settle
     bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q + (16 if plane else 0)   # + the normal
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -429,19 +434,26 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
                     "launches_timed": int(prof[1]),
                     "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
-                                  "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
+                                  "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac,
+                                  "queued_for_warp_search_frac": queued_frac},
                     "stein_adam_avg_launch_us": stein_us}
     elif nn == "bf16":
         peak, peak_kind = measured_peak("bf16_tflops")
-        cols = 256 * ((M + 255) // 256)
-        mma_flops = 2.0 * 16 * queries_per_launch * cols    # executed: K = 16 slots, padded columns
-        achieved = mma_flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None
+        R = (M + 255) // 256
+        qtiles, rtiles = float(st[8]), float(st[9])   # query tiles and reference tiles swept over the step
+        swept = rtiles / qtiles if qtiles else float(R)
+        # executed: 128 x 256 x 16 MMAs over the reference tiles the query tiles swept
+        mma_flops = 2.0 * 16 * 128 * 256 * (rtiles / cfg["T"]) if qtiles else 2.0 * 16 * queries_per_launch * 256 * R
+        alg_flops = 2.0 * 4 * queries_per_launch * M
+        achieved = alg_flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None
         roofline = {"kernel": "k_nn_bf16 (transform + tensor-core distance tiles + fp32 re-check + gradient terms) "
                               "and the per-particle reduction, one iteration", "bound": "tensor",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_kind": f"{peak_kind} dense bf16 (burst)",
                     "frac": achieved / peak if achieved else None, "traffic": None,
-                    "mma_flops_per_launch": mma_flops,
-                    "algorithmic_flops_per_launch": 2.0 * 4 * queries_per_launch * M,
+                    "algorithmic_flops_per_launch": alg_flops,
+                    "executed_mma_flops_per_launch": mma_flops,
+                    "executed_tflops": mma_flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None,
+                    "reference_tiles": R, "reference_tiles_swept_per_query_tile": swept,
                     "avg_launch_us": grad_ms * 1e3 if grad_ms else None, "launches_timed": int(prof[1]),
                     "stein_adam_avg_launch_us": stein_us}
     elif nn == "fp32":
@@ -818,10 +830,10 @@ def run_ours_mc(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
-        sub = 8   # a bounded sample: 8 of the runs, a few iterations
+        sub = 100   # a bounded sample: 100 of the runs, as many iterations as fit in about 10 s
         th = d["particles"][:sub].astype(np.float64).copy()
         mom, vel = np.zeros_like(th), np.zeros_like(th)
-        po = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, independent=True)
+        po = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, independent=True, tree=O.KDTree(d["ref"]))
         t0 = time.perf_counter()
         n = 0
         while time.perf_counter() - t0 < 10.0 and n < cfg["T"]:
@@ -829,7 +841,7 @@ def run_ours_mc(args):
             n += 1
         dt = time.perf_counter() - t0
         cpu = {"value": sub * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": O.num_threads(),
-               "kind": "oracle", "sample": f"{sub} of the {R} runs, {n} iterations, exhaustive FP64 search, {dt:.1f} s"}
+               "kind": "oracle", "sample": f"{sub} of the {R} runs, {n} iterations, FP64, exact k-d tree search, {dt:.1f} s"}
     S.sicp_destroy(ctx)
     if rank == 0:
         line = {"metric": "particle_point_evals_per_sec", "value": job_value(evals, world, ms_max),

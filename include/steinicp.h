@@ -36,8 +36,10 @@
  *  - Environment (for diagnosis; results do not change):
  *    SICP_NO_GRAPH runs the registration loop as plain launches instead of a
  *    captured CUDA graph; SICP_NO_PDL launches its kernels in plain stream
- *    order instead of with programmatic dependent launch (read once per
- *    process).
+ *    order instead of with programmatic dependent launch;
+ *    SICP_GRID_WARP_SEARCH makes the grid search's gradient kernel search
+ *    every query with a whole warp instead of one lane per query over the
+ *    cells' neighbourhood lists (read once per process).
  */
 #ifndef STEINICP_H
 #define STEINICP_H
@@ -218,6 +220,22 @@ int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, cons
                           const float* particles_in, const sicp_params* p, int32_t trial_iters,
                           const char* cache_path, float* out_cell_factor, int32_t* out_points_per_item,
                           int on_device);
+
+/* Trace of one iteration of a batched run, for checking the persistent
+ * kernel step by step against a plain implementation (no counterpart in the
+ * paper).  sicp_trace_batched(ctx, t) arms the next sicp_register_batched
+ * call on this context to record iteration t (0-based; t < 0 disarms; the
+ * arming lasts one run): the particles and Adam moments the iteration starts
+ * from, its correspondences, and the mean gradients and Stein directions of
+ * its update.  sicp_read_batched_trace copies them to host arrays, all
+ * problems' particles back to back as in particles_in: theta, adam_m,
+ * adam_v, gbar, phi [sum K][6] float32 and nn [sum K][m] int32 (reference
+ * indices within the problem, -1 for none); any may be NULL.  Errors:
+ * SICP_EINVAL (no trace recorded since the last arming: the run failed, had
+ * T <= t, or was an autotuning trial), SICP_ECUDA. */
+int sicp_trace_batched(sicp_ctx* ctx, int32_t t);
+int sicp_read_batched_trace(sicp_ctx* ctx, float* theta, float* adam_m, float* adam_v, int32_t* nn, float* gbar,
+                            float* phi);
 
 /* ---- single steps of the iteration, for users who drive the loop ---- */
 
@@ -446,16 +464,21 @@ int sicp_surrogate_infer(sicp_ctx* ctx, const float* q, int64_t n, float* out_di
 
 /* ---- measurement ---- */
 
-/* Work counters of the grid search (no counterpart in the paper; they state
+/* Work counters of the searches (no counterpart in the paper; they state
  * the algorithmic bytes a search moved).  Copies the counters accumulated
- * since the previous call into out8 (may be NULL): queries, rows examined
- * (one row span each), row segments read (two cell offsets each), candidate
- * points read (16 bytes each), queries that went on to the coarse level,
- * queries that went on to the exhaustive scan, queries put to the surrogate,
- * surrogate queries sent on to the exact search; then zeroes them and turns
- * counting on (enable = 1) or off.  Counting adds six warp-aggregated atomics
- * per 32 lanes. */
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out8);
+ * since the previous call into out11 (may be NULL): grid search queries, rows
+ * examined (one row span each), row segments read (two cell offsets each; a
+ * query's neighbourhood list counts as one), candidate points read (16 bytes
+ * each), queries that went on to the coarse level, queries that went on to
+ * the exhaustive scan, queries put to the surrogate, surrogate queries sent
+ * on to the exact search, query tiles of the tensor-core search (128 queries
+ * each), reference tiles those query tiles swept (256 points each; the
+ * others were ruled out by their bounding boxes), queries of the grid
+ * gradient kernel that its neighbourhood lists could not settle (searched
+ * again by a whole warp); then zeroes them and turns counting on
+ * (enable = 1) or off.  Counting adds a few warp-aggregated atomics per 32
+ * lanes. */
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out11);
 
 /* Kernel timing inside sicp_register (no counterpart in the paper).  With
  * stride s > 0 the captured loop records CUDA events around the gradient and

@@ -46,6 +46,7 @@ EXPORTS = (
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
     "sicp_export_state", "sicp_import_state", "sicp_resume", "sicp_set_memory_limit", "sicp_set_wait_check",
+    "sicp_trace_batched", "sicp_read_batched_trace",
 )
 
 SURROGATE_NPARAM = 33040
@@ -116,6 +117,8 @@ def lib() -> ctypes.CDLL:
             "sicp_compound": (ctypes.c_int, [P, P, P, P, I32, P, P]),
             "sicp_set_memory_limit": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "sicp_set_wait_check": (ctypes.c_int, [P, ctypes.c_int, I64]),
+            "sicp_trace_batched": (ctypes.c_int, [P, I32]),
+            "sicp_read_batched_trace": (ctypes.c_int, [P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -449,9 +452,11 @@ def sicp_moments_circular(ctx, particles):
 def sicp_stats(ctx, enable: bool = True):
     """Search counters since the last call (queries, rows, segments, points,
     coarse-level queries, exhaustive-scan queries, surrogate queries,
-    surrogate queries sent to the exact search) as a uint64 array; then
-    resets them and sets counting on/off."""
-    out = np.zeros(8, np.uint64)
+    surrogate queries sent to the exact search, tensor-core query tiles,
+    reference tiles they swept, grid gradient queries the neighbourhood lists
+    could not settle) as a uint64 array; then resets them and sets counting
+    on/off."""
+    out = np.zeros(11, np.uint64)
     _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
@@ -600,6 +605,21 @@ def sicp_register_batched(ctx, problems, params: sicp_params):
                                             _ptr(mean, np.float64), _ptr(cov, np.float64), dev))
     parts = [out[part_off[i]:part_off[i + 1]] for i in range(P)]
     return parts, mean, cov
+
+
+def sicp_trace_batched(ctx, t: int):
+    """Record iteration t of the next sicp_register_batched call (t < 0: none)."""
+    _check(ctx, lib().sicp_trace_batched(ctx, int(t)))
+
+
+def sicp_read_batched_trace(ctx, Ktot: int, m: int):
+    """The recorded iteration: dict of theta, adam_m, adam_v, gbar, phi [sum K][6] and nn [sum K][m]."""
+    out = {k: np.empty((Ktot, 6), np.float32) for k in ("theta", "adam_m", "adam_v", "gbar", "phi")}
+    out["nn"] = np.empty((Ktot, m), np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(ctx, lib().sicp_read_batched_trace(ctx, ptr(out["theta"]), ptr(out["adam_m"]), ptr(out["adam_v"]),
+                                              ptr(out["nn"]), ptr(out["gbar"]), ptr(out["phi"])))
+    return out
 
 
 def sicp_autotune_batched(ctx, problems, params: sicp_params, trial_iters: int = 5, cache_path=None):

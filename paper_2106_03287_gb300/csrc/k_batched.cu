@@ -232,6 +232,11 @@ struct BatchArgs {
     unsigned* bar;                       // arrival count, generation
     int* err;
     unsigned long long* stats;           // search work counters or null
+    // trace of iteration trace_t (-1: none): the particles and Adam moments it starts from
+    // [sum K][6], its correspondences [sum K][m] and mean gradients and Stein directions [sum K][6]
+    int trace_t;
+    float *tr_theta, *tr_am, *tr_av, *tr_gbar, *tr_phi;
+    int32_t* tr_nn;
     long long max_spins;                 // polls of a barrier wait before it gives up (0: kMaxSpins)
     unsigned extra;                      // arrivals a barrier waits for beyond the grid's CTAs (1 only in
                                          // the failure-detection check, where every wait must give up)
@@ -270,6 +275,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t W = (int64_t)gridDim.x * (kPersistThreads / 32);
     for (int t = 0; t < b.T; ++t) {
+        const bool tr = t == b.trace_t;
+        if (tr) {   // the state this iteration starts from (theta changes only after the barrier)
+            const int64_t n = 6 * (int64_t)b.part_off[b.P];
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+                b.tr_theta[i] = b.theta[i];
+                b.tr_am[i] = b.am[i];
+                b.tr_av[i] = b.av[i];
+            }
+        }
         // gradient phase: one warp per item, items interleaved over the whole grid
         for (int64_t it = (int64_t)blockIdx.x * (kPersistThreads / 32) + warp; it < b.total_items; it += W) {
             const int p = find_problem(b.item_off, b.P, it);
@@ -292,6 +306,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
                 const float3 q = apply_pose(P[warp], s);
                 Best B;
                 grid_search(S, q, B, w);
+                if (tr && lane == 0) b.tr_nn[(int64_t)jg * b.m + k] = B.i != kNone ? B.i : -1;
                 if (lane == 0 && B.i != kNone) {
                     float tt[6];
                     grad_terms(P[warp], s, make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z), tt);
@@ -331,7 +346,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
                 a.sigma[q] = b.sigma[q];
                 a.kappa[q] = b.kappa[q];
             }
-            a.out_phi = nullptr;
+            a.out_phi = tr ? b.tr_phi + 6 * off : nullptr;
+            a.out_gbar = tr ? b.tr_gbar + 6 * off : nullptr;
             a.out_h = nullptr;
             a.med_state = nullptr;
             a.arrive = nullptr;
@@ -408,10 +424,16 @@ struct BatchState {
     int kkc = 4;
     int grid_ctas = 0;
     size_t smem = 0;
+    // trace of one iteration (sicp_trace_batched): armed iteration, and what the last run recorded
+    int trace_t = -1;
+    bool trace_ready = false;
+    int64_t trace_K = 0;
+    int trace_m = 0;
+    Buf tr;
     ~BatchState() {
         if (exec) cudaGraphExecDestroy(exec);
         Buf* bs[] = {&ref4, &src4, &mb, &theta, &am, &av, &partial, &moments, &stage, &flags, &bar,
-                     &ref_off, &src_off, &part_off, &item_off, &lohi, &searches};
+                     &ref_off, &src_off, &part_off, &item_off, &lohi, &searches, &tr};
         for (Buf* x : bs)
             if (x->p) cudaFree(x->p);
         for (Level& L : lv) {
@@ -676,6 +698,21 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
         a.kappa[q] = p.prior_kappa[q];
     }
     a.bar = (unsigned*)B.bar.p;
+    a.trace_t = -1;
+    const bool tracing = B.trace_t >= 0 && B.trace_t < p.T && !elapsed_ms;
+    if (tracing) {
+        const size_t st = sizeof(float) * 6 * (size_t)Ktot;
+        if ((rc = ensure(ctx, B.tr, 5 * st + sizeof(int32_t) * (size_t)Ktot * p.m))) return rc;
+        char* t0 = (char*)B.tr.p;
+        a.trace_t = B.trace_t;
+        a.tr_theta = (float*)t0;
+        a.tr_am = (float*)(t0 + st);
+        a.tr_av = (float*)(t0 + 2 * st);
+        a.tr_gbar = (float*)(t0 + 3 * st);
+        a.tr_phi = (float*)(t0 + 4 * st);
+        a.tr_nn = (int32_t*)(t0 + 5 * st);
+    }
+    B.trace_ready = false;
     a.max_spins = ctx->wait_polls;
     a.extra = ctx->wait_never ? 1u : 0u;
     a.err = (int*)B.flags.p + 2;
@@ -769,6 +806,12 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
     SICP_CUDA(cudaStreamSynchronize(s));
     B.grid_ctas = ctas;
     B.smem = smem;
+    if (tracing) {
+        B.trace_ready = true;
+        B.trace_K = Ktot;
+        B.trace_m = p.m;
+        B.trace_t = -1;   // one run per arming
+    }
     return SICP_OK;
 }
 
@@ -926,5 +969,33 @@ extern "C" int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* re
     B.graph_valid = false;
     if (out_cell_factor) *out_cell_factor = B.cell_factor;
     if (out_points_per_item) *out_points_per_item = B.kkc;
+    return SICP_OK;
+}
+
+extern "C" int sicp_trace_batched(sicp_ctx* ctx, int32_t t) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch) ctx->batch = new BatchState();
+    ctx->batch->trace_t = t < 0 ? -1 : t;
+    return SICP_OK;
+}
+
+extern "C" int sicp_read_batched_trace(sicp_ctx* ctx, float* theta, float* adam_m, float* adam_v, int32_t* nn,
+                                       float* gbar, float* phi) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch || !ctx->batch->trace_ready)
+        return set_err(ctx, SICP_EINVAL, "no batched trace recorded since sicp_trace_batched");
+    BatchState& B = *ctx->batch;
+    DeviceScopeB ds(ctx->device);
+    const size_t st = sizeof(float) * 6 * (size_t)B.trace_K;
+    const char* t0 = (const char*)B.tr.p;
+    float* outs[5] = {theta, adam_m, adam_v, gbar, phi};
+    for (int i = 0; i < 5; ++i)
+        if (outs[i]) SICP_CUDA(cudaMemcpyAsync(outs[i], t0 + i * st, st, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nn)
+        SICP_CUDA(cudaMemcpyAsync(nn, t0 + 5 * st, sizeof(int32_t) * (size_t)B.trace_K * B.trace_m,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SICP_CUDA(cudaStreamSynchronize(ctx->stream));
     return SICP_OK;
 }

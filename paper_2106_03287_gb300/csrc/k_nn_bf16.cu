@@ -28,6 +28,16 @@
 // (points within a few bound widths of the best so far) are rare once u has
 // come down.
 //
+// Tiles that cannot hold an answer are skipped.  Before its sweep a query tile
+// takes, for every query, the fp32 squared distance U_q to the seed point of
+// its grid cell (a reference point near the cell centre): the query's answer
+// is at most that far.  A reference tile whose bounding box lies farther from
+// the query tile's bounding box than max_q U_q, with margins for fp32
+// rounding, holds no point that can be the answer or tie with it, and is
+// left out of the sweep with its MMA and its accumulator readback.  The kept
+// tiles (all of them when R exceeds the list's capacity) are swept in the
+// same order as before.
+//
 // Pipeline per CTA (one 128-query tile at a time, persistent over tiles, one
 // CTA per SM; the sweep starts at the reference tile holding the grid cell of
 // the tile's first query and wraps around): the 16 warps copy each reference tile (8 KB, precomputed per
@@ -71,7 +81,11 @@ constexpr int sQ = sRing + kSlots * kSlotBytes;       // float4 per row
 constexpr int sXD = sQ + kQRows * 16;                 // quarters 1..3: best distance, index, point
 constexpr int sXI = sXD + 3 * kQRows * 4;
 constexpr int sXP = sXI + 3 * kQRows * 4;
-constexpr int kBfSmemUsed = sXP + 3 * kQRows * 16;
+constexpr int kMaxList = 8192;                        // reference tiles a sweep list holds (2M points)
+constexpr int sList = sXP + 3 * kQRows * 16;          // uint16 [kMaxList]: the kept tiles in sweep order
+constexpr int kBfSmemUsed = sList + kMaxList * 2;
+constexpr float kBoxRel = 1e-6f;                      // box gaps shrink by this x the coordinate magnitudes
+constexpr float kSkipRel = 1e-5f;                     // a tile is skipped only if its bound beats U by this
 // Launched with more shared memory than it uses so that no two CTAs share an
 // SM: each holds all 512 tensor-memory columns for its whole life.
 constexpr int kBfSmem = 120 * 1024;
@@ -122,6 +136,38 @@ __global__ void k_bf16_btiles(const float4* __restrict__ sorted, int M, float3 c
     store_row16(out + (size_t)tile * kTileBytes, row, v);
 }
 
+// Bounding box of each reference tile's points (tbox[2 t] = lo, tbox[2 t + 1] =
+// hi) and the largest coordinate magnitude of the cloud (amax, zeroed
+// beforehand); one warp per tile.
+__global__ void k_bf16_tbox(const float4* __restrict__ sorted, int M, int R, float4* __restrict__ tbox,
+                            unsigned* __restrict__ amax) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= R) return;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int k = lane; k < kRCols; k += 32) {
+        const int64_t i = (int64_t)warp * kRCols + k;
+        if (i < M) {
+            const float4 r = sorted[i];
+            lo[0] = fminf(lo[0], r.x); lo[1] = fminf(lo[1], r.y); lo[2] = fminf(lo[2], r.z);
+            hi[0] = fmaxf(hi[0], r.x); hi[1] = fmaxf(hi[1], r.y); hi[2] = fmaxf(hi[2], r.z);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    }
+    if (lane == 0) {
+        tbox[2 * warp] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        tbox[2 * warp + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        const float m = fmaxf(fmaxf(fmaxf(fabsf(lo[0]), fabsf(lo[1])), fmaxf(fabsf(lo[2]), fabsf(hi[0]))),
+                              fmaxf(fabsf(hi[1]), fabsf(hi[2])));
+        atomicMax(amax, __float_as_uint(m));
+    }
+}
+
 // What the search reads of the current reference, kept in device memory and
 // rewritten by every tile build (bf16_prepare), so a captured graph of the
 // search stays valid when the reference changes.
@@ -131,6 +177,8 @@ struct BfRef {
     const unsigned char* btiles;
     const float* nmax;         // [R]
     GridView grid;             // the fine grid: where each cell's points start in `sorted`
+    const float4* tbox;        // [R][2]: each tile's bounding box (lo, hi)
+    const float* amax;         // largest coordinate magnitude of the cloud
 };
 
 struct BfArgs {
@@ -148,6 +196,8 @@ struct BfArgs {
     const float* nmax;         // [R]
     const float4* sorted;
     GridView grid;             // the fine grid: where each cell's points start in `sorted`
+    const float4* tbox;
+    float amax;
     int M, R;
     int32_t* out_idx;          // grad = 0: [n]; grad = 1: [K][m] or null
     float* out_d2;             // grad = 0
@@ -155,6 +205,7 @@ struct BfArgs {
     int* err;
     const float4* normals;     // grad = 1, point-to-plane: unit normals by original index; null: point-to-point
     int64_t mb_stride;         // grad = 1: minibatch entries between particles' rows (0: one shared row)
+    unsigned long long* stats; // work counters or null: [8] query tiles, [9] reference tiles swept
     long long polls;           // polls of an mbarrier wait before it gives up (0: kPolls)
     int never;                 // failure-detection check: first wait on an mbarrier nothing arrives on
 };
@@ -226,16 +277,21 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         a.nmax = r->nmax;
         a.grid = r->grid;
         a.sorted = r->grid.sorted;
+        a.tbox = r->tbox;
+        a.amax = *r->amax;
     }
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t tfull[2], tnever;
     __shared__ uint32_t tbase;
-    __shared__ int s_fail, s_rot;
+    __shared__ int s_fail, s_rot, s_T;
+    __shared__ float s_red[4][8];
+    __shared__ int s_cnt[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const int64_t Q = a.grad ? (int64_t)a.K * a.m : a.n;
     const int64_t ntiles = (Q + kQRows - 1) / kQRows;
-    const int T = a.R;
     float4* qrow = reinterpret_cast<float4*>(sm + sQ);
+    uint16_t* list = reinterpret_cast<uint16_t*>(sm + sList);
+    const bool use_list = a.R <= kMaxList;
     float* xd = reinterpret_cast<float*>(sm + sXD);
     unsigned* xi = reinterpret_cast<unsigned*>(sm + sXI);
     float4* xp = reinterpret_cast<float4*>(sm + sXP);
@@ -262,15 +318,17 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     const uint32_t tmem = tbase;
     const uint32_t idesc = tc::idesc_bf16(kQRows, kRCols);
     const uint64_t adesc = tc::smem_desc(tc::smem_u32(sm + sA), 128, kKDim * 16, false);
-    int rot = 0;
+    int rot = 0, T = a.R;
     const int qtr = warp >> 2, rq = warp & 3, row = 32 * rq + lane;
     int64_t N0 = 0;   // MMAs issued by this CTA before the current query tile
+    // reference tile swept at step t of the current query tile
+    auto tile_at = [&](int t) -> int { return use_list ? (int)list[t] : ref_tile(t, a.R, rot); };
 
     // asynchronous copy (no registers) of this thread's 16 bytes of tile t
     // and of its points; one commit group per tile
     auto fetch = [&](int t) {
         if (t < T) {
-            const int rt = ref_tile(t, a.R, rot);
+            const int rt = tile_at(t);
             unsigned char* slot = sm + sRing + (t % kSlots) * kSlotBytes;
             cp_async16(slot + 16 * tid, a.btiles + (size_t)rt * kTileBytes + 16 * tid);
             if (tid < kRCols && rt * kRCols + tid < a.M)
@@ -314,6 +372,28 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             const float p[3] = {q.x - a.c.x, q.y - a.c.y, q.z - a.c.z};
             const float n2 = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
             qrow[tid] = make_float4(q.x, q.y, q.z, sqrtf(n2));
+            if (use_list) {
+                // U_q: the fp32 squared distance to the seed point of the query's grid cell (an
+                // actual reference point, so the answer is at most that far); the query tile's
+                // box; padding rows (g >= Q) take no part
+                const GridView& G = a.grid;
+                float U = g < Q ? FLT_MAX : 0.f;
+                if (g < Q && G.seed4) {
+                    const int cx = cell_coord(q.x, G.origin.x, G.inv_cell, G.dims.x);
+                    const int cy = cell_coord(q.y, G.origin.y, G.inv_cell, G.dims.y);
+                    const int cz = cell_coord(q.z, G.origin.z, G.inv_cell, G.dims.z);
+                    const float4 sp = __ldg(G.seed4 + ((int64_t)cz * G.dims.y + cy) * G.dims.x + cx);
+                    if (__float_as_int(sp.w) >= 0) U = dist2(sp, q);
+                }
+                float v[8] = {U, g < Q ? -q.x : -FLT_MAX, g < Q ? -q.y : -FLT_MAX, g < Q ? -q.z : -FLT_MAX,
+                              g < Q ? q.x : -FLT_MAX, g < Q ? q.y : -FLT_MAX, g < Q ? q.z : -FLT_MAX,
+                              g < Q ? fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z)) : 0.f};
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    for (int off = 16; off > 0; off >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], off));
+                if (lane == 0)
+                    for (int k = 0; k < 8; ++k) s_red[warp][k] = v[k];
+            }
             __nv_bfloat16 v[16];
             const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
             for (int k = 0; k < 16; ++k) v[k] = z;
@@ -339,6 +419,59 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         }
         __syncthreads();
         rot = s_rot;
+        if (use_list) {
+            // the query tile's bound and box (max over the four row warps)
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = fmaxf(fmaxf(s_red[0][k], s_red[1][k]), fmaxf(s_red[2][k], s_red[3][k]));
+            const float U = v[0];
+            const float qlo[3] = {-v[1], -v[2], -v[3]}, qhi[3] = {v[4], v[5], v[6]};
+            const float tol = kBoxRel * (v[7] + a.amax);   // covers the fp32 rounding of the box gaps
+            // this thread's run of tiles in sweep order: keep those whose box can hold an answer
+            const int per = (a.R + kBfThreads - 1) / kBfThreads;
+            const int t0 = min(a.R, tid * per), t1 = min(a.R, t0 + per);
+            uint32_t keep = 0;   // per <= kMaxList / kBfThreads = 16 tiles
+            int cnt = 0;
+            for (int t = t0; t < t1; ++t) {
+                const int rt = ref_tile(t, a.R, rot);
+                const float4 lo = __ldg(a.tbox + 2 * rt), hi = __ldg(a.tbox + 2 * rt + 1);
+                const float gx = fmaxf(fmaxf(lo.x - qhi[0], qlo[0] - hi.x) - tol, 0.f);
+                const float gy = fmaxf(fmaxf(lo.y - qhi[1], qlo[1] - hi.y) - tol, 0.f);
+                const float gz = fmaxf(fmaxf(lo.z - qhi[2], qlo[2] - hi.z) - tol, 0.f);
+                const float lb2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                if (!(lb2 * (1.f - kSkipRel) > U)) {
+                    keep |= 1u << (t - t0);
+                    ++cnt;
+                }
+            }
+            // exclusive prefix of the counts over the CTA, then the kept tiles in order
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += x;
+            }
+            if (lane == 31) s_cnt[warp] = incl;
+            __syncthreads();
+            int base = incl - cnt;
+            for (int w = 0; w < warp; ++w) base += s_cnt[w];
+            for (int t = t0; t < t1; ++t)
+                if (keep >> (t - t0) & 1u) list[base++] = (uint16_t)ref_tile(t, a.R, rot);
+            if (tid == kBfThreads - 1) s_T = base;
+            __syncthreads();
+            if (s_T == 0) {   // (not reached: the tile of row 0's seed point is always kept)
+                if (tid == 0) {
+                    list[0] = (uint16_t)rot;
+                    s_T = 1;
+                }
+                __syncthreads();
+            }
+            T = s_T;
+        }
+        if (tid == 0 && a.stats) {
+            atomicAdd(a.stats + 8, 1ull);
+            atomicAdd(a.stats + 9, (unsigned long long)T);
+        }
         // ---- prologue: tiles 0 .. kAhead in flight, tile 0 landed and its MMA issued
         for (int t = 0; t <= kAhead; ++t) fetch(t);
         asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
@@ -381,7 +514,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             tmem_ld16_nw(tb + 32, r + 32);
             tmem_ld16_nw(tb + 48, r + 48);
             tmem_wait_ld();
-            const int rt = ref_tile(t, a.R, rot);
+            const int rt = tile_at(t);
             const float nt = __ldg(a.nmax + rt);
             const float E = fmaf(aq, nt, fmaf(kEpsRR * nt, nt, eq));
             float g[8];
@@ -477,15 +610,22 @@ int bf16_prepare(sicp_ctx* ctx) {
     if (ctx->bf16_ready) return SICP_OK;
     const int R = (int)((ctx->M + kRCols - 1) / kRCols);
     const size_t tiles_bytes = (size_t)R * kTileBytes;
-    int rc = ensure(ctx, ctx->bf16_tiles, tiles_bytes + sizeof(float) * (size_t)R);
+    // tiles, then N_t [R], the largest coordinate magnitude, and the tile boxes [R][2] (16-byte aligned)
+    const size_t box_off = (tiles_bytes + sizeof(float) * ((size_t)R + 1) + 15) / 16 * 16;
+    int rc = ensure(ctx, ctx->bf16_tiles, box_off + sizeof(float4) * 2 * (size_t)R);
     if (rc) return rc;
     const float3 c = make_float3(0.5f * (ctx->ref_lo.x + ctx->ref_hi.x), 0.5f * (ctx->ref_lo.y + ctx->ref_hi.y),
                                  0.5f * (ctx->ref_lo.z + ctx->ref_hi.z));
     unsigned* nmax = (unsigned*)((char*)ctx->bf16_tiles.p + tiles_bytes);
-    SICP_CUDA(cudaMemsetAsync(nmax, 0, sizeof(float) * (size_t)R, ctx->stream));
+    unsigned* amax = nmax + R;
+    float4* tbox = (float4*)((char*)ctx->bf16_tiles.p + box_off);
+    SICP_CUDA(cudaMemsetAsync(nmax, 0, sizeof(float) * ((size_t)R + 1), ctx->stream));
     const int64_t rows = (int64_t)R * kRCols;
     k_bf16_btiles<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->grid.v.sorted, (int)ctx->M, c, R, (unsigned char*)ctx->bf16_tiles.p, nmax);
+    SICP_CUDA(cudaGetLastError());
+    k_bf16_tbox<<<(unsigned)(((int64_t)R * 32 + 255) / 256), 256, 0, ctx->stream>>>(ctx->grid.v.sorted, (int)ctx->M,
+                                                                                  R, tbox, amax);
     SICP_CUDA(cudaGetLastError());
     ctx->bf16_centre = c;
     ctx->bf16_R = R;
@@ -496,6 +636,8 @@ int bf16_prepare(sicp_ctx* ctx) {
     h.btiles = (const unsigned char*)ctx->bf16_tiles.p;
     h.nmax = (const float*)nmax;
     h.grid = ctx->grid.v;
+    h.tbox = tbox;
+    h.amax = (const float*)amax;
     if ((rc = ensure(ctx, ctx->bf16_ref, sizeof(BfRef)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->bf16_ref.p, &h, sizeof(BfRef), cudaMemcpyHostToDevice, ctx->stream));
     ctx->bf16_ready = true;
@@ -508,6 +650,7 @@ static BfArgs bf_args(sicp_ctx* ctx, int* err) {
     a.err = err;
     a.polls = ctx->wait_polls;
     a.never = ctx->wait_never;
+    a.stats = ctx->stats_on ? (unsigned long long*)ctx->stats.p : nullptr;
     return a;
 }
 

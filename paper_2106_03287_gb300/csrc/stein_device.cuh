@@ -346,6 +346,7 @@ __device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
         for (int idx = tid; idx < 6 * K; idx += blockDim.x) {
             const float x = a.theta[idx], gb = a.partial[idx];
             const int c = idx % 6;
+            if (a.out_gbar) a.out_gbar[idx] = gb * a.inv_m;
             th[idx] = x;
             float pr = 0.f;
             if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);
@@ -362,6 +363,7 @@ __device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (lane == 0) {
                 const float x = a.theta[idx];
+                if (a.out_gbar) a.out_gbar[idx] = s * a.inv_m;
                 th[idx] = x;
                 float pr = 0.f;
                 if (a.prior == 1) pr = (c < 3) ? -(x - a.mu[c]) / a.sigma[c] : -a.kappa[c - 3] * sinf(x - a.mu[c]);

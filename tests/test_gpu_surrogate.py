@@ -7,7 +7,8 @@ rounds at the same points, so the two differ only by fp32 accumulation order
 and by the rare bf16 rounding decision that an fp32 and an fp64 value take
 differently (one bf16 ulp, 2^-8 relative, of one activation).  Measured on a
 GB300: gradient relative L2 error 1.4e-3 against the bf16 oracle and 6.5e-3
-against the plain FP64 one; the bounds below leave a factor of about 3.
+against the plain FP64 one; the bounds below (5e-3 and 2e-2) leave a factor
+of about 3.
 """
 import math
 
@@ -66,6 +67,11 @@ def test_loss_grad_matches_bf16_oracle(ctx, n, seed):
     e64 = np.linalg.norm(gg - g64) / np.linalg.norm(g64)
     assert e16 <= 5e-3, e16
     assert e16 < 0.5 * e64, (e16, e64)     # the kernels round where the bf16 oracle rounds
+    # against the plain FP64 network, an absolute bound: bf16 keeps 8 significant bits (relative
+    # rounding 2^-9 per value), and the features, weights, two activations and the deltas are each
+    # rounded once on the way to a weight gradient; measured 6.5e-3, bound 2e-2
+    assert e64 <= 2e-2, e64
+    assert abs(lg - l64) <= 2e-2 * abs(l64), (lg, l64)
     for name, (a, b) in BLOCKS.items():
         ref = g16[a:b]
         if name in ("W3", "b3"):
