@@ -392,7 +392,6 @@ def run_ours(args):
     queries = max(st[0], 1.0)   # grid-search counters (zero in the exhaustive modes)
     rows_q, segs_q, pts_q = st[1] / queries, st[2] / queries, st[3] / queries
     coarse_frac, exhaustive_frac = st[4] / queries, st[5] / queries
-    queued_frac = st[10] / queries   # grid gradient queries the neighbourhood lists did not settle
     bytes_per_query = 16 + 4 + 8 * rows_q + 8 * segs_q + 16 * pts_q + (16 if plane else 0)   # + the normal
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -434,8 +433,7 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": grad_ms * 1e3 if grad_ms else None,
                     "launches_timed": int(prof[1]),
                     "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
-                                  "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac,
-                                  "queued_for_warp_search_frac": queued_frac},
+                                  "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
                     "stein_adam_avg_launch_us": stein_us}
     elif nn == "bf16":
         peak, peak_kind = measured_peak("bf16_tflops")

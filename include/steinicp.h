@@ -36,10 +36,8 @@
  *  - Environment (for diagnosis; results do not change):
  *    SICP_NO_GRAPH runs the registration loop as plain launches instead of a
  *    captured CUDA graph; SICP_NO_PDL launches its kernels in plain stream
- *    order instead of with programmatic dependent launch;
- *    SICP_GRID_WARP_SEARCH makes the grid search's gradient kernel search
- *    every query with a whole warp instead of one lane per query over the
- *    cells' neighbourhood lists (read once per process).
+ *    order instead of with programmatic dependent launch (read once per
+ *    process).
  */
 #ifndef STEINICP_H
 #define STEINICP_H
@@ -429,6 +427,21 @@ int sicp_icp_grad_noalloc(const float* ref_xyz, int64_t M, const float* src_xyz,
 int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
                          float lr, float* out_loss);
 
+/* sicp_surrogate_train with the training queries that a registration run
+ * puts to the search: n_queries source points s drawn uniformly from
+ * src_xyz [N][3], each moved by a pose theta drawn uniformly from the
+ * axis-aligned box that the run's initial particles [K][6] span,
+ * q = R(theta) s + u, labelled by the exact grid search.  The particles of
+ * the early iterations, where the surrogate stands in for the search, move
+ * inside that box towards the answer.  Everything else (normalisation,
+ * initial weights from `seed`, epochs, batches, Adam, out_loss) as
+ * sicp_surrogate_train.  on_device as everywhere.  Errors as
+ * sicp_surrogate_train, plus SICP_EINVAL for N outside [1, 2^31 - 1], K
+ * outside [1, 2048] or a non-finite input. */
+int sicp_surrogate_train_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles, int32_t K,
+                             int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch, float lr,
+                             float* out_loss, int on_device);
+
 /* Read (set = 0) or replace (set = 1) the surrogate's parameters: params
  * [33040] float32 in the layout above, norm4 = (cx, cy, cz, s); host arrays.
  * Setting marks the surrogate trained.  Errors: SICP_EINVAL (NULL,
@@ -466,19 +479,16 @@ int sicp_surrogate_infer(sicp_ctx* ctx, const float* q, int64_t n, float* out_di
 
 /* Work counters of the searches (no counterpart in the paper; they state
  * the algorithmic bytes a search moved).  Copies the counters accumulated
- * since the previous call into out11 (may be NULL): grid search queries, rows
- * examined (one row span each), row segments read (two cell offsets each; a
- * query's neighbourhood list counts as one), candidate points read (16 bytes
- * each), queries that went on to the coarse level, queries that went on to
- * the exhaustive scan, queries put to the surrogate, surrogate queries sent
- * on to the exact search, query tiles of the tensor-core search (128 queries
- * each), reference tiles those query tiles swept (256 points each; the
- * others were ruled out by their bounding boxes), queries of the grid
- * gradient kernel that its neighbourhood lists could not settle (searched
- * again by a whole warp); then zeroes them and turns counting on
- * (enable = 1) or off.  Counting adds a few warp-aggregated atomics per 32
- * lanes. */
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out11);
+ * since the previous call into out10 (may be NULL): grid search queries, rows
+ * examined (one row span each), row segments read (two cell offsets each),
+ * candidate points read (16 bytes each), queries that went on to the coarse
+ * level, queries that went on to the exhaustive scan, queries put to the
+ * surrogate, surrogate queries sent on to the exact search, query tiles of
+ * the tensor-core search (128 queries each), reference tiles those query
+ * tiles swept (256 points each; the others were ruled out by their bounding
+ * boxes); then zeroes them and turns counting on (enable = 1) or off.
+ * Counting adds a few warp-aggregated atomics per 32 lanes. */
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out10);
 
 /* Kernel timing inside sicp_register (no counterpart in the paper).  With
  * stride s > 0 the captured loop records CUDA events around the gradient and

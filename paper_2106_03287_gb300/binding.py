@@ -46,7 +46,7 @@ EXPORTS = (
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
     "sicp_export_state", "sicp_import_state", "sicp_resume", "sicp_set_memory_limit", "sicp_set_wait_check",
-    "sicp_trace_batched", "sicp_read_batched_trace",
+    "sicp_trace_batched", "sicp_read_batched_trace", "sicp_surrogate_train_run",
 )
 
 SURROGATE_NPARAM = 33040
@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
             "sicp_set_memory_limit": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "sicp_set_wait_check": (ctypes.c_int, [P, ctypes.c_int, I64]),
             "sicp_trace_batched": (ctypes.c_int, [P, I32]),
+            "sicp_surrogate_train_run": (ctypes.c_int, [P, P, I64, P, I32, I64, U64, I32, I32, F32, P, ctypes.c_int]),
             "sicp_read_batched_trace": (ctypes.c_int, [P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -453,10 +454,9 @@ def sicp_stats(ctx, enable: bool = True):
     """Search counters since the last call (queries, rows, segments, points,
     coarse-level queries, exhaustive-scan queries, surrogate queries,
     surrogate queries sent to the exact search, tensor-core query tiles,
-    reference tiles they swept, grid gradient queries the neighbourhood lists
-    could not settle) as a uint64 array; then resets them and sets counting
-    on/off."""
-    out = np.zeros(11, np.uint64)
+    reference tiles they swept) as a uint64 array; then resets them and sets
+    counting on/off."""
+    out = np.zeros(10, np.uint64)
     _check(ctx, lib().sicp_stats(ctx, int(enable), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
@@ -480,6 +480,19 @@ def sicp_profile(ctx, stride: int = 0):
     out = np.zeros(4, np.float64)
     _check(ctx, lib().sicp_profile(ctx, int(stride), out.ctypes.data_as(ctypes.c_void_p)))
     return out
+
+
+def sicp_surrogate_train_run(ctx, src_xyz, particles, n_queries: int, seed: int = 0, epochs: int = 10,
+                             batch: int = 4096, lr: float = 1e-3) -> float:
+    """Train the learned field on a run's own queries (source points under poses from the box of the
+    initial particles); returns the mean batch loss of the last epoch."""
+    src_xyz, particles = _host(src_xyz, np.float32), _host(particles, np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(ctx, lib().sicp_surrogate_train_run(ctx, _ptr(src_xyz, np.float32), src_xyz.shape[0],
+                                               _ptr(particles, np.float32), particles.shape[0], int(n_queries),
+                                               seed & ((1 << 64) - 1), int(epochs), int(batch), float(lr),
+                                               ctypes.byref(loss), _on_device(src_xyz, particles)))
+    return float(loss.value)
 
 
 def sicp_surrogate_train(ctx, n_queries: int, seed: int = 0, epochs: int = 10, batch: int = 4096,

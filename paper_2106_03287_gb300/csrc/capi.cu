@@ -75,7 +75,6 @@ struct LoopKey {
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
     int64_t wait_polls;     // failure-detection check settings (the kernels take them by value)
     int32_t wait_never, pad2;
-    const void* fastq;      // the fast grid kernel's work queue
     const void* ptrs[12];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -279,21 +278,10 @@ void collect_profile(sicp_ctx* ctx, GraphSlot& s) {
     s.pending = false;
 }
 
-// The gradient kernel of an exact search.  The grid search's lane-per-query kernel takes its work
-// queue from ctx->fastq (sized and zeroed by the caller when grid_fast_path holds).
 cudaError_t launch_grad(sicp_ctx* ctx, int32_t mode, const GradArgs& g) {
     if (mode == SICP_NN_GRID)
-        return launch_grad_grid(ctx, g, grid_fast_path(ctx, g.K, g.m) ? ctx->fastq.p : nullptr);
+        return launch_grad_grid(g, (const GridSearch*)ctx->search_dev.p, ctx->search_slot, ctx->stream);
     return launch_grad_brute(g, ctx->ref4, ctx->M, ctx->stream);
-}
-
-// Size and zero the fast grid kernel's work queue (in stream order).
-int prepare_grid_queue(sicp_ctx* ctx, int32_t K, int32_t m) {
-    if (!grid_fast_path(ctx, K, m)) return SICP_OK;
-    int rc = ensure(ctx, ctx->fastq, grid_fast_queue_bytes(K, m));
-    if (rc) return rc;
-    SICP_CUDA(cudaMemsetAsync(ctx->fastq.p, 0, 64, ctx->stream));   // the counters
-    return SICP_OK;
 }
 
 constexpr int32_t kMaxK = 2048;
@@ -359,8 +347,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar,
-                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume, &c->blk_start,
-                   &c->blk_pts, &c->fastq};
+                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -556,7 +543,6 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.inv_m = 1.f / (float)m;
     g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
     g.mb_stride = 0;
-    if (mode == SICP_NN_GRID && (rc = prepare_grid_queue(ctx, K, m))) return rc;
     if (surr) {
         SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, m, g.theta, K, kSurrogateIcpGradConf, (float*)ctx->partial.p,
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
@@ -570,7 +556,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     }
     if ((rc = copy_out(ctx, out_gbar, d_g, sizeof(float) * 6 * K, on_device))) return rc;
     if (out_nn && (rc = copy_out(ctx, out_nn, d_nn, sizeof(int32_t) * (size_t)m * K, on_device))) return rc;
-    if (surr || bf || mode == SICP_NN_GRID) {
+    if (surr || bf) {
         if ((rc = read_flags(ctx, flags))) return rc;
         if (flags[3]) return set_err(ctx, SICP_ETIMEOUT, "a bounded wait on the GPU gave up");
     }
@@ -728,8 +714,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if ((rc = ensure(ctx, ctx->gbar, b_th + 4 * sizeof(float)))) return rc;   // + the two blocks' medians
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
-    const bool fastq = grid && grid_fast_path(ctx, K, p.m);
-    if (fastq && (rc = ensure(ctx, ctx->fastq, grid_fast_queue_bytes(K, p.m)))) return rc;
 
     const void *d_src, *d_th0;
     if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
@@ -786,7 +770,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.ref_M = ctx->M;   // (the grid and BF16 kernels read the reference's description from device memory)
     key.wait_polls = ctx->wait_polls;
     key.wait_never = ctx->wait_never;
-    key.fastq = fastq ? ctx->fastq.p : nullptr;
     key.ptrs[0] = ctx->src4.p;
     key.ptrs[1] = ctx->mb.p;
     key.ptrs[2] = ctx->theta.p;
@@ -804,8 +787,6 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
     const bool use_graph = getenv("SICP_NO_GRAPH") == nullptr;
     auto record = [&](GraphSlot* prof) -> int {
-        // the lane-per-query grid kernel's queue counters start at zero (each launch leaves them so)
-        if (fastq) SICP_CUDA(cudaMemsetAsync(ctx->fastq.p, 0, 64, ctx->stream));
         if (indep)
             SICP_CUDA(launch_minibatch_runs(p.seed, t0, p.T, N, p.m, K, (int32_t*)ctx->mb.p, ctx->stream));
         else
@@ -1084,21 +1065,21 @@ int sicp_resume(sicp_ctx* ctx, const float* src_xyz, int64_t N, const sicp_param
     return SICP_OK;
 }
 
-int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out11) {
+int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out10) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     DeviceScope ds(ctx->device);
-    int rc = ensure(ctx, ctx->stats, 11 * sizeof(unsigned long long));
+    int rc = ensure(ctx, ctx->stats, 10 * sizeof(unsigned long long));
     if (rc) return rc;
-    if (out11) {
-        unsigned long long h[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (out10) {
+        unsigned long long h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (ctx->stats_on) {
             SICP_CUDA(cudaMemcpyAsync(h, ctx->stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
             if ((rc = sync(ctx))) return rc;
         }
-        for (int a = 0; a < 11; ++a) out11[a] = (uint64_t)h[a];
+        for (int a = 0; a < 10; ++a) out10[a] = (uint64_t)h[a];
     }
-    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 11 * sizeof(unsigned long long), ctx->stream));
+    SICP_CUDA(cudaMemsetAsync(ctx->stats.p, 0, 10 * sizeof(unsigned long long), ctx->stream));
     ctx->stats_on = enable != 0;
     return sync(ctx);
 }

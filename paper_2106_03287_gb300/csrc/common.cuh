@@ -165,10 +165,6 @@ struct GridSearch {
     SearchTable tab;
     const float4* ref4;
     int M;
-    // per fine cell c, the points of the 3 x 3 x 3 cells around it (clipped at the grid's edges),
-    // row by row: blk_pts[blk_start[c] .. blk_start[c + 1]) (null when the cloud is too large for them)
-    const int32_t* blk_start;
-    const float4* blk_pts;
 };
 
 bool pdl_enabled();   // false when the environment sets SICP_NO_PDL
@@ -246,10 +242,6 @@ struct sicp_ctx {
     sicp::Buf resume;                    // device staging of that state for sicp_resume
     sicp::Buf normals;                   // point-to-plane: float4 [M] unit normals by original index
     int normals_k = 0;                   // neighbours they were computed from; 0: none for this reference
-    // the fine level's per-cell neighbourhood lists (GridSearch::blk_start / blk_pts) and the work
-    // queue of the lane-per-query grid gradient kernel (8 counters, then one entry per query)
-    sicp::Buf blk_start, blk_pts, fastq;
-    int fast_ctas = 0;                   // resident CTAs of that kernel on this device (0: not known yet)
     // failure-detection check (sicp_set_wait_check): when set, every bounded device wait of the
     // context's kernels waits for an event that never comes, polling at most wait_polls times
     // (0: each wait's default limit)
@@ -416,13 +408,7 @@ cudaError_t launch_nn_grid(const GridSearch& g, const float* q, int64_t n, int32
                            unsigned long long* stats, cudaStream_t s);
 // d_search: the device copy of the context's GridSearch (sicp_ctx::search_dev);
 // slot: the context's constant-memory copy (sicp_ctx::search_slot), or < 0
-// The grid search's gradient kernel(s) and the reduction.  With `queue` (grid_fast_queue_bytes; its
-// first 64 bytes, the counters, zeroed before the first launch; every launch leaves them zeroed) and
-// the fine level's block lists: the lane-per-query kernel and the queue kernel; otherwise the
-// warp-per-query kernel.
-cudaError_t launch_grad_grid(sicp_ctx* ctx, const GradArgs& a, void* queue);
-bool grid_fast_path(const sicp_ctx* ctx, int32_t K, int32_t m);
-size_t grid_fast_queue_bytes(int32_t K, int32_t m);
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s);
 int search_slot_acquire();   // a free constant-memory slot, or -1
 void search_slot_release(int slot);
 

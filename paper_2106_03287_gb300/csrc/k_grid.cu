@@ -35,8 +35,6 @@
 #include <float.h>
 #include <math.h>
 
-#include <stdlib.h>
-
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -145,239 +143,6 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
         if (lane == 0 && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
     }
     if (kStats) add_stats(a.stats, w);
-}
-
-// ---------------------------------------------------------------- lane-per-query gradient kernel
-//
-// Most queries of a registration lie near the reference surface once the
-// particles have moved in, and their nearest point is then among the few
-// points of the 3 x 3 x 3 fine cells around the query's own cell.  Those
-// points are stored contiguously per cell (blk_pts, built with the grid), so a
-// lane can take one query by itself: one offset load, then a scan of ~30
-// points with the search's distance and tie rule.  The answer is certified
-// when the best distance found is below the distance from the query to the
-// faces of that 3 x 3 x 3 block (widened by the grid's tol and bound2, as in
-// the table walk; a face on the grid's edge has nothing beyond it): every
-// point outside the block is then strictly farther.  A query that is not
-// certified goes to a work queue with its best point so far, and a second
-// kernel takes the queued queries one warp each with the warp-per-query
-// search (prove), starting from that point.  Either way the answer is the
-// exact one of the same search, and the gradient terms are the same
-// arithmetic as k_grad_grid's, so the two paths give the same results.
-//
-// Work: warp w of the first kernel takes queries 32 w .. 32 w + 31 (query
-// g = k K + j: minibatch entry k under particle j) and appends its
-// uncertified ones to the queue (counter ctl[1], one 64-bit entry each:
-// best index + 1 in the high half, g in the low half).  The second kernel is
-// persistent; its warps take entries from counter ctl[2] until the count of
-// the first (complete by then: the second kernel waits for it) is reached,
-// and its last warp to leave zeroes the counters for the next launch.
-constexpr int64_t kMaxBlockPoints = (int64_t)1 << 26;   // block-list entries (27 per point at most): 1 GB
-constexpr int kFastThreads = 128;
-constexpr int kFastWarps = kFastThreads / 32;
-constexpr int kPoseTable = 128;               // particles whose poses a CTA keeps in shared memory
-
-// Distance from the query to the faces of the 3 x 3 x 3 block around cell c
-// along one axis (faces on the grid's edge do not count).
-__device__ __forceinline__ float block_face(float v, float o, float cell, int c, int n) {
-    float d = FLT_MAX;
-    if (c - 1 > 0) d = fminf(d, v - fmaf((float)(c - 1), cell, o));
-    if (c + 1 < n - 1) d = fminf(d, fmaf((float)(c + 2), cell, o) - v);
-    return d;
-}
-
-// One query by one lane: the scan of its cell's block list; writes the
-// gradient terms and returns true when the answer is certified, else leaves
-// the best point so far in *best.
-__device__ __forceinline__ bool fast_query(const GradArgs& a, const GridSearch& S, const Pose& P, int j, int k,
-                                           unsigned* best, Work& w) {
-    const GridView& F = S.fine;
-    const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
-    const float3 s = make_float3(s4.x, s4.y, s4.z);
-    const float3 q = apply_pose(P, s);
-    const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
-    const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
-    const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
-    const int64_t cell = ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx;
-    const int b0 = __ldg(S.blk_start + cell), b1 = __ldg(S.blk_start + cell + 1);
-    Best B;
-    B.d = FLT_MAX;
-    B.i = kNone;
-    B.p = make_float3(0.f, 0.f, 0.f);
-    for (int t = b0; t < b1; ++t) {
-        const float4 r = __ldg(S.blk_pts + t);
-        take(B, r, q, __float_as_int(r.w));
-    }
-    w.queries += 1;
-    w.segs += 1;
-    w.pts += (unsigned)(b1 - b0);
-    const float face = fminf(block_face(q.x, F.origin.x, F.cell, cx, F.dims.x),
-                             fminf(block_face(q.y, F.origin.y, F.cell, cy, F.dims.y),
-                                   block_face(q.z, F.origin.z, F.cell, cz, F.dims.z))) - F.tol;
-    if (!(B.i != kNone && face > 0.f && face * face > bound2(B.d))) {
-        *best = (unsigned)B.i;
-        return false;
-    }
-    float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
-    if (a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
-    float t6[6];
-    grad_terms(P, s, d, t6);
-    float* dst = a.partial + ((int64_t)j * a.m + k) * 6;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) dst[c] = t6[c];
-    if (a.out_nn) a.out_nn[(int64_t)j * a.m + k] = B.i;
-    return true;
-}
-
-// A queued query by one warp, from its best point so far (kNone: from the seed).
-__device__ __forceinline__ void queued_query(const GradArgs& a, const GridSearch& S, const Pose& P, int j, int k,
-                                             int bi, Work& w) {
-    const int lane = threadIdx.x & 31;
-    const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
-    const float3 s = make_float3(s4.x, s4.y, s4.z);
-    const float3 q = apply_pose(P, s);
-    Best B;
-    if (bi != kNone) {
-        const float4 r = __ldg(S.ref4 + bi);
-        B.d = dist2(r, q);
-        B.i = bi;
-        B.p = make_float3(r.x, r.y, r.z);
-        prove(S, q, B, w);
-    } else {
-        grid_search(S, q, B, w);
-        w.queries -= lane == 0;   // (counted when a lane took it)
-    }
-    const bool found = B.i != kNone;   // false only for a non-finite distance
-    float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
-    if (found && a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
-    if (lane < 6) a.partial[((int64_t)j * a.m + k) * 6 + lane] = found ? grad_term(P, s, d, lane) : 0.f;
-    if (lane == 0 && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
-}
-
-template <bool kStats, bool kConst>
-__global__ void __launch_bounds__(kFastThreads) k_grad_grid_fast(GradArgs a, const GridSearch* __restrict__ Sd,
-                                                                  int slot, unsigned* __restrict__ ctl,
-                                                                  unsigned long long* __restrict__ fbq) {
-    extern __shared__ Pose Pt[];                  // [K] when K <= kPoseTable
-    const int lane = threadIdx.x & 31;
-    pdl_wait();      // the particles of the previous Stein step
-    pdl_trigger();   // the queue kernel may be scheduled (it waits for this grid)
-    const bool table = a.K <= kPoseTable;
-    if (table) {
-        for (int i = threadIdx.x; i < a.K; i += blockDim.x) make_pose(a.theta + 6 * i, Pt[i]);
-        __syncthreads();
-    }
-    const GridSearch& S = kConst ? c_search[slot] : *Sd;
-    const int64_t Q = (int64_t)a.K * a.m;
-    const int64_t g = (int64_t)blockIdx.x * kFastThreads + threadIdx.x;
-    Work w;
-    bool queue = false;
-    unsigned best = (unsigned)kNone;
-    if (g < Q) {
-        const int k = (int)(g / a.K), j = (int)(g % a.K);
-        if (table) {
-            queue = !fast_query(a, S, Pt[j], j, k, &best, w);
-        } else {
-            Pose own;
-            make_pose(a.theta + 6 * j, own);
-            queue = !fast_query(a, S, own, j, k, &best, w);
-        }
-    }
-    const unsigned mq = __ballot_sync(kFull, queue);
-    if (mq) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(ctl + 1, (unsigned)__popc(mq));
-        base = __shfl_sync(kFull, base, 0);
-        if (queue) fbq[base + (unsigned)__popc(mq & ((1u << lane) - 1u))] =
-            ((unsigned long long)(best + 1u) << 32) | (unsigned long long)(unsigned)g;
-    }
-    if (kStats) {
-        add_stats(a.stats, w);
-        if (lane == 0 && mq) atomicAdd(a.stats + 10, (unsigned long long)__popc(mq));
-    }
-}
-
-template <bool kStats, bool kConst>
-__global__ void __launch_bounds__(kFastThreads) k_grad_grid_queue(GradArgs a, const GridSearch* __restrict__ Sd,
-                                                                   int slot, unsigned* __restrict__ ctl,
-                                                                   const unsigned long long* __restrict__ fbq) {
-    extern __shared__ Pose Pt[];                  // [K] when K <= kPoseTable
-    __shared__ Pose Pw[kFastWarps];               // a query's pose when there is no table
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // The particles are final before this grid starts (the lane kernel it follows started only
-    // after the previous Stein step had completed), so the pose table is built before the wait.
-    const bool table = a.K <= kPoseTable;
-    if (table) {
-        for (int i = threadIdx.x; i < a.K; i += blockDim.x) make_pose(a.theta + 6 * i, Pt[i]);
-        __syncthreads();
-    }
-    pdl_wait();      // the lane kernel: every queue entry is written
-    pdl_trigger();   // the reduction may be scheduled (it waits for this grid)
-    const GridSearch& S = kConst ? c_search[slot] : *Sd;
-    const unsigned n = *(volatile unsigned*)(ctl + 1);
-    Work w;
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(ctl + 2, 1u);
-        i = __shfl_sync(kFull, i, 0);
-        if (i >= n) break;
-        const unsigned long long e = fbq[i];
-        const int64_t g = (int64_t)(unsigned)e;
-        const int bi = (int)((unsigned)(e >> 32) - 1u);
-        const int k = (int)(g / a.K), j = (int)(g % a.K);
-        if (table) {
-            queued_query(a, S, Pt[j], j, k, bi, w);
-        } else {
-            if (lane == 0) make_pose(a.theta + 6 * j, Pw[warp]);
-            __syncwarp();
-            queued_query(a, S, Pw[warp], j, k, bi, w);
-            __syncwarp();
-        }
-    }
-    if (kStats) add_stats(a.stats, w);
-    // the last warp to leave zeroes the counters for the next launch
-    if (lane == 0) {
-        __threadfence();
-        if (atomicAdd(ctl + 3, 1u) + 1u == gridDim.x * kFastWarps) {
-            ctl[1] = ctl[2] = ctl[3] = 0u;
-            __threadfence();
-        }
-    }
-}
-
-// Per fine cell, the number of points of the 3 x 3 x 3 block around it.
-__global__ void k_blk_count(GridView g, int64_t ncells, int32_t* __restrict__ counts) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y),
-                  z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
-        const int x0 = max(x - 1, 0), x1 = min(x + 1, g.dims.x - 1);
-        int n = 0;
-        for (int zz = max(z - 1, 0); zz <= min(z + 1, g.dims.z - 1); ++zz)
-            for (int yy = max(y - 1, 0); yy <= min(y + 1, g.dims.y - 1); ++yy) {
-                const int64_t row = ((int64_t)zz * g.dims.y + yy) * g.dims.x;
-                n += g.cell_start[row + x1 + 1] - g.cell_start[row + x0];
-            }
-        counts[c] = n;
-    }
-}
-
-// The block lists themselves: one warp per cell copies its nine row segments.
-__global__ void k_blk_fill(GridView g, int64_t ncells, const int32_t* __restrict__ start, float4* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncells; c += nw) {
-        const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y),
-                  z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
-        const int x0 = max(x - 1, 0), x1 = min(x + 1, g.dims.x - 1);
-        int o = start[c];
-        for (int zz = max(z - 1, 0); zz <= min(z + 1, g.dims.z - 1); ++zz)
-            for (int yy = max(y - 1, 0); yy <= min(y + 1, g.dims.y - 1); ++yy) {
-                const int64_t row = ((int64_t)zz * g.dims.y + yy) * g.dims.x;
-                const int b = g.cell_start[row + x0], e = g.cell_start[row + x1 + 1];
-                for (int i = b + lane; i < e; i += 32) out[o + (i - b)] = g.sorted[i];
-                o += e - b;
-            }
-    }
 }
 
 // ---------------------------------------------------------------- build kernels
@@ -588,29 +353,6 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     return SICP_OK;
 }
 
-// The fine level's block lists (k_blk_count, scan, k_blk_fill).  The list
-// array is sized for the bound of 27 entries per point, so no count has to be
-// read back; clouds past kMaxBlockPoints / 27 points go without (the gradient
-// kernel then searches every query with the warp-per-query search).
-int blk_build(sicp_ctx* ctx) {
-    const int64_t M = ctx->M;
-    if (27 * M > kMaxBlockPoints) return SICP_OK;
-    Grid& G = ctx->grid;
-    const int64_t ncells = G.ncells;
-    cudaStream_t s = ctx->stream;
-    int rc;
-    if ((rc = ensure(ctx, ctx->blk_start, sizeof(int32_t) * ((size_t)ncells + 1)))) return rc;
-    if ((rc = ensure(ctx, ctx->blk_pts, sizeof(float4) * (size_t)(27 * M)))) return rc;
-    // the fine level's counts and scan scratch are free once the level is built
-    k_blk_count<<<blocks_for(ncells, 256), 256, 0, s>>>(G.v, ncells, G.counts);
-    SICP_CUDA(cudaGetLastError());
-    SICP_CUDA(launch_exclusive_scan(G.counts, ncells, (int32_t*)ctx->blk_start.p, G.scan_sums, s));
-    k_blk_fill<<<blocks_for(ncells * 32, 256), 256, 0, s>>>(G.v, ncells, (const int32_t*)ctx->blk_start.p,
-                                                           (float4*)ctx->blk_pts.p);
-    SICP_CUDA(cudaGetLastError());
-    return SICP_OK;
-}
-
 }  // namespace
 
 int search_table_init(sicp_ctx* ctx) {
@@ -692,15 +434,12 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
         }
     }
     if ((rc = build_level(ctx, ctx->grid, lo, ext, X, c, true))) return rc;
-    if ((rc = blk_build(ctx))) return rc;
     const double c2 = (double)ctx->grid.v.cell * kCoarseFactor;
     if ((rc = build_level(ctx, ctx->grid2, lo, ext, X, c2, false))) return rc;
     ctx->search.fine = ctx->grid.v;
     ctx->search.coarse = ctx->grid2.v;
     ctx->search.ref4 = ctx->ref4;
     ctx->search.M = (int)M;
-    ctx->search.blk_start = 27 * M <= kMaxBlockPoints ? (const int32_t*)ctx->blk_start.p : nullptr;
-    ctx->search.blk_pts = 27 * M <= kMaxBlockPoints ? (const float4*)ctx->blk_pts.p : nullptr;
     // the device copy the captured gradient launches read
     if ((rc = ensure(ctx, ctx->search_dev, sizeof(GridSearch)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->search_dev.p, &ctx->search, sizeof(GridSearch), cudaMemcpyHostToDevice, s));
@@ -741,40 +480,8 @@ void search_slot_release(int slot) {
     g_slot_used[slot] = false;
 }
 
-bool grid_fast_path(const sicp_ctx* ctx, int32_t K, int32_t m) {
-    static const bool off = getenv("SICP_GRID_WARP_SEARCH") != nullptr;
-    return !off && ctx->search.blk_pts != nullptr && (int64_t)K * m < ((int64_t)1 << 31);
-}
-
-size_t grid_fast_queue_bytes(int32_t K, int32_t m) { return 64 + sizeof(unsigned long long) * (size_t)K * m; }
-
-cudaError_t launch_grad_grid(sicp_ctx* ctx, const GradArgs& a, void* queue) {
-    const GridSearch* d_search = (const GridSearch*)ctx->search_dev.p;
-    const int slot = ctx->search_slot;
-    cudaStream_t s = ctx->stream;
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s) {
     cudaError_t e;
-    if (queue && grid_fast_path(ctx, a.K, a.m)) {
-        const size_t smem = a.K <= kPoseTable ? sizeof(Pose) * (size_t)a.K : 0;
-        auto kf = slot >= 0 ? (a.stats ? k_grad_grid_fast<true, true> : k_grad_grid_fast<false, true>)
-                            : (a.stats ? k_grad_grid_fast<true, false> : k_grad_grid_fast<false, false>);
-        auto kq = slot >= 0 ? (a.stats ? k_grad_grid_queue<true, true> : k_grad_grid_queue<false, true>)
-                            : (a.stats ? k_grad_grid_queue<true, false> : k_grad_grid_queue<false, false>);
-        const int64_t Q = (int64_t)a.K * a.m;
-        unsigned* ctl = (unsigned*)queue;
-        unsigned long long* fbq = (unsigned long long*)((char*)queue + 64);
-        e = launch_pdl(kf, dim3((unsigned)((Q + kFastThreads - 1) / kFastThreads)), dim3(kFastThreads), smem, s, a,
-                       d_search, slot, ctl, fbq);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kq, kFastThreads, smem)) != cudaSuccess)
-            return e;
-        const int64_t want = (Q + kFastWarps - 1) / kFastWarps;
-        const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * ctx->num_sms, want));
-        e = launch_pdl(kq, dim3(ctas), dim3(kFastThreads), smem, s, a, d_search, slot, ctl,
-                       (const unsigned long long*)fbq);
-        if (e != cudaSuccess) return e;
-        return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
-    }
     dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
     const dim3 blk(kGradThreads);
     if (slot >= 0)

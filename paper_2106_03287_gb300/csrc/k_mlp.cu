@@ -427,6 +427,10 @@ __global__ void k_mlp_images(const float* __restrict__ params, unsigned char* __
     }
 }
 
+struct Pose6 {
+    float v[6];
+};
+
 // Training queries: even samples around reference points (normal offsets
 // whose standard deviation is log-uniform in [sd_n / 50, sd_n], normalised
 // units), odd samples uniform in the unit cube; stored normalised and in
@@ -455,6 +459,32 @@ __global__ void k_surr_samples(const float4* __restrict__ ref, int M, int64_t n,
         qw[3 * i] = c.x + s * p.x;
         qw[3 * i + 1] = c.y + s * p.y;
         qw[3 * i + 2] = c.z + s * p.z;
+    }
+}
+
+// Training queries of a registration run: source point s (uniform over the
+// source cloud) moved by a pose theta drawn uniformly from the box lo..hi of
+// the run's initial particles, q = R(theta) s + u -- the queries that the
+// run's own iterations put to the search, as the particles move from their
+// initial spread towards the answer.  Stored normalised and in metres.
+__global__ void k_surr_samples_run(const float4* __restrict__ src, int64_t N, Pose6 lo, Pose6 hi, int64_t n,
+                                   uint64_t seed, float3 c, float s, float* __restrict__ qn, float* __restrict__ qw) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t base = sm64_at(seed, (uint64_t)i + 1);
+        float u[7];
+        for (int k = 0; k < 7; ++k) u[k] = ((float)(sm64_at(base, k + 1) >> 40) + 0.5f) * (1.f / 16777216.f);
+        const float4 s4 = src[min((int64_t)(u[0] * (float)N), N - 1)];
+        float th[6];
+        for (int a = 0; a < 6; ++a) th[a] = fmaf(hi.v[a] - lo.v[a], u[1 + a], lo.v[a]);
+        Pose P;
+        make_pose(th, P);
+        const float3 q = apply_pose(P, make_float3(s4.x, s4.y, s4.z));
+        qw[3 * i] = q.x;
+        qw[3 * i + 1] = q.y;
+        qw[3 * i + 2] = q.z;
+        qn[3 * i] = (q.x - c.x) / s;
+        qn[3 * i + 1] = (q.y - c.y) / s;
+        qn[3 * i + 2] = (q.z - c.z) / s;
     }
 }
 
@@ -949,10 +979,19 @@ int read_err_flag(sicp_ctx* ctx, int* out) {
 
 }  // namespace
 
-extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
-                                    float lr, float* out_loss) {
-    if (!ctx) return SICP_EINVAL;
-    ctx->err.clear();
+namespace {
+
+// Where the training queries come from: the fixed distribution around the
+// reference (src null), or a run's source points under poses from its
+// particles' box.
+struct RunSampling {
+    const float4* src = nullptr;
+    int64_t N = 0;
+    Pose6 lo{}, hi{};
+};
+
+int surrogate_train_impl(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch, float lr,
+                         float* out_loss, const RunSampling& run) {
     if (ctx->M < 1) return set_err(ctx, SICP_ENOREF, "no reference cloud set");
     if (n_queries < kRows || n_queries > ((int64_t)1 << 26) || epochs < 1 || epochs > 100000 || batch < kRows ||
         batch > kMaxTrainRows || batch % kRows || !(lr > 0.f) || !isfinite(lr))
@@ -988,8 +1027,12 @@ extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t s
     SICP_CUDA(cudaMemsetAsync(S.step.p, 0, sizeof(int) * 4, s));
     SICP_CUDA(launch_images(S, s));
     // labelled samples: exact correspondences from the grid search
-    k_surr_samples<<<blocks_n(n, 256), 256, 0, s>>>(ctx->ref4, (int)ctx->M, n, seed, S.c, S.s, 0.1f,
-                                                     (float*)S.qn.p, (float*)S.qw.p);
+    if (run.src)
+        k_surr_samples_run<<<blocks_n(n, 256), 256, 0, s>>>(run.src, run.N, run.lo, run.hi, n, seed, S.c, S.s,
+                                                             (float*)S.qn.p, (float*)S.qw.p);
+    else
+        k_surr_samples<<<blocks_n(n, 256), 256, 0, s>>>(ctx->ref4, (int)ctx->M, n, seed, S.c, S.s, 0.1f,
+                                                         (float*)S.qn.p, (float*)S.qw.p);
     SICP_CUDA(cudaGetLastError());
     SICP_CUDA(launch_nn_grid(ctx->search, (const float*)S.qw.p, n, (int32_t*)S.idx.p, nullptr, nullptr, s));
     k_surr_targets<<<blocks_n(n, 256), 256, 0, s>>>(ctx->ref4, (const float*)S.qw.p, (const int32_t*)S.idx.p, n,
@@ -1042,6 +1085,64 @@ extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t s
         *out_loss = (float)(sum / steps);   // mean batch loss over the last epoch
     }
     return SICP_OK;
+}
+
+}  // namespace
+
+extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
+                                    float lr, float* out_loss) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    return surrogate_train_impl(ctx, n_queries, seed, epochs, batch, lr, out_loss, RunSampling{});
+}
+
+extern "C" int sicp_surrogate_train_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles,
+                                        int32_t K, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
+                                        float lr, float* out_loss, int on_device) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (!src_xyz || !particles || N < 1 || N > 0x7fffffff || K < 1 || K > 2048)
+        return set_err(ctx, SICP_EINVAL, "run sampling needs a source (1 <= N < 2^31) and 1 <= K <= 2048 particles");
+    DevScope ds(ctx->device);
+    std::vector<float> th(6 * (size_t)K);
+    if (on_device) {
+        SICP_CUDA(cudaMemcpyAsync(th.data(), particles, sizeof(float) * th.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        SICP_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        memcpy(th.data(), particles, sizeof(float) * th.size());
+    }
+    RunSampling run;
+    for (int a = 0; a < 6; ++a) {
+        run.lo.v[a] = run.hi.v[a] = th[a];
+        for (int32_t j = 1; j < K; ++j) {
+            run.lo.v[a] = fminf(run.lo.v[a], th[6 * j + a]);
+            run.hi.v[a] = fmaxf(run.hi.v[a], th[6 * j + a]);
+        }
+        if (!isfinite(run.lo.v[a]) || !isfinite(run.hi.v[a])) return set_err(ctx, SICP_EINVAL, "non-finite particle");
+    }
+    const void* d_src = src_xyz;
+    if (!on_device) {
+        int rc = ensure(ctx, ctx->tmp_in, sizeof(float) * 3 * (size_t)N);
+        if (rc) return rc;
+        SICP_CUDA(cudaMemcpyAsync(ctx->tmp_in.p, src_xyz, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+        d_src = ctx->tmp_in.p;
+    }
+    int rc = ensure(ctx, ctx->src4, sizeof(float4) * (size_t)N);
+    if (rc) return rc;
+    SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
+    SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    int bad = 0;
+    {
+        int flags[4];
+        SICP_CUDA(cudaMemcpyAsync(flags, ctx->flags.p, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
+        SICP_CUDA(cudaStreamSynchronize(ctx->stream));
+        bad = flags[0];
+    }
+    if (bad) return set_err(ctx, SICP_EINVAL, "non-finite source point");
+    run.src = (const float4*)ctx->src4.p;
+    run.N = N;
+    return surrogate_train_impl(ctx, n_queries, seed, epochs, batch, lr, out_loss, run);
 }
 
 extern "C" int sicp_surrogate_params(sicp_ctx* ctx, int set, float* params, float* norm4) {
