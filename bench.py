@@ -714,7 +714,7 @@ def run_ours_batched(args):
                 "config": {"workload": "batched", "problems": len(raw), "reference_points_total": Mtot,
                            "source_points_total": Ntot, "particles_total": sum(Ks), "minibatch": cfg["m"],
                            "iterations": cfg["T"], "nn": "voxel grid (exact), one persistent launch per step",
-                           "autotuned": {"cell_factor": tuned[0], "points_per_item": tuned[1]},
+                           "autotuned": {"cell_factor": tuned[0], "points_per_item": tuned[1], "cta_threads": tuned[2]},
                            "l2": "256 MB buffer written between timed steps (outside the events)"},
                 "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},

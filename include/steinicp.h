@@ -207,17 +207,21 @@ int sicp_register_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, cons
 
 /* Autotuner of the batched path (no counterpart in the paper): times
  * trial_iters iterations of the persistent kernel for each candidate grid
- * cell-size factor (0.35, 0.5, 0.7, 1.0 times the volumetric point spacing)
- * and minibatch entries per work item (2, 4, 8) on the given batch, keeps the
- * fastest on the context for later sicp_register_batched calls, and returns
- * it.  With cache_path (may be NULL) the choice is read from / written to a
- * small JSON file keyed by GPU name, problem count, mean reference size and
- * m.  Arguments otherwise as sicp_register_batched. */
+ * cell-size factor (0.35, 0.5, 0.7, 1.0 times the volumetric point spacing),
+ * minibatch entries per work item (2, 4, 8) and CTA shape (1024 threads per
+ * CTA, one CTA per SM, with the Stein phase's pair distances kept in shared
+ * memory; or 512 or 256 threads, three or six CTAs per SM, without that
+ * cache) on the given batch, keeps the fastest on the context for later
+ * sicp_register_batched calls, and returns it (out_cta_threads: threads per
+ * CTA; any out pointer may be NULL).  With cache_path (may be NULL) the
+ * choice is read from / written to a small JSON file keyed by GPU name,
+ * problem count, mean reference size and m.  Arguments otherwise as
+ * sicp_register_batched. */
 int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, const float* ref_xyz,
                           const int64_t* src_off, const float* src_xyz, const int32_t* part_off,
                           const float* particles_in, const sicp_params* p, int32_t trial_iters,
                           const char* cache_path, float* out_cell_factor, int32_t* out_points_per_item,
-                          int on_device);
+                          int32_t* out_cta_threads, int on_device);
 
 /* Trace of one iteration of a batched run, for checking the persistent
  * kernel step by step against a plain implementation (no counterpart in the

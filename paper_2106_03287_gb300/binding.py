@@ -98,7 +98,7 @@ def lib() -> ctypes.CDLL:
             "sicp_profile": (ctypes.c_int, [P, ctypes.c_int, P]),
             "sicp_icp_grad_noalloc": (ctypes.c_int, [P, I64, P, I64, P, I32, P, I32, P, P]),
             "sicp_register_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, P, P, P, ctypes.c_int]),
-            "sicp_autotune_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, I32, ctypes.c_char_p, P, P,
+            "sicp_autotune_batched": (ctypes.c_int, [P, I32, P, P, P, P, P, P, pp, I32, ctypes.c_char_p, P, P, P,
                                                      ctypes.c_int]),
             "sicp_surrogate_train": (ctypes.c_int, [P, I64, U64, I32, I32, F32, P]),
             "sicp_surrogate_params": (ctypes.c_int, [P, ctypes.c_int, P, P]),
@@ -636,16 +636,17 @@ def sicp_read_batched_trace(ctx, Ktot: int, m: int):
 
 
 def sicp_autotune_batched(ctx, problems, params: sicp_params, trial_iters: int = 5, cache_path=None):
-    """Pick and keep the fastest (cell-size factor, minibatch entries per work item)."""
+    """Pick and keep the fastest (cell-size factor, minibatch entries per work item, CTA threads)."""
     b = problems if isinstance(problems, dict) else pack_batch(problems)
     ref, src, par, ref_off, src_off, part_off, dev = (b["ref"], b["src"], b["par"], b["ref_off"], b["src_off"],
                                                       b["part_off"], b["dev"])
     f = ctypes.c_float()
     k = ctypes.c_int32()
+    t = ctypes.c_int32()
     _check(ctx, lib().sicp_autotune_batched(ctx, len(ref_off) - 1, ref_off.ctypes.data_as(ctypes.c_void_p),
                                             _ptr(ref, np.float32), src_off.ctypes.data_as(ctypes.c_void_p),
                                             _ptr(src, np.float32), part_off.ctypes.data_as(ctypes.c_void_p),
                                             _ptr(par, np.float32), ctypes.byref(params), trial_iters,
                                             cache_path.encode() if cache_path else None, ctypes.byref(f),
-                                            ctypes.byref(k), dev))
-    return f.value, k.value
+                                            ctypes.byref(k), ctypes.byref(t), dev))
+    return f.value, k.value, t.value

@@ -253,6 +253,7 @@ SteinArgs stein_args(const sicp_params& p, float* theta, float* am, float* av, c
     a.gen = 0;
     a.max_spins = 0;
     a.extra = 0;
+    a.cache = 1;
     return a;
 }
 

@@ -363,6 +363,8 @@ struct SteinArgs {
     // (extra = 1 only in the failure-detection check, where the wait must give up)
     long long max_spins;
     uint32_t extra;
+    // single-CTA form: keep the pair distances in shared memory when they fit (1) or never (0)
+    int32_t cache;
 };
 cudaError_t launch_stein_adam(const SteinArgs& a, cudaStream_t s);
 // Independent runs (no Stein coupling): Adam on g = -G_j for every particle j,

@@ -49,7 +49,11 @@ namespace {
 
 using namespace gs;
 
-constexpr int kPersistThreads = 1024;
+// CTA shapes of the persistent kernel the autotuner chooses from: 1024 threads, one CTA per SM, with
+// the Stein phase's pair distances kept in shared memory; or 512 x 3 / 256 x 6 per SM without that
+// cache (48 warps per SM for the search phase, the Stein phase recomputing the distances).
+constexpr int kShapes = 3;
+constexpr int kShapeThreads[kShapes] = {1024, 512, 256};
 constexpr long long kMaxSpins = 1ll << 27;   // ~10 s of 64 ns polls
 
 // Largest p with off[p] <= i, for off[0] = 0 <= i < off[P].
@@ -237,6 +241,7 @@ struct BatchArgs {
     int trace_t;
     float *tr_theta, *tr_am, *tr_av, *tr_gbar, *tr_phi;
     int32_t* tr_nn;
+    int cache;                           // Stein phase: pair distances in shared memory (1) or not (0)
     long long max_spins;                 // polls of a barrier wait before it gives up (0: kMaxSpins)
     unsigned extra;                      // arrivals a barrier waits for beyond the grid's CTAs (1 only in
                                          // the failure-detection check, where every wait must give up)
@@ -270,10 +275,11 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long max_spins, unsig
     return *(volatile int*)err == 0;
 }
 
-__global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b) {
-    __shared__ Pose P[kPersistThreads / 32];
+template <int kThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) kb_persistent(BatchArgs b) {
+    __shared__ Pose P[kThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (kPersistThreads / 32);
+    const int64_t W = (int64_t)gridDim.x * (kThreads / 32);
     for (int t = 0; t < b.T; ++t) {
         const bool tr = t == b.trace_t;
         if (tr) {   // the state this iteration starts from (theta changes only after the barrier)
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
             }
         }
         // gradient phase: one warp per item, items interleaved over the whole grid
-        for (int64_t it = (int64_t)blockIdx.x * (kPersistThreads / 32) + warp; it < b.total_items; it += W) {
+        for (int64_t it = (int64_t)blockIdx.x * (kThreads / 32) + warp; it < b.total_items; it += W) {
             const int p = find_problem(b.item_off, b.P, it);
             const int K = b.part_off[p + 1] - b.part_off[p];
             const int64_t r = it - b.item_off[p];
@@ -355,6 +361,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) kb_persistent(BatchArgs b)
             a.gen = 0;
             a.max_spins = 0;
             a.extra = 0;
+            a.cache = b.cache;
             sd::stein_adam_block(a);
             __syncthreads();
         }
@@ -422,6 +429,7 @@ struct BatchState {
     std::vector<unsigned char> key;
     float cell_factor = 0.5f;
     int kkc = 4;
+    int shape = 0;                       // index into kShapeThreads
     int grid_ctas = 0;
     size_t smem = 0;
     // trace of one iteration (sicp_trace_batched): armed iteration, and what the last run recorded
@@ -604,7 +612,7 @@ int check_batch(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p) {
 // Upload, build and (optionally) run T iterations; elapsed_ms (if not NULL)
 // receives the persistent kernel's time measured with CUDA events.
 int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int on_device, float factor, int kkc,
-                bool use_graph, float* particles_out, double* mean6, double* cov36, float* elapsed_ms) {
+                int shape_ix, bool use_graph, float* particles_out, double* mean6, double* cov36, float* elapsed_ms) {
     BatchState& B = *ctx->batch;
     cudaStream_t s = ctx->stream;
     const int P = in.P;
@@ -660,12 +668,19 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
     SICP_CUDA(cudaMemsetAsync(B.av.p, 0, sizeof(float) * 6 * Ktot, s));
     if ((rc = build_batched(ctx, B, P, ro, factor))) return rc;
 
-    // the persistent kernel's configuration: one 1024-thread CTA per SM
+    // the persistent kernel's CTA shape (autotuned): 1024 threads with the Stein pair cache, or
+    // 512 / 256 threads without it
+    const int shape = shape_ix < 0 || shape_ix >= kShapes ? 0 : shape_ix;
+    const int threads = kShapeThreads[shape];
+    const bool cache = shape == 0;
+    void (*kern)(BatchArgs) = shape == 0 ? kb_persistent<1024, 1> : shape == 1 ? kb_persistent<512, 3>
+                                                                                 : kb_persistent<256, 6>;
     const size_t pairs = (size_t)maxK * (maxK - 1) / 2;
-    const size_t smem = sizeof(float) * (18 * (size_t)maxK + (2 * pairs <= (size_t)sd::kCacheFloats ? 2 * pairs : 0));
-    SICP_CUDA(cudaFuncSetAttribute(kb_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem =
+        sizeof(float) * (18 * (size_t)maxK + (cache && 2 * pairs <= (size_t)sd::kCacheFloats ? 2 * pairs : 0));
+    SICP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SICP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_persistent, kPersistThreads, smem));
+    SICP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return set_err(ctx, SICP_ECUDA, "persistent kernel does not fit on an SM (smem %zu)", smem);
     const int ctas = per_sm * ctx->num_sms;
 
@@ -698,6 +713,7 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
         a.kappa[q] = p.prior_kappa[q];
     }
     a.bar = (unsigned*)B.bar.p;
+    a.cache = cache ? 1 : 0;
     a.trace_t = -1;
     const bool tracing = B.trace_t >= 0 && B.trace_t < p.T && !elapsed_ms;
     if (tracing) {
@@ -734,7 +750,7 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
         if (p.T > 0) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(ctas);
-            cfg.blockDim = dim3(kPersistThreads);
+            cfg.blockDim = dim3(threads);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
             cudaLaunchAttribute attr[1];
@@ -742,7 +758,7 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            SICP_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent, a));
+            SICP_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
         }
         kb_moments<<<P, 64, 0, s>>>((const float*)B.theta.p, (const int32_t*)B.part_off.p, (double*)B.moments.p);
         SICP_CUDA(cudaGetLastError());
@@ -750,12 +766,13 @@ int run_batched(sicp_ctx* ctx, const BatchInputs& in, const sicp_params& p, int 
     };
     if (e0) SICP_CUDA(cudaEventRecord(e0, s));
     if (use_graph) {
-        std::vector<unsigned char> key(sizeof(BatchArgs) + sizeof(int) * 2 + sizeof(uint64_t));
+        std::vector<unsigned char> key(sizeof(BatchArgs) + sizeof(int) * 3 + sizeof(uint64_t));
         memcpy(key.data(), &a, sizeof(BatchArgs));
         memcpy(key.data() + sizeof(BatchArgs), &ctas, sizeof(int));
         const int sm_i = (int)smem;
         memcpy(key.data() + sizeof(BatchArgs) + sizeof(int), &sm_i, sizeof(int));
-        memcpy(key.data() + sizeof(BatchArgs) + 2 * sizeof(int), &p.seed, sizeof(uint64_t));
+        memcpy(key.data() + sizeof(BatchArgs) + 2 * sizeof(int), &threads, sizeof(int));
+        memcpy(key.data() + sizeof(BatchArgs) + 3 * sizeof(int), &p.seed, sizeof(uint64_t));
         if (!(B.graph_valid && B.key == key)) {
             if (B.exec) cudaGraphExecDestroy(B.exec);
             B.exec = nullptr;
@@ -824,9 +841,9 @@ std::string gpu_name(int dev) {
     return prop.name;
 }
 
-// Cache file: one line per entry, `"key": [cell_factor, points_per_item],`
-// inside a JSON object.
-bool cache_lookup(const char* path, const std::string& key, float* f, int* k) {
+// Cache file: one line per entry, `"key": [cell_factor, points_per_item, shape],`
+// inside a JSON object (shape: index of the CTA shape, 1024 / 512 / 256 threads).
+bool cache_lookup(const char* path, const std::string& key, float* f, int* k, int* sh) {
     if (!path) return false;
     FILE* fp = fopen(path, "r");
     if (!fp) return false;
@@ -837,13 +854,13 @@ bool cache_lookup(const char* path, const std::string& key, float* f, int* k) {
         const char* at = strstr(line, needle.c_str());
         if (!at) continue;
         const char* br = strchr(at + needle.size(), '[');
-        if (br && sscanf(br, "[%f, %d]", f, k) == 2) found = true;
+        if (br && sscanf(br, "[%f, %d, %d]", f, k, sh) == 3) found = true;
     }
     fclose(fp);
     return found;
 }
 
-void cache_store(const char* path, const std::string& key, float f, int k) {
+void cache_store(const char* path, const std::string& key, float f, int k, int sh) {
     if (!path) return;
     std::vector<std::string> lines;
     FILE* fp = fopen(path, "r");
@@ -860,7 +877,7 @@ void cache_store(const char* path, const std::string& key, float f, int k) {
         fclose(fp);
     }
     char buf[512];
-    snprintf(buf, sizeof buf, "  %s: [%.3f, %d]", needle.c_str(), f, k);
+    snprintf(buf, sizeof buf, "  %s: [%.3f, %d, %d]", needle.c_str(), f, k, sh);
     lines.push_back(buf);
     fp = fopen(path, "w");
     if (!fp) return;
@@ -919,15 +936,15 @@ extern "C" int sicp_register_batched(sicp_ctx* ctx, int32_t P, const int64_t* re
     DeviceScopeB ds(ctx->device);
     if (!ctx->batch) ctx->batch = new BatchState();
     const bool graph = getenv("SICP_NO_GRAPH") == nullptr;
-    return run_batched(ctx, in, p, on_device, ctx->batch->cell_factor, ctx->batch->kkc, graph, particles_out, mean6,
-                       cov36, nullptr);
+    return run_batched(ctx, in, p, on_device, ctx->batch->cell_factor, ctx->batch->kkc, ctx->batch->shape, graph,
+                       particles_out, mean6, cov36, nullptr);
 }
 
 extern "C" int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* ref_off, const float* ref_xyz,
                                      const int64_t* src_off, const float* src_xyz, const int32_t* part_off,
                                      const float* particles_in, const sicp_params* p_in, int32_t trial_iters,
                                      const char* cache_path, float* out_cell_factor, int32_t* out_points_per_item,
-                                     int on_device) {
+                                     int32_t* out_cta_threads, int on_device) {
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!p_in || trial_iters < 1) return set_err(ctx, SICP_EINVAL, "autotune needs params and trial_iters >= 1");
@@ -944,31 +961,35 @@ extern "C" int sicp_autotune_batched(sicp_ctx* ctx, int32_t P, const int64_t* re
              (int)lround(log2(fmax(meanM, 1.0))), p.m);
     const std::string key(keybuf);
     float f = 0.f;
-    int k = 0;
-    if (cache_lookup(cache_path, key, &f, &k) && f > 0.f && k > 0) {
+    int k = 0, sh = 0;
+    if (cache_lookup(cache_path, key, &f, &k, &sh) && f > 0.f && k > 0 && sh >= 0 && sh < kShapes) {
         B.cell_factor = f;
         B.kkc = k;
+        B.shape = sh;
     } else {
         p.T = trial_iters;
         const float factors[] = {0.35f, 0.5f, 0.7f, 1.0f};
         const int items[] = {2, 4, 8};
         float best_ms = FLT_MAX;
-        for (float fc : factors)
-            for (int kk : items) {
-                float ms = 0.f;
-                rc = run_batched(ctx, in, p, on_device, fc, kk, false, nullptr, nullptr, nullptr, &ms);
-                if (rc) return rc;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    B.cell_factor = fc;
-                    B.kkc = kk;
+        for (int shape = 0; shape < kShapes; ++shape)
+            for (float fc : factors)
+                for (int kk : items) {
+                    float ms = 0.f;
+                    rc = run_batched(ctx, in, p, on_device, fc, kk, shape, false, nullptr, nullptr, nullptr, &ms);
+                    if (rc) return rc;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        B.cell_factor = fc;
+                        B.kkc = kk;
+                        B.shape = shape;
+                    }
                 }
-            }
-        cache_store(cache_path, key, B.cell_factor, B.kkc);
+        cache_store(cache_path, key, B.cell_factor, B.kkc, B.shape);
     }
     B.graph_valid = false;
     if (out_cell_factor) *out_cell_factor = B.cell_factor;
     if (out_points_per_item) *out_points_per_item = B.kkc;
+    if (out_cta_threads) *out_cta_threads = kShapeThreads[B.shape];
     return SICP_OK;
 }
 

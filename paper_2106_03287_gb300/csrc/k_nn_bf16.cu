@@ -179,6 +179,9 @@ struct BfRef {
     GridView grid;             // the fine grid: where each cell's points start in `sorted`
     const float4* tbox;        // [R][2]: each tile's bounding box (lo, hi)
     const float* amax;         // largest coordinate magnitude of the cloud
+    // query-tile scheduling of a launch: next tile, CTAs done (zero between launches: written as
+    // zeros with the description, and the last CTA of every launch zeroes them again)
+    unsigned long long sched[2];
 };
 
 struct BfArgs {
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     __shared__ uint64_t tfull[2], tnever;
     __shared__ uint32_t tbase;
     __shared__ int s_fail, s_rot, s_T;
+    __shared__ long long s_tile;
     __shared__ float s_red[4][8];
     __shared__ int s_cnt[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
@@ -351,7 +355,12 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         }
     };
 
-    for (int64_t tile = blockIdx.x; tile < ntiles && !skip; tile += gridDim.x) {
+    // query tiles are taken from a counter, so that CTAs that drew cheap tiles (few reference tiles
+    // within reach) take more of them
+    unsigned long long* sched = const_cast<unsigned long long*>(args.ref->sched);
+    if (tid == 0) s_tile = skip ? ntiles : (long long)atomicAdd(sched, 1ull);
+    __syncthreads();
+    for (int64_t tile = s_tile; tile < ntiles && !skip; tile = s_tile) {
         // ---- A operand and the fp32 queries of this tile.  In a registration
         // iteration the rows go minibatch-major (the K particles' images of one
         // source point are neighbours), which keeps a tile's queries close.
@@ -590,12 +599,23 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             }
         }
         N0 += T;
+        if (tid == 0) s_tile = (long long)atomicAdd(sched, 1ull);
         __syncthreads();
         if (s_fail) break;
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    // the last CTA to leave zeroes the counters for the next launch (every CTA's last take of a
+    // tile happened before its own arrival here)
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(sched + 1, 1ull) + 1ull == (unsigned long long)gridDim.x) {
+            sched[0] = 0ull;
+            sched[1] = 0ull;
+            __threadfence();
+        }
+    }
 }
 
 }  // namespace
@@ -638,6 +658,7 @@ int bf16_prepare(sicp_ctx* ctx) {
     h.grid = ctx->grid.v;
     h.tbox = tbox;
     h.amax = (const float*)amax;
+    h.sched[0] = h.sched[1] = 0ull;
     if ((rc = ensure(ctx, ctx->bf16_ref, sizeof(BfRef)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->bf16_ref.p, &h, sizeof(BfRef), cudaMemcpyHostToDevice, ctx->stream));
     ctx->bf16_ready = true;

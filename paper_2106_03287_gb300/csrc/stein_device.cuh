@@ -339,7 +339,7 @@ __device__ __forceinline__ void stein_adam_block(const SteinArgs& a) {
     __shared__ float s_h[2];
     const int K = a.K, tid = threadIdx.x;
     const int pairs = K * (K - 1) / 2;
-    const bool cached = 2 * pairs <= kCacheFloats;
+    const bool cached = a.cache && 2 * pairs <= kCacheFloats;
 
     // G = -N gbar + grad log prior, gbar = inv_m * (sum of the chunk partials)
     if (a.chunks == 1) {

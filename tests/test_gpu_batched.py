@@ -189,15 +189,59 @@ def test_batched_autotune_and_cache(ctx, tmp_path):
     probs = _mixed_problems()
     params = S.sicp_default_params(T=3, m=100, lr=0.01, seed=1, nn_mode=S.SICP_NN_GRID)
     cache = str(tmp_path / "tune.json")
-    f, k = S.sicp_autotune_batched(ctx, probs, params, trial_iters=2, cache_path=cache)
-    assert any(abs(f - c) < 1e-6 for c in (0.35, 0.5, 0.7, 1.0)) and k in (2, 4, 8)
+    f, k, t = S.sicp_autotune_batched(ctx, probs, params, trial_iters=2, cache_path=cache)
+    assert any(abs(f - c) < 1e-6 for c in (0.35, 0.5, 0.7, 1.0)) and k in (2, 4, 8) and t in (1024, 512, 256)
     text = open(cache).read()
     json.loads(text)
-    f2, k2 = S.sicp_autotune_batched(ctx, probs, params, trial_iters=2, cache_path=cache)   # read back
-    assert abs(f2 - f) < 1e-3 and k2 == k
+    f2, k2, t2 = S.sicp_autotune_batched(ctx, probs, params, trial_iters=2, cache_path=cache)   # read back
+    assert abs(f2 - f) < 1e-3 and k2 == k and t2 == t
     parts, _, _ = S.sicp_register_batched(ctx, probs, S.sicp_default_params(T=1, m=100, lr=0.01, seed=40,
                                                                             nn_mode=S.SICP_NN_GRID))
     _one_step_matches_oracle(parts, probs, 100, 40, 0.01)          # still exact with the tuned layout
+
+
+def test_batched_every_cta_shape_matches_oracle(ctx):
+    """The three CTA shapes the autotuner picks from (1024 threads with the
+    Stein pair cache, 512 and 256 without) give the same correspondences,
+    the same gbar bit for bit and the same phi up to the reduction shape: the
+    trace of iteration 0 under each."""
+    probs = _mixed_problems()
+    m, seed = 100, 11
+    Ktot = sum(pr[2].shape[0] for pr in probs)
+    params = S.sicp_default_params(T=1, m=m, lr=0.01, seed=seed, nn_mode=S.SICP_NN_GRID)
+    c2 = S.sicp_create(0)
+    try:
+        traces = []
+        for shape_cache in (1024, 512, 256):
+            # pin the shape through the autotuner's cache file (one entry, this shape)
+            _force_shape(c2, probs, params, shape_cache)
+            S.sicp_trace_batched(c2, 0)
+            S.sicp_register_batched(c2, probs, params)
+            traces.append(S.sicp_read_batched_trace(c2, Ktot, m))
+        for tr in traces[1:]:
+            assert np.array_equal(tr["nn"], traces[0]["nn"])
+            assert np.array_equal(tr["gbar"], traces[0]["gbar"])    # same search, same chunk sums
+            scale = np.maximum(np.abs(traces[0]["phi"]).max(1, keepdims=True), 1e-30)
+            assert np.all(np.abs(tr["phi"] - traces[0]["phi"]) <= 1e-5 * scale)   # other reduction shape
+    finally:
+        S.sicp_destroy(c2)
+
+
+def _force_shape(ctx, probs, params, threads):
+    import tempfile
+    shape = {1024: 0, 512: 1, 256: 2}[threads]
+    meanM = sum(pr[0].shape[0] for pr in probs) / len(probs)
+    import torch as _t
+    name = _t.cuda.get_device_name(0)
+    key = f"{name}|P={len(probs)}|M~2^{int(round(math.log2(max(meanM, 1.0))))}|m={params.m}"
+    fd, path = tempfile.mkstemp(suffix=".json")
+    with os.fdopen(fd, "w") as f:
+        f.write("{\n  " + json.dumps(key) + f": [0.500, 4, {shape}]\n}}\n")
+    try:
+        f_, k_, t_ = S.sicp_autotune_batched(ctx, probs, params, trial_iters=1, cache_path=path)
+        assert t_ == threads and k_ == 4
+    finally:
+        os.unlink(path)
 
 
 def test_batched_errors(ctx):
