@@ -211,43 +211,41 @@ def ncu_traffic_per_query():
 
 def cpu_baseline(d, cfg, budget_s=10.0, metric="point", single_budget_s=5.0):
     """The oracle as it stands, on a bounded number of iterations of the same workload
-    (point-to-plane: the reference normals are computed before the timed sample)."""
+    (point-to-plane: the reference normals are computed before the timed sample): on all
+    host threads, then the same iterations again on one thread."""
     import oracle as O
     ref, src = d["ref"], d["src"]
-    th = d["particles"].astype(np.float64).copy()
-    mom, vel = np.zeros_like(th), np.zeros_like(th)
     normals = O.normals(ref, NORMAL_K)[0] if metric == "plane" else None
     t0 = time.perf_counter()
     tree = O.KDTree(ref)
     build_s = time.perf_counter() - t0
     p = O.Params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, normals=normals, tree=tree)
-    K = th.shape[0]
-    t0 = time.perf_counter()
-    O.step(ref, src, th, mom, vel, p, 0)
-    first = time.perf_counter() - t0
-    n = max(1, min(cfg["T"] - 1, int(budget_s / max(first, 1e-6))))
-    t0 = time.perf_counter()
-    for t in range(1, 1 + n):
-        O.step(ref, src, th, mom, vel, p, t)
-    dt = time.perf_counter() - t0
+    K = d["particles"].shape[0]
+
+    def sample(budget, first):
+        th = d["particles"].astype(np.float64).copy()
+        mom, vel = np.zeros_like(th), np.zeros_like(th)
+        O.step(ref, src, th, mom, vel, p, 0)   # untimed first iteration
+        t0 = time.perf_counter()
+        n = 0
+        while n < min(cfg["T"] - 1, first) and (n == 0 or time.perf_counter() - t0 < budget):
+            n += 1
+            O.step(ref, src, th, mom, vel, p, n)
+        return n, time.perf_counter() - t0
+
     cores = O.num_threads()
+    n, dt = sample(budget_s, cfg["T"])
     out = {"value": K * cfg["m"] * n / dt, "unit": "particle_point_evals/s", "cores": cores,
            "kind": "oracle",
            "sample": f"{n} SVGD iterations (iterations 1..{n}) of the same workload, FP64, exact k-d tree search "
                      f"(tree built once in {build_s * 1e3:.0f} ms, not timed), {dt:.1f} s", "iters_per_sec": n / dt}
-    # the same oracle on one thread, for the next few iterations (a shorter bounded sample)
-    n1 = min(cfg["T"] - 1 - n, max(1, int(single_budget_s * n / max(dt, 1e-6) / max(cores, 1))))
-    if n1 >= 1:
-        O.set_threads(1)
-        try:
-            t0 = time.perf_counter()
-            for t in range(1 + n, 1 + n + n1):
-                O.step(ref, src, th, mom, vel, p, t)
-            dt1 = time.perf_counter() - t0
-        finally:
-            O.set_threads(cores)
-        out["single_thread"] = {"value": K * cfg["m"] * n1 / dt1, "cores": 1,
-                                "sample": f"{n1} SVGD iterations (iterations {1 + n}..{n + n1}), {dt1:.1f} s"}
+    O.set_threads(1)
+    try:
+        n1, dt1 = sample(single_budget_s, n)
+    finally:
+        O.set_threads(cores)
+    out["single_thread"] = {"value": K * cfg["m"] * n1 / dt1, "cores": 1,
+                            "sample": f"{n1} SVGD iterations (iterations 1..{n1}) on one thread, {dt1:.1f} s"}
     return out
 
 

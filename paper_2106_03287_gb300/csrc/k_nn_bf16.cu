@@ -39,8 +39,8 @@
 // same order as before.
 //
 // Pipeline per CTA (one 128-query tile at a time, persistent over tiles, one
-// CTA per SM; the sweep starts at the reference tile holding the grid cell of
-// the tile's first query and wraps around): the 16 warps copy each reference tile (8 KB, precomputed per
+// CTA per SM, query tiles taken from a counter; the sweep starts at the reference tile holding the
+// grid cell of the tile's first query and wraps around): the 16 warps copy each reference tile (8 KB, precomputed per
 // reference cloud in the spatially sorted order of the voxel grid) and its 256
 // fp32 points into a shared-memory ring with asynchronous 16-byte copies,
 // three tiles ahead; thread 0 issues a landed tile's MMA into one of two
@@ -356,9 +356,10 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     };
 
     // query tiles are taken from a counter, so that CTAs that drew cheap tiles (few reference tiles
-    // within reach) take more of them
+    // within reach) take more of them; with no more tiles than CTAs, CTA b takes tile b alone
     unsigned long long* sched = const_cast<unsigned long long*>(args.ref->sched);
-    if (tid == 0) s_tile = skip ? ntiles : (long long)atomicAdd(sched, 1ull);
+    const bool dyn = ntiles > (int64_t)gridDim.x;
+    if (tid == 0) s_tile = skip ? ntiles : dyn ? (long long)atomicAdd(sched, 1ull) : (long long)blockIdx.x;
     __syncthreads();
     for (int64_t tile = s_tile; tile < ntiles && !skip; tile = s_tile) {
         // ---- A operand and the fp32 queries of this tile.  In a registration
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             }
         }
         N0 += T;
-        if (tid == 0) s_tile = (long long)atomicAdd(sched, 1ull);
+        if (tid == 0) s_tile = dyn ? (long long)atomicAdd(sched, 1ull) : ntiles;
         __syncthreads();
         if (s_fail) break;
     }
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
     // the last CTA to leave zeroes the counters for the next launch (every CTA's last take of a
     // tile happened before its own arrival here)
-    if (tid == 0) {
+    if (tid == 0 && dyn) {
         __threadfence();
         if (atomicAdd(sched + 1, 1ull) + 1ull == (unsigned long long)gridDim.x) {
             sched[0] = 0ull;
