@@ -255,7 +255,10 @@ def test_training_learns_the_field(trained):
 
 def test_register_surrogate_matches_exact(trained):
     """C5: 200 iterations, the first 150 on the surrogate; the final particle
-    mean and spread against the all-exact run."""
+    mean and spread against the all-exact run: a sanity bound (5 mm, 0.2
+    deg, spread within 1 cm, both runs within 5 cm of the true pose), not the
+    1 mm / 0.05 deg gate, which the learned field does not meet (see the
+    next test)."""
     c, d, _, _ = trained
     W5 = synth.WORKLOADS["surrogate"]
     res = {}
@@ -273,6 +276,53 @@ def test_register_surrogate_matches_exact(trained):
     assert np.all(np.abs(np.sqrt(np.diag(c_s))[:3] - np.sqrt(np.diag(c_e))[:3]) <= 1e-2)
     # and both are near the true pose
     assert np.linalg.norm(m_s[:3] - d["theta_true"][:3]) < 0.05
+
+
+def test_what_the_learned_field_gains_on_the_kinect_scene(trained):
+    """What the trained network gains over the method without it, on C5
+    (the kinect scene, 200 iterations, the first 150 on the learned field):
+    iterations per second and the final pose mean and spread against the
+    all-exact run, beside the all-exact run's own sensitivity (its particles
+    moved by one float32 ulp), for the field trained on the fixed
+    distribution and on the run's own queries (sicp_surrogate_train_run).
+
+    On this scene the field gains nothing: a learned iteration (three layers
+    per query plus the fallback queries' exact search) costs more device
+    time than an exact grid iteration (measured on a GB300: 0.65-0.67x the
+    all-exact speed), and its final pose lies about as far from the
+    all-exact run as that run's own one-ulp floor or farther (2.96 / 2.97 mm
+    in the mean against a 2.5 mm floor).  The test measures and prints both
+    and holds the code to the speed it measured; a change that made the field
+    pay would fail it and have to be documented."""
+    import time
+    c, d, _, _ = trained
+    W5 = synth.WORKLOADS["surrogate"]
+    from paper_2106_03287_gb300 import gate
+
+    def timed(p, particles, reps=3):
+        out = S.sicp_register(c, d["src"], particles, p)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = S.sicp_register(c, d["src"], particles, p)
+        return out, (time.perf_counter() - t0) / reps
+
+    pe = S.sicp_default_params(T=W5["T"], m=W5["m"], lr=W5["lr"], nn_mode=S.SICP_NN_GRID, seed=5)
+    (_, m_e, c_e), t_e = timed(pe, d["particles"])
+    _, m_u, c_u = S.sicp_register(c, d["src"], np.nextafter(d["particles"], np.float32(np.inf)), pe)
+    floor = gate.pose_errors(m_u, c_u, m_e, c_e)
+    rows = {}
+    for name in ("fixed", "run"):
+        if name == "run":
+            S.sicp_surrogate_train_run(c, d["src"], d["particles"], 1 << 21, seed=3, epochs=10, batch=4096, lr=1e-3)
+        ps = S.sicp_default_params(T=W5["T"], m=W5["m"], lr=W5["lr"], nn_mode=S.SICP_NN_SURROGATE, seed=5,
+                                   surrogate_iters=W5["surrogate_iters"])
+        (_, m_s, c_s), t_s = timed(ps, d["particles"])
+        rows[name] = (t_e / t_s, gate.pose_errors(m_s, c_s, m_e, c_e))
+    print(f"all-exact run {1e3 * t_e:.2f} ms, its one-ulp floor {floor}")
+    for name, (speed, err) in rows.items():
+        print(f"learned field trained on {name} queries: speed {speed:.2f}x the all-exact run, pose errors {err}")
+        assert 0 < speed < 1.0
+        assert np.isfinite(list(err.values())).all()
 
 
 def test_exact_registration_is_independent_of_context_history(trained):
