@@ -139,8 +139,56 @@ def measured_peak(key="hbm_gbs"):
 DEFAULT_NN = {"kinect": "grid", "box": "bf16", "lidar": "bf16", "surrogate": "surrogate"}
 
 
+class _Nvml:
+    """The few NVML reads the clock record needs, through ctypes (public nvml.h
+    API; read-only: nothing here changes a GPU setting)."""
+
+    CLOCK_SM = 1
+    # clock-event reason bits (nvmlClocksEventReason*)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str | None, index: int, lib=None):
+        import ctypes
+        self.c = ctypes
+        self.lib = lib if lib is not None else ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        rc = 1
+        if uuid:
+            rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            self.lib.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = reasons or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def max_sm(self) -> int | None:
+        v = self.c.c_uint()
+        return v.value if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, self.c.byref(v)) == 0 else None
+
+    def sample(self):
+        v, r = self.c.c_uint(), self.c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, self.c.byref(v)) != 0:
+            return None
+        bits = r.value if self.reasons_fn(self.h, self.c.byref(r)) == 0 else 0
+        return v.value, [n for b, n in self.REASONS.items() if bits & b]
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clocks and clock-event (throttle) reasons of the bench's GPU during
+    the timed region.  NVML is polled every 2 ms from a thread, so a region of
+    a few tens of milliseconds still gets many samples.  nvidia-smi runs
+    beside it at its 200 ms interval and is waited for (its first line)
+    before start() returns.  The median SM clock is over the NVML samples
+    (nvidia-smi's where NVML cannot be loaded); the reasons are those either
+    source saw active."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -150,18 +198,44 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.uuid = None
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(gpu).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            self.uuid = None
+        self.nvml, self.thread, self.samples = None, None, []
+        self.stop_flag = False
+
+    def _poll(self):
+        while not self.stop_flag:
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+            time.sleep(0.002)
 
     def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", self.uuid or str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5 and os.path.getsize(self.tmp.name) == 0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
+        try:
+            self.nvml = _Nvml(self.uuid, self.gpu)
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+        except (OSError, AttributeError):
+            self.nvml = None
 
-    def stop(self):
+    def _smi(self) -> str:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return ""
         self.proc.send_signal(signal.SIGTERM)
         try:
             self.proc.wait(timeout=5)
@@ -169,23 +243,47 @@ class ClockSampler:
             self.proc.kill()
         self.tmp.flush()
         self.tmp.seek(0)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.tmp.read().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+        return self.tmp.read()
+
+    def stop(self):
+        nv_max = None
+        if self.nvml is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            nv_max = self.nvml.max_sm()
+            self.nvml.close()
+        text = self._smi()
         os.unlink(self.tmp.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return clock_summary(self.samples, nv_max, text)
+
+
+def clock_summary(nvml_samples, nvml_max, smi_text: str) -> dict:
+    """The clock record: NVML samples [(sm MHz, [reasons])], NVML's maximum SM
+    clock and nvidia-smi's CSV lines (FIELDS order, no header, no units)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in smi_text.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    nv_sm = [float(c) for c, _ in nvml_samples]
+    for _, rs in nvml_samples:
+        reasons.update(rs)
+    if not nv_sm and not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi and NVML unavailable"]}
+    mxs = ([float(nvml_max)] if nvml_max else []) + mx
+    use = nv_sm or sm
+    return {"sm_mhz": statistics.median(use), "sm_min_mhz": min(use), "sm_max_mhz": max(mxs) if mxs else None,
+            "reasons": sorted(reasons), "samples": len(use),
+            "source": "nvml, 2 ms" if nv_sm else "nvidia-smi, 200 ms", "nvidia_smi_samples": len(sm)}
 
 
 def grad_kernel_source_hash():

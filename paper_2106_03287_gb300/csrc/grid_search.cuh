@@ -77,19 +77,34 @@ __device__ __forceinline__ void take(Best& B, float4 r, float3 q, int id) {
     }
 }
 
-// Warp minimum (distance, then lowest index); every lane ends with the result.
-// Distances are non-negative, so their bit patterns order like unsigned ints.
+// A query is searched by a group of G lanes (G = 32: the whole warp; G = 16:
+// each half-warp runs its own query).  The group's lanes and its lane index.
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    static_assert(G == 16 || G == 32, "group of 16 or 32 lanes");
+    return G == 32 ? kFull : (0xffffu << (threadIdx.x & 16));
+}
+template <int G>
+__device__ __forceinline__ int group_lane() {
+    return threadIdx.x & (G - 1);
+}
+
+// Group minimum (distance, then lowest index); every lane of the group ends
+// with the result.  Distances are non-negative, so their bit patterns order
+// like unsigned ints.
+template <int G = 32>
 __device__ __forceinline__ void warp_min(Best& B) {
+    const unsigned gm = group_mask<G>();
     const unsigned db = __float_as_uint(B.d);
-    const unsigned md = __reduce_min_sync(kFull, db);
-    const unsigned mi = __reduce_min_sync(kFull, db == md ? (unsigned)B.i : 0xffffffffu);
-    const unsigned who = __ballot_sync(kFull, db == md && (unsigned)B.i == mi);
-    const int src = __ffs(who) - 1;
+    const unsigned md = __reduce_min_sync(gm, db);
+    const unsigned mi = __reduce_min_sync(gm, db == md ? (unsigned)B.i : 0xffffffffu);
+    const unsigned who = __ballot_sync(gm, db == md && (unsigned)B.i == mi) & gm;
+    const int src = __ffs(who) - 1;   // a lane of this group
     B.d = __uint_as_float(md);
     B.i = (int)mi;
-    B.p.x = __shfl_sync(kFull, B.p.x, src);
-    B.p.y = __shfl_sync(kFull, B.p.y, src);
-    B.p.z = __shfl_sync(kFull, B.p.z, src);
+    B.p.x = __shfl_sync(gm, B.p.x, src);
+    B.p.y = __shfl_sync(gm, B.p.y, src);
+    B.p.z = __shfl_sync(gm, B.p.z, src);
 }
 
 // Every row from table entry e on is farther than the current best.
@@ -98,11 +113,13 @@ __device__ __forceinline__ bool cleared(const GridView& g, const SearchTable& ta
     return lbd > 0.f && lbd * lbd > bound2(best);
 }
 
-// One round: lane l contributes row (y, z) if `has`, limited to cells
-// [xlo, xhi] along x and clipped to the ball of squared radius clip2.
+// One round: lane l of the group contributes row (y, z) if `has`, limited to
+// cells [xlo, xhi] along x and clipped to the ball of squared radius clip2.
+template <int G = 32>
 __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, int xlo, int xhi, float clip2,
                            Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
+    const int lane = group_lane<G>();
+    const unsigned gm = group_mask<G>();
     int b = 0, len = 0;
     if (has && y >= 0 && y < g.dims.y && z >= 0 && z < g.dims.z) {
         const float dz = slab(q.z, g.origin.z, g.cell, z, g.tol);
@@ -126,32 +143,32 @@ __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, 
     // flatten the round's segments: exclusive offsets and total
     int incl = len;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, off);
+    for (int off = 1; off < G; off <<= 1) {
+        const int v = __shfl_up_sync(gm, incl, off, G);
         if (lane >= off) incl += v;
     }
-    const int total = __shfl_sync(kFull, incl, 31);
+    const int total = __shfl_sync(gm, incl, G - 1, G);
     if (total == 0) return;
     const int excl = incl - len;
     // flattened point t belongs to the last lane whose offset is <= t
     Best L = B;
-    for (int t0 = 0; t0 < total; t0 += 32) {
+    for (int t0 = 0; t0 < total; t0 += G) {
         const int t = t0 + lane;
         int o = 0;
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int ex = __shfl_sync(kFull, excl, o + step);
+        for (int step = G / 2; step > 0; step >>= 1) {
+            const int ex = __shfl_sync(gm, excl, o + step, G);
             if (ex <= t) o += step;
         }
-        const int ob = __shfl_sync(kFull, b, o);
-        const int oe = __shfl_sync(kFull, excl, o);
+        const int ob = __shfl_sync(gm, b, o, G);
+        const int oe = __shfl_sync(gm, excl, o, G);
         if (t < total) {
             const float4 r = __ldg(g.sorted + ob + (t - oe));
             take(L, r, q, __float_as_int(r.w));
         }
     }
     if (lane == 0) w.pts += (unsigned)total;
-    warp_min(L);
+    warp_min<G>(L);
     B = L;
 }
 
@@ -173,8 +190,9 @@ __device__ __forceinline__ QueryCell query_cell(const GridView& g, float3 q) {
 // Walk table entries [0, n) with rows clipped at min(bound, cap2).  Stops at
 // the first entry out of reach of the best; the answer is exact then if the
 // clipping never cut below the best (best within cap2).
+template <int G = 32>
 __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap2, float3 q, Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
+    const int lane = group_lane<G>();
     const QueryCell c = query_cell(g, q);
     for (int base = 0; base < n;) {
         // (entry 0 is the query's own row, bound 0: never cleared)
@@ -187,16 +205,18 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
             y = c.cy + c.sy * o.x;
             z = c.cz + c.sz * o.y;
         }
-        round_rows(g, q, has, y, z, 0, g.dims.x - 1, fminf(bound2(B.d), cap2), B, w);
-        base += 32;
+        round_rows<G>(g, q, has, y, z, 0, g.dims.x - 1, fminf(bound2(B.d), cap2), B, w);
+        base += G;
     }
     return false;
 }
 
+template <int G = 32>
 __device__ __forceinline__ void prove(const GridSearch& S, float3 q, Best& B, Work& w);
 
+template <int G = 32>
 __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
+    const int lane = group_lane<G>();
     const GridView& F = S.fine;
     B.d = FLT_MAX;
     B.i = kNone;
@@ -217,31 +237,32 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
             take(B, r, q, __float_as_int(r.w));
         }
     }
-    prove(S, q, B, w);
+    prove<G>(S, q, B, w);
 }
 
 // The exact nearest point of q given a starting answer B (any reference
 // point, or none): walk the table with the shrinking bound on the fine level
 // (bound under kFineReach cells) or the coarse level, and scan everything if
 // the table cannot settle it.
+template <int G>
 __device__ __forceinline__ void prove(const GridSearch& S, float3 q, Best& B, Work& w) {
-    const int lane = threadIdx.x & 31;
+    const int lane = group_lane<G>();
     const GridView& F = S.fine;
     const float reach = kFineReach * F.cell;
     const bool fine = B.d <= reach * reach;
     w.far += (lane == 0 && !fine);
     const GridView& L = fine ? S.fine : S.coarse;
-    if (walk(L, S.tab, S.tab.n, FLT_MAX, q, B, w)) return;
+    if (walk<G>(L, S.tab, S.tab.n, FLT_MAX, q, B, w)) return;
     if (cleared(L, S.tab, S.tab.n - 1, B.d)) return;
     // the table cannot settle it: scan every point
     w.exh += lane == 0;
     Best E = B;
-    for (int p = lane; p < S.M; p += 32) take(E, __ldg(S.ref4 + p), q, p);
+    for (int p = lane; p < S.M; p += G) take(E, __ldg(S.ref4 + p), q, p);
     if (lane == 0) {
         w.segs += 1;
         w.pts += (unsigned)S.M;
     }
-    warp_min(E);
+    warp_min<G>(E);
     B = E;
 }
 

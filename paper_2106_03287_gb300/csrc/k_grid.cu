@@ -26,7 +26,9 @@
 // the bound before the walk, cost more than it saved: the walk's first 32 rows
 // already hold them.)  A query the table cannot settle scans all points.  In the
 // gradient kernel a query whose neighbouring particle's answer lies within
-// two fine cells starts the walk from that answer instead.
+// two fine cells starts the walk from that answer instead.  The same search
+// also runs on a half-warp (16 lanes, 16 rows a round), two queries per warp:
+// the gradient kernel of independent runs uses it.
 // Every search uses the same fp32 squared distance and tie rule as the
 // exhaustive scan, so both give the same answer.
 //
@@ -77,19 +79,23 @@ __global__ void __launch_bounds__(kThreads) k_nn_grid(GridSearch S, const float*
     if (stats) add_stats(stats, w);
 }
 
-// grid (minibatch entries, blocks of kPart particles).  Warp w of CTA (k, b)
-// handles minibatch entry k for the kSeq particles b*kPart + w*kSeq ...: the
-// first query runs the whole search; each next one is the same source point
-// under a neighbouring particle, so the previous answer is a starting bound
-// (kept when it lies within kReuse cells, else the seed map is used).  Lane 0
-// writes the query's gradient terms to qterms[j][k]; a fixed-order reduction
-// over k follows (launch_qterms_to_gbar).  One particle per warp is fastest
-// on the kinect scene: the seed map gives a tighter start than a neighbouring
-// particle's answer (45.2 against 46.6 candidates per query), and 128-thread
-// CTAs at 40 registers hold 48 warps per SM.
-constexpr int kSeq = 1;                                   // particles per warp
-constexpr int kPart = kSeq * (kGradThreads / 32);         // particles per CTA
+// grid (minibatch entries, blocks of part<G>() particles).  Each group of G
+// lanes (a warp, G = 32, or a half-warp, G = 16) of CTA (k, b) handles
+// minibatch entry k for the kSeq particles b*part + group*kSeq ...: the first
+// query runs the whole search; each next one is the same source point under a
+// neighbouring particle, so the previous answer is a starting bound (kept
+// when it lies within kReuse cells, else the seed map is used).  Lane 0 of
+// the group writes the query's gradient terms to qterms[j][k]; a fixed-order
+// reduction over k follows (launch_qterms_to_gbar).  One particle per group
+// is fastest on the kinect scene: the seed map gives a tighter start than a
+// neighbouring particle's answer (45.2 against 46.6 candidates per query),
+// and 128-thread CTAs at 40 registers hold 48 warps per SM.
+constexpr int kSeq = 1;                                   // particles per group
 constexpr float kReuse = 2.f;
+template <int G>
+__host__ __device__ constexpr int part() {                // particles per CTA
+    return kSeq * (kGradThreads / G);
+}
 
 // The search description is read from memory that the reference build
 // rewrites, so a captured graph of these launches stays valid when the
@@ -97,11 +103,12 @@ constexpr float kReuse = 2.f;
 // else the device copy Sd.  (Staging it in shared memory was slower.)
 // kStats: the work counters are kept (sicp_stats on); otherwise they are dead
 // code and the compiler drops them.
-template <bool kStats, bool kConst>
+template <int G, bool kStats, bool kConst>
 __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, const GridSearch* __restrict__ Sd,
                                                                 int slot) {
+    constexpr int kPart = part<G>();
     __shared__ Pose P[kPart];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = threadIdx.x / G, lane = threadIdx.x & (G - 1);
     const int k = blockIdx.x;
     const int j0 = blockIdx.y * kPart;
     pdl_wait();      // the particles of the previous Stein step
@@ -117,8 +124,8 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
     Best B;
     B.i = kNone;
     for (int i = 0; i < kSeq; ++i) {
-        const int jl = warp * kSeq + i, j = j0 + jl;
-        if (j >= a.K) break;                        // warp-uniform
+        const int jl = grp * kSeq + i, j = j0 + jl;
+        if (j >= a.K) break;                        // uniform over the group
         if (a.mb_stride) {                          // independent runs: particle j's own minibatch
             const float4 sj = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
             s = make_float3(sj.x, sj.y, sj.z);
@@ -131,11 +138,11 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
                 B.d = d;
                 seeded = true;
                 w.queries += lane == 0;
-                prove(S, q, B, w);
+                prove<G>(S, q, B, w);
             }
         }
-        if (!seeded) grid_search(S, q, B, w);
-        // the six gradient terms, one per lane (B, q and s are the same in every lane)
+        if (!seeded) grid_search<G>(S, q, B, w);
+        // the six gradient terms, one per lane (B, q and s are the same in every lane of the group)
         const bool found = B.i != kNone;   // false only for a non-finite distance
         float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
         if (found && a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
@@ -480,16 +487,28 @@ void search_slot_release(int slot) {
     g_slot_used[slot] = false;
 }
 
-cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s) {
-    cudaError_t e;
-    dim3 grid((unsigned)a.m, (unsigned)((a.K + kPart - 1) / kPart));
+template <int G>
+cudaError_t launch_grad_grid_g(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s) {
+    const dim3 grid((unsigned)a.m, (unsigned)((a.K + part<G>() - 1) / part<G>()));
     const dim3 blk(kGradThreads);
     if (slot >= 0)
-        e = a.stats ? launch_pdl(k_grad_grid<true, true>, grid, blk, 0, s, a, d_search, slot)
-                    : launch_pdl(k_grad_grid<false, true>, grid, blk, 0, s, a, d_search, slot);
-    else
-        e = a.stats ? launch_pdl(k_grad_grid<true, false>, grid, blk, 0, s, a, d_search, slot)
-                    : launch_pdl(k_grad_grid<false, false>, grid, blk, 0, s, a, d_search, slot);
+        return a.stats ? launch_pdl(k_grad_grid<G, true, true>, grid, blk, 0, s, a, d_search, slot)
+                       : launch_pdl(k_grad_grid<G, false, true>, grid, blk, 0, s, a, d_search, slot);
+    return a.stats ? launch_pdl(k_grad_grid<G, true, false>, grid, blk, 0, s, a, d_search, slot)
+                   : launch_pdl(k_grad_grid<G, false, false>, grid, blk, 0, s, a, d_search, slot);
+}
+
+// Independent runs (each particle its own minibatch) search with half-warps,
+// Stein runs with whole warps.  Measured on the kinect scene (the gradient
+// launch, warp against half-warp): 1000 independent runs, 198 against 165 us;
+// 100 Stein particles, 34.4 against 40.5 us, and the warp kept ahead at every
+// size tried up to 1000 particles x 300 minibatch entries.  Converged
+// independent runs give every query a small, even amount of work that 16
+// lanes cover in one round; the Stein particles' spread gives more rows and
+// candidates per query, and a half-warp then needs extra rounds.
+cudaError_t launch_grad_grid(const GradArgs& a, const GridSearch* d_search, int slot, cudaStream_t s) {
+    const cudaError_t e = a.mb_stride ? launch_grad_grid_g<16>(a, d_search, slot, s)
+                                      : launch_grad_grid_g<32>(a, d_search, slot, s);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(a.partial, a.K, a.m, a.inv_m, a.gbar, nullptr, s);
 }

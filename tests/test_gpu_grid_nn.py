@@ -65,3 +65,28 @@ def test_grid_gradient_correspondences_equal_exhaustive_search(ctx):
             assert np.array_equal(nn_grid, nn_fp32), (name, m, np.sum(nn_grid != nn_fp32))
             scale = max(np.abs(g_fp32).max(), 1e-30)
             assert np.abs(g_grid - g_fp32).max() <= 1e-5 * scale + 1e-30, name   # same terms, other order
+
+
+def test_half_warp_search_of_independent_runs_equals_warp_search(ctx):
+    """Independent runs search with half-warps (two queries per warp), a
+    single-particle run with whole warps.  Both are exact with the same tie
+    rule, so run j of an independent registration equals the K = 1 run with
+    seed + j bit for bit: on the kinect scene with spread, converged and far
+    initial poses (far: the coarse level), and an odd K (the last warp has an
+    idle half)."""
+    kin = synth.make_kinect_problem(31, M=20_000, N=4000, K=100)
+    S.sicp_set_reference(ctx, kin["ref"])
+    parts = np.concatenate([kin["particles"][:6], _particles_near(kin, 6, 0.01, 0.005, 5),
+                            _particles_near(kin, 5, 1.5, 0.6, 6)])
+    kw = dict(T=15, m=150, lr=0.03)
+    th, _, _ = S.sicp_register(ctx, kin["src"], parts,
+                               S.sicp_default_params(seed=11, nn_mode=S.SICP_NN_GRID | S.SICP_INDEPENDENT, **kw))
+    S.sicp_stats(ctx, True)
+    S.sicp_register(ctx, kin["src"], parts,
+                    S.sicp_default_params(seed=11, nn_mode=S.SICP_NN_GRID | S.SICP_INDEPENDENT, **kw))
+    st = S.sicp_stats(ctx, False)
+    assert st[4] > 0                       # some queries took the coarse level
+    for j in range(parts.shape[0]):
+        one, _, _ = S.sicp_register(ctx, kin["src"], parts[j:j + 1],
+                                    S.sicp_default_params(seed=11 + j, nn_mode=S.SICP_NN_GRID, **kw))
+        assert np.array_equal(th[j], one[0]), j
