@@ -294,9 +294,9 @@ def grad_kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_query():
-    """DRAM bytes per query of the gradient kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def ncu_grad_record():
+    """The committed ncu summary of the gradient kernel (DRAM and L2 bytes of
+    one launch), if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "k_grad_grid_kinect.json")
     if not os.path.exists(path):
         return None
@@ -304,7 +304,37 @@ def ncu_traffic_per_query():
         rec = json.load(f)
     if rec.get("source_hash") != grad_kernel_source_hash():
         return None
-    return rec["dram_bytes"] / rec["queries"]
+    return rec
+
+
+def measure_l2_gbs(torch, sizes_mb=(4, 8, 16, 24), reps=50):
+    """Bandwidth of a copy whose source and destination stay in the 129 MB
+    L2: bytes read plus written per second, CUDA events around one graph of
+    `reps` back-to-back copies after a warm-up; the best over buffer sizes
+    (MB per buffer).  Returns (GB/s, size in MB)."""
+    best = (0.0, 0)
+    for mb in sizes_mb:
+        n = mb * (1 << 20) // 4
+        a = torch.ones(n, dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        for _ in range(10):
+            b.copy_(a)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()   # one graph of `reps` copies: no host launch gaps between them
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                b.copy_(a)
+        g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gbs = 2.0 * n * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        best = max(best, (gbs, mb))
+        del g, a, b
+    return best
 
 
 def cpu_baseline(d, cfg, budget_s=10.0, metric="point", single_budget_s=5.0):
@@ -520,7 +550,11 @@ def run_ours(args):
         peak, peak_kind = measured_peak()
         alg_bytes = bytes_per_query * queries_per_launch
         achieved = alg_bytes / (grad_ms * 1e-3) / 1e9 if grad_ms else None
-        tpq = ncu_traffic_per_query()
+        rec = ncu_grad_record()
+        tpq = rec["dram_bytes"] / rec["queries"] if rec else None
+        l2pq = rec["lts_bytes"] / rec["queries"] if rec and "lts_bytes" in rec else None
+        l2_gbs, l2_mb = measure_l2_gbs(torch)
+        l2_achieved = l2pq * queries_per_launch / (grad_ms * 1e-3) / 1e9 if l2pq and grad_ms else None
         roofline = {"kernel": "k_grad_grid (transform + grid NN + gradient, one iteration)"
                               + (", point-to-plane" if plane else ""), "bound": "hbm",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "peak_kind": f"{peak_kind} copy bandwidth",
@@ -530,6 +564,12 @@ def run_ours(args):
                     "launches_timed": int(prof[1]),
                     "per_query": {"rows": rows_q, "segments": segs_q, "candidates": pts_q, "bytes": bytes_per_query,
                                   "far_frac": coarse_frac, "exhaustive_frac": exhaustive_frac},
+                    "l2": {"bytes_per_launch": l2pq * queries_per_launch if l2pq else None,
+                           "achieved": l2_achieved, "peak": l2_gbs, "unit": "GB/s",
+                           "peak_kind": f"measured L2-resident copy (2 x {l2_mb} MB, read + write; "
+                                        "best of 4-24 MB buffers)",
+                           "frac": l2_achieved / l2_gbs if l2_achieved else None,
+                           "bytes_source": "lts__t_sectors.sum x 32 B of the committed ncu capture"},
                     "stein_adam_avg_launch_us": stein_us}
     elif nn == "bf16":
         peak, peak_kind = measured_peak("bf16_tflops")

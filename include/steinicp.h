@@ -506,6 +506,35 @@ int sicp_stats(sicp_ctx* ctx, int enable, uint64_t* out10);
  * Synchronises the context's stream. */
 int sicp_profile(sicp_ctx* ctx, int stride, double* out4);
 
+/* Per-iteration telemetry (no counterpart in the paper).  With on = 1 every
+ * later registration run of the context (sicp_register,
+ * sicp_register_continue, sicp_resume; not the batched path) records one row
+ * of 16 float32 per iteration t, kept on the device until the next run:
+ *   [0..5]   mean of the six pose parameters of the particles the iteration
+ *            starts from (the arithmetic mean, as sicp_moments),
+ *   [6..11]  their standard deviations (divisor K-1; 0 for K = 1),
+ *   [12]     mean Euclidean distance from the iteration's K m transformed
+ *            minibatch points to their correspondences (Eq.
+ *            correspondences; in iterations on the learned field, the
+ *            residual the field or its exact fallback gave),
+ *   [13]     share of the iteration's queries the learned field answered
+ *            (0 in exact iterations),
+ *   [14]     the iteration's absolute index (t0 + t),
+ *   [15]     share of the queries that had a correspondence (1 unless a
+ *            transformed point was non-finite).
+ * It adds two small launches per iteration (sicp_profile's Stein times
+ * include them) and the exact searches' correspondence writes; the run's
+ * results are unchanged, bit for bit.  on = 0 turns it off.  Errors:
+ * SICP_EINVAL (null ctx). */
+int sicp_set_telemetry(sicp_ctx* ctx, int on);
+
+/* Copies at most max_rows rows of the last run's telemetry to out
+ * [rows][16] float32 (host memory); *rows (may be NULL) receives the number
+ * of rows that run recorded: its T, or 0 when telemetry was off or the run
+ * did not finish.  Errors: SICP_EINVAL (max_rows < 0, or out NULL with
+ * max_rows > 0). */
+int sicp_read_telemetry(sicp_ctx* ctx, float* out, int32_t max_rows, int32_t* rows);
+
 /* ---- resource limits and failure detection (no counterpart in the paper) ---- */
 
 /* Device memory budget of a context: from now on an allocation that would
@@ -533,6 +562,21 @@ int sicp_set_memory_limit(sicp_ctx* ctx, size_t bytes, size_t* held);
  * operation; polls then still caps the waits (0: the defaults).  Errors:
  * SICP_EINVAL (polls outside [0, 2^30]). */
 int sicp_set_wait_check(sicp_ctx* ctx, int on, int64_t polls);
+
+/* Index checks of the bounds-checked build (no counterpart in the paper).
+ * The library built with SICP_CHECKED checks every index that comes from
+ * data (cell coordinates, the seed map, cell bounds, the row table, minibatch
+ * entries, search results, fallback lists, batched work items) before its
+ * access; an index outside its buffer is recorded and replaced by 0, so the
+ * access stays inside the buffer.  *checked (may be NULL) receives 1 for
+ * that build and 0 for the normal one; *first (may be NULL) the first failed
+ * check since the last call, 0 if none, else bit 63 | site << 40 | the low
+ * 40 bits of the index (sites: 1 query cell, 2 seed point, 3 cell bounds,
+ * 4 candidate point, 5 row table, 6 source point, 7 reference point or
+ * normal, 8 fallback query, 9 batched problem); *count (may be NULL) how many
+ * checks failed.  Clears both.  Synchronises the device (all streams) first.
+ * Errors: SICP_ECUDA (the synchronisation failed). */
+int sicp_check_status(int32_t* checked, uint64_t* first, uint64_t* count);
 
 #ifdef __cplusplus
 }

@@ -12,5 +12,6 @@ from .binding import (  # noqa: F401
     sicp_register_continue, sicp_surrogate_save, sicp_surrogate_load, sicp_reference_normals, SICP_POINT_TO_PLANE,
     SICP_INDEPENDENT, sicp_gaussian_kl, sicp_gaussian_ovl, sicp_pose_distribution, sicp_compound, chain_odometry,
     sicp_export_state, sicp_import_state, sicp_resume, sicp_set_memory_limit, sicp_set_wait_check,
-    sicp_trace_batched, sicp_read_batched_trace, sicp_surrogate_train_run,
+    sicp_trace_batched, sicp_read_batched_trace, sicp_surrogate_train_run, sicp_set_telemetry,
+    sicp_read_telemetry, TELEMETRY_FIELDS, sicp_check_status,
 )

@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsteinicp.so")
+# SICP_CHECKED=1: the bounds-checked build (build.build(checked=True)) instead of the normal one
+LIB_PATH = os.path.join(_HERE, "libsteinicp_checked.so" if os.environ.get("SICP_CHECKED") == "1"
+                        else "libsteinicp.so")
 
 SICP_OK = 0
 SICP_EINVAL = -1
@@ -46,7 +48,8 @@ EXPORTS = (
     "sicp_surrogate_train", "sicp_surrogate_params", "sicp_surrogate_loss_grad", "sicp_surrogate_infer",
     "sicp_register_continue", "sicp_surrogate_save", "sicp_surrogate_load",
     "sicp_export_state", "sicp_import_state", "sicp_resume", "sicp_set_memory_limit", "sicp_set_wait_check",
-    "sicp_trace_batched", "sicp_read_batched_trace", "sicp_surrogate_train_run",
+    "sicp_trace_batched", "sicp_read_batched_trace", "sicp_surrogate_train_run", "sicp_set_telemetry",
+    "sicp_read_telemetry", "sicp_check_status",
 )
 
 SURROGATE_NPARAM = 33040
@@ -120,6 +123,9 @@ def lib() -> ctypes.CDLL:
             "sicp_trace_batched": (ctypes.c_int, [P, I32]),
             "sicp_surrogate_train_run": (ctypes.c_int, [P, P, I64, P, I32, I64, U64, I32, I32, F32, P, ctypes.c_int]),
             "sicp_read_batched_trace": (ctypes.c_int, [P, P, P, P, P, P, P]),
+            "sicp_set_telemetry": (ctypes.c_int, [P, ctypes.c_int]),
+            "sicp_read_telemetry": (ctypes.c_int, [P, P, I32, ctypes.POINTER(I32)]),
+            "sicp_check_status": (ctypes.c_int, [ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -472,6 +478,38 @@ def sicp_set_wait_check(ctx, on: bool, polls: int = 0):
     """Make every bounded device wait of later calls wait for an event that never comes (on = True),
     giving up after `polls` polls (0: the defaults)."""
     _check(ctx, lib().sicp_set_wait_check(ctx, int(bool(on)), int(polls)))
+
+
+TELEMETRY_FIELDS = ("mean_x", "mean_y", "mean_z", "mean_roll", "mean_pitch", "mean_yaw",
+                    "sd_x", "sd_y", "sd_z", "sd_roll", "sd_pitch", "sd_yaw",
+                    "nn_mean_dist", "learned_share", "t", "found_share")
+
+
+def sicp_set_telemetry(ctx, on: bool = True):
+    """Record one telemetry row per iteration of later registration runs (TELEMETRY_FIELDS)."""
+    _check(ctx, lib().sicp_set_telemetry(ctx, int(bool(on))))
+
+
+def sicp_read_telemetry(ctx, max_rows: int = 1 << 20):
+    """The last run's telemetry rows, float32 [T][16] (columns TELEMETRY_FIELDS)."""
+    n = ctypes.c_int32(0)
+    _check(ctx, lib().sicp_read_telemetry(ctx, None, 0, ctypes.byref(n)))
+    rows = min(int(n.value), int(max_rows))
+    out = np.zeros((rows, 16), np.float32)
+    if rows:
+        _check(ctx, lib().sicp_read_telemetry(ctx, out.ctypes.data_as(ctypes.c_void_p), rows, ctypes.byref(n)))
+    return out
+
+
+def sicp_check_status():
+    """(checked, first, count): whether the loaded library is the bounds-checked build, the first
+    index check that failed since the last call (0: none; else bit 63 | site << 40 | index) and
+    how many failed; then clears them.  Synchronises the device."""
+    c, f, n = ctypes.c_int32(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = lib().sicp_check_status(ctypes.byref(c), ctypes.byref(f), ctypes.byref(n))
+    if rc != SICP_OK:
+        raise SicpError(rc, "sicp_check_status failed")
+    return bool(c.value), int(f.value), int(n.value)
 
 
 def sicp_profile(ctx, stride: int = 0):

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 
 namespace sicp {
 
@@ -22,6 +23,19 @@ int set_err(sicp_ctx* c, int code, const char* fmt, ...) {
     if (c) c->err = buf;
     return code;
 }
+
+std::vector<CheckReader>& check_registry() {
+    static std::vector<CheckReader> r;
+    return r;
+}
+
+void check_register(CheckReader r) { check_registry().push_back(r); }
+
+#ifdef SICP_CHECKED
+constexpr int32_t kCheckedBuild = 1;
+#else
+constexpr int32_t kCheckedBuild = 0;
+#endif
 
 int cuda_err(sicp_ctx* c, cudaError_t e, const char* what) {
     set_err(c, SICP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -64,7 +78,7 @@ int ensure(sicp_ctx* c, Buf& b, size_t bytes) {
 // Key of a captured registration loop: everything its kernels read as arguments.
 struct LoopKey {
     int64_t N;
-    int32_t K, T, m, mode, chunks, stride, pad;
+    int32_t K, T, m, mode, chunks, stride, tel;   // tel: telemetry rows recorded
     int32_t pi[4];          // T, m, nn_mode, prior
     float pf[16];           // lr, betas, eps, prior mu/sigma/kappa
     int32_t surr_iters;
@@ -75,7 +89,7 @@ struct LoopKey {
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
     int64_t wait_polls;     // failure-detection check settings (the kernels take them by value)
     int32_t wait_never, pad2;
-    const void* ptrs[12];
+    const void* ptrs[15];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -348,7 +362,8 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar,
-                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume};
+                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume, &c->tel,
+                   &c->tel_nn, &c->tel_part};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->ref4) cudaFree(c->ref4);
@@ -367,6 +382,7 @@ void sicp_destroy(sicp_ctx* c) {
 const char* sicp_last_error(const sicp_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_size, int on_device) {
+    NvtxRange nvtx_("reference_build");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!xyz || M < 1 || M > kMaxM) return set_err(ctx, SICP_EINVAL, "reference needs 1 <= M <= 2^30 points");
@@ -407,6 +423,7 @@ int sicp_set_reference(sicp_ctx* ctx, const float* xyz, int64_t M, float cell_si
 
 int sicp_minibatch(sicp_ctx* ctx, uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
                    int32_t* out_idx, int on_device) {
+    NvtxRange nvtx_("sample");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!out_idx || T < 1 || t0 < 0 || N < 1 || N > kMaxN || m < 1 || m > N)
@@ -429,6 +446,7 @@ int sicp_minibatch(sicp_ctx* ctx, uint64_t seed, int64_t t0, int32_t T, int64_t 
 
 int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out_idx, float* out_d2,
             int on_device) {
+    NvtxRange nvtx_("nn");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (n < 0 || n > kMaxN) return set_err(ctx, SICP_EINVAL, "query count out of range");
@@ -475,6 +493,7 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
 int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t* mb, int32_t m,
                   const float* particles, int32_t K, int32_t mode, float* out_gbar, int32_t* out_nn,
                   int on_device) {
+    NvtxRange nvtx_("transform_nn_gradient");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!src_xyz || !mb || !particles || !out_gbar) return set_err(ctx, SICP_EINVAL, "null pointer");
@@ -525,6 +544,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     int32_t* d_nn = (int32_t*)((char*)ctx->tmp_out.p + sizeof(float) * 6 * K);
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    ctx->src_n = N;
     SICP_CUDA(launch_check_finite((const float*)d_th, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
     SICP_CUDA(launch_check_index((const int32_t*)d_mb, m, N, (int*)ctx->flags.p, ctx->stream));
     int flags[4];
@@ -544,6 +564,8 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
     g.inv_m = 1.f / (float)m;
     g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
     g.mb_stride = 0;
+    g.n_src = N;
+    g.n_ref = ctx->M;
     if (surr) {
         SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, m, g.theta, K, kSurrogateIcpGradConf, (float*)ctx->partial.p,
                                         d_g, g.stats, (int*)ctx->flags.p + 3));
@@ -567,6 +589,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
 int sicp_stein_adam(sicp_ctx* ctx, float* particles, float* adam_m, float* adam_v, const float* gbar,
                     int32_t K, int64_t N, int64_t t, const sicp_params* p_in, float* out_phi, float* out_h,
                     int on_device) {
+    NvtxRange nvtx_("stein_adam");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!particles || !adam_m || !adam_v || !gbar || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
@@ -643,6 +666,7 @@ int moments_entry(sicp_ctx* ctx, const float* particles, int32_t K, double* mean
 extern "C" {
 
 int sicp_moments(sicp_ctx* ctx, const float* particles, int32_t K, double* mean6, double* cov36, int on_device) {
+    NvtxRange nvtx_("moments");
     return moments_entry(ctx, particles, K, mean6, cov36, on_device, false);
 }
 
@@ -662,6 +686,7 @@ namespace {
 int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles_in, int32_t K,
                  const sicp_params* p_in, float* particles_out, double* mean6, double* cov36, int on_device,
                  int64_t t0, const float* adam_in, float* adam_out) {
+    NvtxRange nvtx_("register");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!src_xyz || !particles_in || !particles_out || !p_in) return set_err(ctx, SICP_EINVAL, "null pointer");
@@ -715,6 +740,13 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if ((rc = ensure(ctx, ctx->gbar, b_th + 4 * sizeof(float)))) return rc;   // + the two blocks' medians
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
+    const bool tel = ctx->telemetry;
+    ctx->tel_rows = 0;
+    if (tel) {
+        if ((rc = ensure(ctx, ctx->tel, sizeof(float) * 16 * (size_t)(p.T > 0 ? p.T : 1)))) return rc;
+        if ((rc = ensure(ctx, ctx->tel_nn, sizeof(int32_t) * (size_t)K * p.m))) return rc;
+        if ((rc = ensure(ctx, ctx->tel_part, sizeof(float) * 2 * (size_t)K + 16))) return rc;
+    }
 
     const void *d_src, *d_th0;
     if ((rc = stage_in(ctx, src_xyz, sizeof(float) * 3 * N, on_device, ctx->tmp_in, &d_src))) return rc;
@@ -722,6 +754,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     float* theta = (float*)ctx->theta.p;
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    ctx->src_n = N;
     SICP_CUDA(launch_check_finite((const float*)d_th0, 6 * (int64_t)K, (int*)ctx->flags.p, ctx->stream));
     SICP_CUDA(cudaMemcpyAsync(theta, d_th0, b_th, cudaMemcpyDeviceToDevice, ctx->stream));
     if (adam_in) {
@@ -783,41 +816,76 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.ptrs[9] = stats_ptr(ctx);
     key.ptrs[10] = ctx->gbar.p;
     key.ptrs[11] = plane ? ctx->normals.p : nullptr;
+    key.tel = tel ? 1 : 0;
+    key.ptrs[12] = tel ? ctx->tel.p : nullptr;
+    key.ptrs[13] = tel ? ctx->tel_nn.p : nullptr;
+    key.ptrs[14] = tel ? ctx->tel_part.p : nullptr;
 
     GraphCache& gc = *ctx->graphs;
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];
     const bool use_graph = getenv("SICP_NO_GRAPH") == nullptr;
     auto record = [&](GraphSlot* prof) -> int {
-        if (indep)
-            SICP_CUDA(launch_minibatch_runs(p.seed, t0, p.T, N, p.m, K, (int32_t*)ctx->mb.p, ctx->stream));
-        else
-            SICP_CUDA(launch_minibatch(p.seed, t0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
+        {
+            NvtxRange r_sample("sample");
+            if (indep)
+                SICP_CUDA(launch_minibatch_runs(p.seed, t0, p.T, N, p.m, K, (int32_t*)ctx->mb.p, ctx->stream));
+            else
+                SICP_CUDA(launch_minibatch(p.seed, t0, p.T, N, p.m, (int32_t*)ctx->mb.p, ctx->stream));
+        }
         GradArgs g;
         g.src = (const float4*)ctx->src4.p;
         g.m = p.m;
         g.theta = theta;
         g.K = K;
         g.partial = (float*)ctx->partial.p;
-        g.out_nn = nullptr;
+        int32_t* tel_nn = tel ? (int32_t*)ctx->tel_nn.p : nullptr;   // the exact searches' correspondences
+        int* tel_fb = tel ? (int*)((float*)ctx->tel_part.p + 2 * (size_t)K) : nullptr;
+        g.out_nn = tel_nn;
         g.stats = stats_ptr(ctx);
         g.gbar = (float*)ctx->gbar.p;
         g.inv_m = 1.f / (float)p.m;
         g.normals = plane ? (const float4*)ctx->normals.p : nullptr;
         g.mb_stride = indep ? (int64_t)p.T * p.m : 0;   // run j's row of iteration t: mb[(j T + t) m]
+        g.n_src = N;
+        g.n_ref = ctx->M;
         int np = 0;
         for (int32_t t = 0; t < p.T; ++t) {
             const bool timed = prof && stride > 0 && (t % stride) == 0;
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np], ctx->stream, cudaEventRecordExternal));
             g.mb = (const int32_t*)ctx->mb.p + (size_t)t * p.m;
-            if (t < surr_T)
-                SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, p.m, theta, K, p.surrogate_min_conf,
-                                                (float*)ctx->partial.p, (float*)ctx->gbar.p, g.stats,
-                                                (int*)ctx->flags.p + 3));
-            else if (bf)
-                SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, p.m, theta, K, (float*)ctx->partial.p, (float*)ctx->gbar.p,
-                                           nullptr, (int*)ctx->flags.p + 3, g.normals, g.mb_stride));
-            else
-                SICP_CUDA(launch_grad(ctx, exact_mode, g));
+            {
+                NvtxRange r_grad("transform_nn_gradient");
+                if (t < surr_T)
+                    SICP_CUDA(surrogate_launch_grad(ctx, g.src, g.mb, p.m, theta, K, p.surrogate_min_conf,
+                                                    (float*)ctx->partial.p, (float*)ctx->gbar.p, g.stats,
+                                                    (int*)ctx->flags.p + 3, tel_fb));
+                else if (bf)
+                    SICP_CUDA(launch_grad_bf16(ctx, g.src, g.mb, p.m, theta, K, (float*)ctx->partial.p,
+                                               (float*)ctx->gbar.p, tel_nn, (int*)ctx->flags.p + 3, g.normals,
+                                               g.mb_stride));
+                else
+                    SICP_CUDA(launch_grad(ctx, exact_mode, g));
+            }
+            if (tel) {   // the row of iteration t, from the particles it started from
+                NvtxRange r_tel("telemetry");
+                TelArgs ta;
+                ta.theta = theta;
+                ta.K = K;
+                ta.m = p.m;
+                ta.src = g.src;
+                ta.n_src = N;
+                ta.mb = g.mb;
+                ta.mb_stride = g.mb_stride;
+                ta.nn = t < surr_T ? nullptr : tel_nn;
+                ta.ref4 = ctx->ref4;
+                ta.n_ref = ctx->M;
+                ta.qterms = t < surr_T ? (const float*)ctx->partial.p : nullptr;
+                ta.fb = t < surr_T ? tel_fb : nullptr;
+                ta.part = (float*)ctx->tel_part.p;
+                ta.row = (float*)ctx->tel.p + 16 * (size_t)t;
+                ta.t_abs = (double)(t0 + t);
+                SICP_CUDA(launch_telemetry(ta, ctx->stream));
+            }
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 1], ctx->stream, cudaEventRecordExternal));
             // the grid kernel and the surrogate path leave gbar; the exhaustive kernel leaves `chunks` partials
             SteinArgs a = (grid || bf) ? stein_args(p, theta, (float*)ctx->adam_m.p, (float*)ctx->adam_v.p,
@@ -831,15 +899,21 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
             a.gen = (uint32_t)(t + 1);
             a.max_spins = ctx->wait_polls;
             a.extra = ctx->wait_never ? 1u : 0u;
-            if (indep)
-                SICP_CUDA(launch_adam_independent(a, ctx->stream));
-            else
-                SICP_CUDA(launch_stein_adam(a, ctx->stream));
+            {
+                NvtxRange r_stein("stein_adam");
+                if (indep)
+                    SICP_CUDA(launch_adam_independent(a, ctx->stream));
+                else
+                    SICP_CUDA(launch_stein_adam(a, ctx->stream));
+            }
             if (timed) SICP_CUDA(cudaEventRecordWithFlags(prof->ev[3 * np + 2], ctx->stream, cudaEventRecordExternal));
             if (timed) ++np;
         }
         if (prof) prof->n_prof = np;
-        SICP_CUDA(launch_moments(theta, K, (double*)ctx->moments.p, ctx->stream));
+        {
+            NvtxRange r_mom("moments");
+            SICP_CUDA(launch_moments(theta, K, (double*)ctx->moments.p, ctx->stream));
+        }
         return SICP_OK;
     };
     if (use_graph) {
@@ -869,7 +943,10 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
             slot.key = key;
             slot.valid = true;
         }
-        SICP_CUDA(cudaGraphLaunch(slot.exec, ctx->stream));
+        {
+            NvtxRange r_launch("graph_launch");
+            SICP_CUDA(cudaGraphLaunch(slot.exec, ctx->stream));
+        }
         if (stride > 0) {
             // the other slot's last launch finished before this call began
             collect_profile(ctx, gc.slot[1 - gc.next]);
@@ -892,6 +969,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
         if ((rc = copy_out(ctx, adam_out + 6 * (size_t)K, ctx->adam_v.p, b_th, on_device))) return rc;
     }
     if ((rc = sync(ctx))) return rc;
+    ctx->tel_rows = tel ? p.T : 0;
     ctx->run_valid = true;
     ctx->run_K = K;
     ctx->run_t = t0 + p.T;
@@ -1092,6 +1170,35 @@ int sicp_set_wait_check(sicp_ctx* ctx, int on, int64_t polls) {
     ctx->wait_never = on ? 1 : 0;
     ctx->wait_polls = (long long)polls;
     return SICP_OK;
+}
+
+int sicp_check_status(int32_t* checked, uint64_t* first, uint64_t* count) {
+    unsigned long long f = 0, c = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SICP_ECUDA;
+    for (CheckReader r : check_registry()) r(&f, &c);
+    if (checked) *checked = kCheckedBuild;
+    if (first) *first = f;
+    if (count) *count = c;
+    return SICP_OK;
+}
+
+int sicp_set_telemetry(sicp_ctx* ctx, int on) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    ctx->telemetry = on != 0;
+    return SICP_OK;
+}
+
+int sicp_read_telemetry(sicp_ctx* ctx, float* out, int32_t max_rows, int32_t* rows) {
+    if (!ctx) return SICP_EINVAL;
+    ctx->err.clear();
+    if (max_rows < 0 || (max_rows > 0 && !out)) return set_err(ctx, SICP_EINVAL, "out needs max_rows >= 0 rows");
+    if (rows) *rows = ctx->tel_rows;
+    const int32_t n = ctx->tel_rows < max_rows ? ctx->tel_rows : max_rows;
+    if (n <= 0) return SICP_OK;
+    DeviceScope ds(ctx->device);
+    SICP_CUDA(cudaMemcpyAsync(out, ctx->tel.p, sizeof(float) * 16 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    return sync(ctx);
 }
 
 int sicp_set_memory_limit(sicp_ctx* ctx, size_t bytes, size_t* held) {

@@ -10,6 +10,63 @@
 
 namespace sicp {
 
+// ---------------------------------------------------------------- bounds-checked build
+// A build with -DSICP_CHECKED checks every index that comes from data (cell
+// coordinates, the seed map, cell_start, the row table, minibatch entries,
+// search results, fallback lists, work items) before the access:
+// SICP_IDX(i, n, site) is i when 0 <= i < n; otherwise the first such failure
+// of the translation unit is recorded (site and index) and counted, and index
+// 0 is used instead, so the access stays inside the buffer.  In the normal
+// build SICP_IDX(i, n, site) is i.  sicp_check_status reads and clears the
+// records of every translation unit.
+enum CheckSite : int {
+    kChkSeedCell = 1,   // fine-level cell of a query (seed map)
+    kChkSeedPoint,      // seed map entry -> sorted points
+    kChkCellStart,      // row segment bounds -> cell_start
+    kChkSorted,         // candidate -> sorted points
+    kChkTable,          // row table entry
+    kChkSrc,            // minibatch entry -> source points
+    kChkRef,            // search result -> reference points or normals
+    kChkFallback,       // fallback list entry -> queries
+    kChkProblem,        // batched work item -> problem
+};
+using CheckReader = void (*)(unsigned long long* first, unsigned long long* count);
+void check_register(CheckReader r);   // each translation unit's reader (checked build)
+
+#ifdef SICP_CHECKED
+namespace {
+__device__ unsigned long long g_check_first, g_check_count;
+
+__device__ __noinline__ int64_t check_fail(int64_t i, int site) {
+    const unsigned long long code =
+        (1ull << 63) | ((unsigned long long)(site & 0x7fffff) << 40) | ((unsigned long long)i & ((1ull << 40) - 1));
+    atomicCAS(&g_check_first, 0ull, code);
+    atomicAdd(&g_check_count, 1ull);
+    return 0;
+}
+__device__ __forceinline__ int64_t check_idx(int64_t i, int64_t n, int site) {
+    return (uint64_t)i < (uint64_t)n ? i : check_fail(i, site);
+}
+void check_read(unsigned long long* first, unsigned long long* count) {
+    unsigned long long f = 0, c = 0;
+    const unsigned long long z = 0;
+    cudaMemcpyFromSymbol(&f, g_check_first, sizeof f);
+    cudaMemcpyFromSymbol(&c, g_check_count, sizeof c);
+    cudaMemcpyToSymbol(g_check_first, &z, sizeof z);
+    cudaMemcpyToSymbol(g_check_count, &z, sizeof z);
+    if (f && !*first) *first = f;
+    *count += c;
+}
+struct CheckRegistration {
+    CheckRegistration() { check_register(&check_read); }
+};
+CheckRegistration g_check_registration;
+}  // namespace
+#define SICP_IDX(i, n, site) (::sicp::check_idx((int64_t)(i), (int64_t)(n), (site)))
+#else
+#define SICP_IDX(i, n, site) (i)
+#endif
+
 // ---------------------------------------------------------------- device helpers
 
 // splitmix64 (Steele, Lea, Flood 2014): output k >= 1 of the generator
@@ -129,6 +186,7 @@ struct GridView {
     const int32_t* cell_start;      // ncells + 1
     const int32_t* seed;            // ncells: position in `sorted` of a point near the cell centre (fine level)
     const float4* seed4;            // ncells: that point itself (single-problem fine level; null elsewhere)
+    int32_t nsorted;                // entries of `sorted` (bounds checks)
 };
 
 struct Grid {
@@ -250,6 +308,12 @@ struct sicp_ctx {
     // device memory budget (sicp_set_memory_limit; 0: none) and the bytes the context holds in
     // buffers that can grow (references, grids, run state, scratch)
     size_t mem_limit = 0, mem_used = 0;
+    // per-iteration telemetry of registration runs (sicp_set_telemetry): rows [T][16] of the last
+    // run, the correspondences of one iteration, per-particle distance sums and the fallback count
+    bool telemetry = false;
+    sicp::Buf tel, tel_nn, tel_part;
+    int32_t tel_rows = 0;
+    int64_t src_n = 0;   // points packed into src4 (bounds checks)
 };
 
 namespace sicp {
@@ -281,9 +345,9 @@ cudaError_t launch_check_index(const int32_t* idx, int64_t n, int64_t N, int* fl
 cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, float inv_m, float* gbar,
                                    cudaStream_t s);
 // gbar[j][c] = inv_m * sum over k of qterms[j][k][c] ([K][m][6], fixed order); also zeroes
-// *fb_count when it is not null
+// *fb_count when it is not null, after copying it to *fb_keep when that is not null
 cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int* fb_keep = nullptr);
 // ordered-uint bounding box of float4 points into lohi[6] (min xyz, max xyz), pre-initialised
 cudaError_t launch_bbox(const float4* p, int64_t n, unsigned* lohi, cudaStream_t s);
 float ordered_to_float(unsigned u);
@@ -331,6 +395,8 @@ struct GradArgs {
     // minibatch entries between consecutive particles' rows: 0, one row
     // shared by all particles; else particle j reads mb[j * mb_stride + k]
     int64_t mb_stride;
+    int64_t n_src;         // source points (bounds checks)
+    int64_t n_ref;         // reference points (bounds checks)
 };
 cudaError_t launch_grad_brute(const GradArgs& a, const float4* ref, int64_t M, cudaStream_t s);
 
@@ -387,9 +453,10 @@ void surrogate_invalidate(sicp_ctx* ctx);
 // Size the surrogate path's fallback list for `queries` per iteration and
 // clear its count (before capturing a loop that calls surrogate_launch_grad).
 int surrogate_prepare(sicp_ctx* ctx, int64_t queries);
+// fb_keep (or null): receives the number of queries sent to the exact search.
 cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta,
                                   int K, float min_conf, float* qterms, float* gbar, unsigned long long* stats,
-                                  int* err);
+                                  int* err, int* fb_keep = nullptr);
 
 // Exhaustive search with tensor-core distance tiles and an exact fp32 re-check
 // (k_nn_bf16.cu); same results as launch_nn_brute / the fp32 gradient.
@@ -402,6 +469,26 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
 cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta, int K,
                              float* qterms, float* gbar, int32_t* out_nn, int* err, const float4* normals,
                              int64_t mb_stride);
+
+// One telemetry row of a registration iteration (k_telemetry.cu): the particles it starts from,
+// the mean distance from its queries to their correspondences, the share the learned field served.
+struct TelArgs {
+    const float* theta;        // [K][6] particles at the start of the iteration
+    int32_t K, m;
+    const float4* src;         // packed source
+    int64_t n_src;             // its points (bounds checks)
+    const int32_t* mb;         // the iteration's minibatch row (independent runs: row of run 0)
+    int64_t mb_stride;         // run j's row at mb + j * mb_stride (0: one shared row)
+    const int32_t* nn;         // exact iterations: correspondences [K][m] (-1: none); else null
+    const float4* ref4;        // reference points by original index
+    int64_t n_ref;             // their number (bounds checks)
+    const float* qterms;       // learned iterations: per-query terms [K][m][6]; else null
+    const int* fb;             // learned iterations: queries sent to the exact search
+    float* part;               // [K] scratch: per-particle distance sums and counts ([2K])
+    float* row;                // [16] the row
+    double t_abs;              // the iteration's absolute index
+};
+cudaError_t launch_telemetry(const TelArgs& a, cudaStream_t s);
 
 // Grid (uniform voxel) search structure
 int grid_build(sicp_ctx* ctx, float cell_size);

@@ -109,7 +109,7 @@ __device__ __forceinline__ void warp_min(Best& B) {
 
 // Every row from table entry e on is farther than the current best.
 __device__ __forceinline__ bool cleared(const GridView& g, const SearchTable& tab, int e, float best) {
-    const float lbd = __ldg(tab.lb + e) * g.cell - g.tol;
+    const float lbd = __ldg(tab.lb + SICP_IDX(e, tab.n, kChkTable)) * g.cell - g.tol;
     return lbd > 0.f && lbd * lbd > bound2(best);
 }
 
@@ -134,8 +134,9 @@ __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, 
             const int x1 = min(min(cell_floor_clamped(q.x + r, g.origin.x, g.inv_cell, g.dims.x), g.dims.x - 1), xhi);
             if (x0 <= x1) {
                 const int64_t row = (int64_t)rowi * g.dims.x;
-                b = __ldg(g.cell_start + row + x0);
-                len = __ldg(g.cell_start + row + x1 + 1) - b;
+                const int64_t nc1 = (int64_t)g.dims.x * g.dims.y * g.dims.z + 1;   // (bounds checks)
+                b = __ldg(g.cell_start + SICP_IDX(row + x0, nc1, kChkCellStart));
+                len = __ldg(g.cell_start + SICP_IDX(row + x1 + 1, nc1, kChkCellStart)) - b;
                 w.segs += len > 0;
             }
         }
@@ -163,7 +164,7 @@ __device__ void round_rows(const GridView& g, float3 q, bool has, int y, int z, 
         const int ob = __shfl_sync(gm, b, o, G);
         const int oe = __shfl_sync(gm, excl, o, G);
         if (t < total) {
-            const float4 r = __ldg(g.sorted + ob + (t - oe));
+            const float4 r = __ldg(g.sorted + SICP_IDX(ob + (t - oe), g.nsorted, kChkSorted));
             take(L, r, q, __float_as_int(r.w));
         }
     }
@@ -201,7 +202,7 @@ __device__ bool walk(const GridView& g, const SearchTable& tab, int n, float cap
         const bool has = e < n;
         int y = 0, z = 0;
         if (has) {
-            const short2 o = __ldg(tab.off + e);
+            const short2 o = __ldg(tab.off + SICP_IDX(e, tab.n, kChkTable));
             y = c.cy + c.sy * o.x;
             z = c.cz + c.sz * o.y;
         }
@@ -226,14 +227,15 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
     const int cx = cell_coord(q.x, F.origin.x, F.inv_cell, F.dims.x);
     const int cy = cell_coord(q.y, F.origin.y, F.inv_cell, F.dims.y);
     const int cz = cell_coord(q.z, F.origin.z, F.inv_cell, F.dims.z);
-    const int64_t cell = ((int64_t)cz * F.dims.y + cy) * F.dims.x + cx;
+    const int64_t cell = SICP_IDX(((int64_t)cz * F.dims.y + cy) * F.dims.x + cx,
+                                  (int64_t)F.dims.x * F.dims.y * F.dims.z, kChkSeedCell);
     if (F.seed4) {   // the seed point itself: one load
         const float4 r = __ldg(F.seed4 + cell);
         take(B, r, q, __float_as_int(r.w));
     } else {
         const int s = __ldg(F.seed + cell);
         if (s >= 0) {
-            const float4 r = __ldg(F.sorted + s);
+            const float4 r = __ldg(F.sorted + SICP_IDX(s, F.nsorted, kChkSeedPoint));
             take(B, r, q, __float_as_int(r.w));
         }
     }

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "grid_search.cuh"
 #include "stein_device.cuh"
 
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) kb_persistent(BatchArgs 
         }
         // gradient phase: one warp per item, items interleaved over the whole grid
         for (int64_t it = (int64_t)blockIdx.x * (kThreads / 32) + warp; it < b.total_items; it += W) {
-            const int p = find_problem(b.item_off, b.P, it);
+            const int p = (int)SICP_IDX(find_problem(b.item_off, b.P, it), b.P, kChkProblem);
             const int K = b.part_off[p + 1] - b.part_off[p];
             const int64_t r = it - b.item_off[p];
             const int c = (int)(r / K), j = (int)(r % K);
@@ -307,7 +308,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) kb_persistent(BatchArgs 
             for (int kk = 0; kk < b.kkc; ++kk) {
                 const int k = c * b.kkc + kk;
                 if (k >= b.m) break;
-                const float4 s4 = __ldg(srcp + __ldg(mbp + k));
+                const float4 s4 =
+                    __ldg(srcp + SICP_IDX(__ldg(mbp + k), b.src_off[p + 1] - b.src_off[p], kChkSrc));
                 const float3 s = make_float3(s4.x, s4.y, s4.z);
                 const float3 q = apply_pose(P[warp], s);
                 Best B;
@@ -518,6 +520,7 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
         for (int p = 0; p < P; ++p) {
             GridView& v = L.hv[p];
             v.sorted = (const float4*)L.sorted.p;
+            v.nsorted = (int32_t)M;
             v.cell_start = (const int32_t*)L.cell_start.p + L.h_cell_off[p];
             v.seed = l == 0 ? (const int32_t*)L.seed.p + L.h_cell_off[p] : nullptr;
             v.seed4 = nullptr;
@@ -921,6 +924,7 @@ extern "C" int sicp_register_batched(sicp_ctx* ctx, int32_t P, const int64_t* re
                                      const int64_t* src_off, const float* src_xyz, const int32_t* part_off,
                                      const float* particles_in, const sicp_params* p_in, float* particles_out,
                                      double* mean6, double* cov36, int on_device) {
+    sicp::NvtxRange nvtx_("batched");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!p_in) return set_err(ctx, SICP_EINVAL, "null params");

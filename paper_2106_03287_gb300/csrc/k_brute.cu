@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kGradMaxThreads) k_grad_brute(GradArgs a, cons
     const bool valid = k < a.m;
     float3 s = make_float3(0.f, 0.f, 0.f);
     if (valid) {
-        float4 s4 = a.src[a.mb[(int64_t)j * a.mb_stride + k]];
+        float4 s4 = a.src[SICP_IDX(a.mb[(int64_t)j * a.mb_stride + k], a.n_src, kChkSrc)];
         s = make_float3(s4.x, s4.y, s4.z);
     }
     const float3 q = apply_pose(P, s);
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kGradMaxThreads) k_grad_brute(GradArgs a, cons
     if (valid && found) {
         const float4 r = ref[bi];
         float3 d = make_float3(q.x - r.x, q.y - r.y, q.z - r.z);
-        if (a.normals) d = plane_residual(__ldg(a.normals + bi), d);
+        if (a.normals) d = plane_residual(__ldg(a.normals + SICP_IDX(bi, a.n_ref, kChkRef)), d);
         grad_terms(P, s, d, g);
     }
     if (valid && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? bi : -1;

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
     const GridSearch& S = kConst ? c_search[slot] : *Sd;
-    const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+    const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + k), a.n_src, kChkSrc));
     float3 s = make_float3(s4.x, s4.y, s4.z);
     const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
     Work w;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
         const int jl = grp * kSeq + i, j = j0 + jl;
         if (j >= a.K) break;                        // uniform over the group
         if (a.mb_stride) {                          // independent runs: particle j's own minibatch
-            const float4 sj = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
+            const float4 sj = __ldg(a.src + SICP_IDX(__ldg(a.mb + (int64_t)j * a.mb_stride + k), a.n_src, kChkSrc));
             s = make_float3(sj.x, sj.y, sj.z);
         }
         const float3 q = apply_pose(P[jl], s);
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
         // the six gradient terms, one per lane (B, q and s are the same in every lane of the group)
         const bool found = B.i != kNone;   // false only for a non-finite distance
         float3 d = make_float3(q.x - B.p.x, q.y - B.p.y, q.z - B.p.z);
-        if (found && a.normals) d = plane_residual(__ldg(a.normals + B.i), d);
+        if (found && a.normals) d = plane_residual(__ldg(a.normals + SICP_IDX(B.i, a.n_ref, kChkRef)), d);
         if (lane < 6) a.partial[((int64_t)j * a.m + k) * 6 + lane] = found ? grad_term(P[jl], s, d, lane) : 0.f;
         if (lane == 0 && a.out_nn) a.out_nn[(int64_t)j * a.m + k] = found ? B.i : -1;
     }
@@ -325,6 +325,7 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     v.tol = (float)(1e-6 * (X + c));
     v.dims = dims;
     v.sorted = G.sorted;
+    v.nsorted = (int32_t)M;
     v.cell_start = G.cell_start;
     v.seed = seeds ? G.seed : nullptr;
     v.seed4 = seeds ? G.seed4 : nullptr;

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "grid_search.cuh"
 #include "tc.cuh"
 
@@ -662,6 +663,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_infer(InferArgs a) {
 
 struct SurrGradArgs {
     const float4* src;
+    int64_t n_src;            // source points (bounds checks)
     const int32_t* mb;        // m indices
     int m;
     const float* theta;       // K x 6
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_grad_surrogate(SurrGradArgs 
     make_pose(a.theta + 6 * j, P);
     float3 s3 = make_float3(0.f, 0.f, 0.f);
     if (live) {
-        const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+        const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + k), a.n_src, kChkSrc));
         s3 = make_float3(s4.x, s4.y, s4.z);
     }
     const float3 q = apply_pose(P, s3);
@@ -741,6 +743,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_grad_surrogate(SurrGradArgs 
 
 struct FallbackArgs {
     const float4* src;
+    int64_t n_src;            // source points (bounds checks)
+    int64_t nq;               // queries of the iteration, K m (bounds checks)
     const int32_t* mb;
     int m;
     const float* theta;
@@ -759,11 +763,11 @@ __global__ void __launch_bounds__(128, 8) k_grad_fallback(FallbackArgs a) {
     const int n = *a.fb_count;
     Work w;
     for (int f = gw; f < n; f += nw) {
-        const int g = __ldg(a.fb_list + f);
+        const int g = (int)SICP_IDX(__ldg(a.fb_list + f), a.nq, kChkFallback);
         const int j = g / a.m, k = g % a.m;
         Pose P;
         make_pose(a.theta + 6 * j, P);
-        const float4 s4 = __ldg(a.src + __ldg(a.mb + k));
+        const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + k), a.n_src, kChkSrc));
         const float3 s3 = make_float3(s4.x, s4.y, s4.z);
         const float3 q = apply_pose(P, s3);
         Best B;
@@ -911,12 +915,13 @@ int surrogate_prepare(sicp_ctx* ctx, int64_t queries) {
 
 cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_t* mb, int m, const float* theta,
                                   int K, float min_conf, float* qterms, float* gbar, unsigned long long* stats,
-                                  int* err) {
+                                  int* err, int* fb_keep) {
     Surrogate& S = *ctx->surr;
     int* fb_count = (int*)S.fb.p;
     int* fb_list = fb_count + 16;
     SurrGradArgs a;
     a.src = src;
+    a.n_src = ctx->src_n;
     a.mb = mb;
     a.m = m;
     a.theta = theta;
@@ -937,6 +942,8 @@ cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_
     if (e != cudaSuccess) return e;
     FallbackArgs f;
     f.src = src;
+    f.n_src = ctx->src_n;
+    f.nq = (int64_t)K * m;
     f.mb = mb;
     f.m = m;
     f.theta = theta;
@@ -947,7 +954,7 @@ cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_
     f.stats = stats;
     k_grad_fallback<<<(unsigned)(ctx->num_sms * 8), 128, 0, ctx->stream>>>(f);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, fb_count, ctx->stream);
+    return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, fb_count, ctx->stream, fb_keep);
 }
 
 }  // namespace sicp
@@ -1091,6 +1098,7 @@ int surrogate_train_impl(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_
 
 extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
                                     float lr, float* out_loss) {
+    sicp::NvtxRange nvtx_("surrogate_train");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     return surrogate_train_impl(ctx, n_queries, seed, epochs, batch, lr, out_loss, RunSampling{});
@@ -1099,6 +1107,7 @@ extern "C" int sicp_surrogate_train(sicp_ctx* ctx, int64_t n_queries, uint64_t s
 extern "C" int sicp_surrogate_train_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* particles,
                                         int32_t K, int64_t n_queries, uint64_t seed, int32_t epochs, int32_t batch,
                                         float lr, float* out_loss, int on_device) {
+    sicp::NvtxRange nvtx_("surrogate_train");
     if (!ctx) return SICP_EINVAL;
     ctx->err.clear();
     if (!src_xyz || !particles || N < 1 || N > 0x7fffffff || K < 1 || K > 2048)
@@ -1132,6 +1141,7 @@ extern "C" int sicp_surrogate_train_run(sicp_ctx* ctx, const float* src_xyz, int
     if (rc) return rc;
     SICP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->stream));
     SICP_CUDA(launch_pack_points((const float*)d_src, N, (float4*)ctx->src4.p, (int*)ctx->flags.p, ctx->stream));
+    ctx->src_n = N;
     int bad = 0;
     {
         int flags[4];

@@ -190,6 +190,7 @@ struct BfArgs {
     const float* q;            // grad = 0: [n][3]
     int64_t n;
     const float4* src;         // grad = 1
+    int64_t n_src;             // its points (bounds checks)
     const int32_t* mb;
     int m;
     const float* theta;
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                     const int k = (int)(g / a.K), j = (int)(g % a.K);
                     Pose P;
                     make_pose(a.theta + 6 * j, P);
-                    const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
+                    const float4 s4 =
+                        __ldg(a.src + SICP_IDX(__ldg(a.mb + (int64_t)j * a.mb_stride + k), a.n_src, kChkSrc));
                     q = apply_pose(P, make_float3(s4.x, s4.y, s4.z));
                 } else {
                     q = make_float3(a.q[3 * g], a.q[3 * g + 1], a.q[3 * g + 2]);
@@ -585,9 +587,10 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                     if (found) {
                         Pose P;
                         make_pose(a.theta + 6 * j, P);
-                        const float4 s4 = __ldg(a.src + __ldg(a.mb + (int64_t)j * a.mb_stride + k));
+                        const float4 s4 =
+                            __ldg(a.src + SICP_IDX(__ldg(a.mb + (int64_t)j * a.mb_stride + k), a.n_src, kChkSrc));
                         float3 dv = make_float3(q.x - bp.x, q.y - bp.y, q.z - bp.z);
-                        if (a.normals) dv = plane_residual(__ldg(a.normals + bi), dv);
+                        if (a.normals) dv = plane_residual(__ldg(a.normals + SICP_IDX(bi, a.M, kChkRef)), dv);
                         grad_terms(P, make_float3(s4.x, s4.y, s4.z), dv, t6);
                     }
 #pragma unroll
@@ -699,6 +702,7 @@ cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb
     a.mb_stride = mb_stride;
     a.grad = 1;
     a.src = src;
+    a.n_src = ctx->src_n;
     a.mb = mb;
     a.m = m;
     a.theta = theta;

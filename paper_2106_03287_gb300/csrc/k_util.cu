@@ -168,12 +168,16 @@ unsigned grid_1d(int64_t n, int threads, int cap = 4096) {
 // fixed butterfly.  Clears the fallback count for the next iteration.
 constexpr int kGbarThreads = 192;
 __global__ void __launch_bounds__(kGbarThreads) k_qterms_to_gbar(const float* __restrict__ qterms, int K, int m,
-                                                                 float inv_m, float* __restrict__ gbar, int* fb_count) {
+                                                                 float inv_m, float* __restrict__ gbar, int* fb_count,
+                                                                 int* fb_keep) {
     __shared__ float part[6][33];
     const int j = blockIdx.x, t = threadIdx.x;
     pdl_trigger();   // the Stein step may be scheduled now (it waits for this grid)
     pdl_wait();
-    if (j == 0 && t == 0 && fb_count) *fb_count = 0;
+    if (j == 0 && t == 0 && fb_count) {
+        if (fb_keep) *fb_keep = *fb_count;
+        *fb_count = 0;
+    }
     const int e = t / 6, c = t % 6;
     const float* row = qterms + (int64_t)j * m * 6;
     float acc = 0.f;
@@ -224,9 +228,10 @@ cudaError_t launch_partial_to_gbar(const float* partial, int chunks, int32_t K, 
 }
 
 cudaError_t launch_qterms_to_gbar(const float* qterms, int32_t K, int32_t m, float inv_m, float* gbar, int* fb_count,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int* fb_keep) {
     if (K <= 0) return cudaSuccess;
-    return launch_pdl(k_qterms_to_gbar, dim3(K), dim3(kGbarThreads), 0, s, qterms, K, m, inv_m, gbar, fb_count);
+    return launch_pdl(k_qterms_to_gbar, dim3(K), dim3(kGbarThreads), 0, s, qterms, K, m, inv_m, gbar, fb_count,
+                      fb_keep);
 }
 
 cudaError_t launch_bbox(const float4* p, int64_t n, unsigned* lohi, cudaStream_t s) {
