@@ -59,6 +59,8 @@ def parse():
                     help="ICP error metric: point-to-point (the paper's Stein ICP) or point-to-plane")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-single", action="store_true",
+                    help="batched workload: skip the single-problem-path comparison")
     return ap.parse_args()
 
 
@@ -671,6 +673,39 @@ def run_ours(args):
     return 0
 
 
+def single_problem_path(S, torch, raw, p, evals, stream, flush, passes=2):
+    """The batch's problems through the single-problem path, outside the timed
+    region: one context per problem (each keeps its captured registration
+    graph), and every pass rebuilds each problem's reference and registers it,
+    as a batched step rebuilds every grid.  Device inputs, CUDA events around
+    each pass after two untimed passes."""
+    dev = [tuple(torch.from_numpy(a).cuda() for a in (d["ref"], d["src"], d["particles"])) for d in raw]
+    ctxs = [S.sicp_create(torch.cuda.current_device(), stream) for _ in dev]
+    try:
+        def run():
+            for c, (r, src, par) in zip(ctxs, dev):
+                S.sicp_set_reference(c, r)
+                S.sicp_register(c, src, par, p)
+        run()
+        run()
+        ms = []
+        for _ in range(passes):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    finally:
+        for c in ctxs:
+            S.sicp_destroy(c)
+    t = statistics.mean(ms)
+    return {"value": evals / (t * 1e-3), "unit": "particle_point_evals/s", "ms_per_pass": t,
+            "how": f"{len(raw)} contexts, one per problem: reference build + one captured registration each, "
+                   f"the same problems and parameters; mean of {passes} passes after 2 untimed ones"}
+
+
 def kernel_profile(S, ctx, step, stride, runs=3):
     """Average kernel durations over `runs` untimed steps with profiling on
     (the first captures the profiling graphs and is discarded)."""
@@ -838,6 +873,7 @@ def run_ours_batched(args):
            "h2d_bytes_per_step": 12 * (Mtot + Ntot) + 24 * sum(Ks), "d2h_bytes_per_step": 24 * sum(Ks) + 8 * 42 * len(raw),
            "ms_per_step": 1e3 * statistics.mean(wall)}
     S.sicp_destroy(ctx)
+    single = single_problem_path(S, torch, raw, p, evals, stream, flush) if not args.no_single else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(raw[0], cfg, budget_s=10.0)
@@ -855,7 +891,7 @@ def run_ours_batched(args):
                 "iters_per_sec": world * cfg["T"] / (ms_max / 1e3),
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": (2 + 2 * 9 + 3 + 4) * args.steps,
-                "roofline": roofline, "cpu_baseline": cpu}
+                "roofline": roofline, "vs_single_problem_path": single, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
