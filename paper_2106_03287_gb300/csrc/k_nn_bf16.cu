@@ -226,36 +226,27 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t r[16]) {
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 columns of the thread's TMEM lane and their minimum, reduced by the load
+// itself (tcgen05.ld.red, .min over the loaded elements: sm_103a).  Like the
+// values, the minimum is valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_min(uint32_t taddr, float r[16], float& mn) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "%16, [%17];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]),
+          "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]),
+          "=f"(mn)
         : "r"(taddr)
         : "memory");
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // min(a, b, c) in one instruction (three-input min.f32 of sm_100 and later).
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
-}
-
-// Minimum of 64 accumulator values and of each run of 8 (g[i] over columns
-// 8i .. 8i + 7): a tree of three-input minimums, 36 instructions (a minimum is
-// exact in any order).  The run minimums let the candidate scan skip the runs
-// that hold no candidate.
-__device__ __forceinline__ float min64_runs(const uint32_t r[64], float g[8]) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const uint32_t* x = r + 8 * i;
-        const float a = min3f(__uint_as_float(x[0]), __uint_as_float(x[1]), __uint_as_float(x[2]));
-        const float b = min3f(__uint_as_float(x[3]), __uint_as_float(x[4]), __uint_as_float(x[5]));
-        g[i] = min3f(a, b, fminf(__uint_as_float(x[6]), __uint_as_float(x[7])));
-    }
-    return min3f(min3f(g[0], g[1], g[2]), min3f(g[3], g[4], g[5]), fminf(g[6], g[7]));
 }
 
 // Reference tile swept at step t (all R tiles, from `rot` on).
@@ -520,17 +511,17 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                 continue;
             }
             const uint32_t tb = tmem + (uint32_t)(b * kRCols + qtr * kQuarter) + ((uint32_t)(32 * rq) << 16);
-            uint32_t r[64];
-            tmem_ld16_nw(tb, r);
-            tmem_ld16_nw(tb + 16, r + 16);
-            tmem_ld16_nw(tb + 32, r + 32);
-            tmem_ld16_nw(tb + 48, r + 48);
+            // the 64 values and the minimum of each run of 16, reduced by the loads
+            float r[64], g[4];
+            tmem_ld16_min(tb, r, g[0]);
+            tmem_ld16_min(tb + 16, r + 16, g[1]);
+            tmem_ld16_min(tb + 32, r + 32, g[2]);
+            tmem_ld16_min(tb + 48, r + 48, g[3]);
             tmem_wait_ld();
             const int rt = tile_at(t);
             const float nt = __ldg(a.nmax + rt);
             const float E = fmaf(aq, nt, fmaf(kEpsRR * nt, nt, eq));
-            float g[8];
-            const float cm = min64_runs(r, g);
+            const float cm = min3f(g[0], g[1], fminf(g[2], g[3]));
             u = fminf(u, cm + E);
             const float thr = u + E;   // lower bound v - E <= u
             if (cm <= thr) {
@@ -539,12 +530,12 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                 const float4* pts =
                     reinterpret_cast<const float4*>(sm + sRing + (t % kSlots) * kSlotBytes + kTileBytes);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     if (g[i] > thr) continue;   // no candidate in this run
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = 8 * i + jj;
-                        if (__uint_as_float(r[j]) <= thr && j < lim) {
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int j = 16 * i + jj;
+                        if (r[j] <= thr && j < lim) {
                             const float4 r4 = pts[col0 + j];
                             const float d = dist2(r4, q);
                             const unsigned id = __float_as_uint(r4.w);
