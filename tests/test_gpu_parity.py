@@ -273,6 +273,44 @@ def test_moments_match_oracle(ctx):
         assert np.allclose(cov, co, rtol=1e-10, atol=1e-15)
 
 
+@pytest.mark.parametrize("mode", [S.SICP_NN_GRID, S.SICP_NN_BRUTE_BF16])
+def test_max_particles(ctx, mode):
+    """K = 2048 (the largest K a registration takes), m = 300: 614,400 queries
+    per iteration.  The first iteration's gradient against the oracle given
+    the GPU's correspondences (1e-4 relative with the FP32 floor), those
+    correspondences against the oracle's k-d tree (the same point, or one
+    whose FP64 distance is within the FP32 transform's rounding of the
+    nearest), and a two-iteration sicp_register against the same two
+    iterations composed from sicp_icp_grad and sicp_stein_adam, bit for bit
+    (the same kernels; the loop's median selection starts from the previous
+    median, the separate call selects from scratch, and both are exact)."""
+    d = synth.make_kinect_problem(4, M=20_000, N=4000, K=2048)
+    S.sicp_set_reference(ctx, d["ref"])
+    ref, src, th = d["ref"], d["src"], d["particles"]
+    assert th.shape == (2048, 6)
+    N, m, seed = src.shape[0], 300, 19
+    mb = O.minibatch(seed, 0, N, m)
+    g, nn = S.sicp_icp_grad(ctx, src, mb, th, mode)
+    th64 = th.astype(np.float64)
+    g_ref = O.icp_grad_given_nn(ref, src, mb, th64, nn)
+    floor = _grad_floor(ref, src, th)
+    assert np.all(np.abs(g - g_ref).max(1) <= np.maximum(1e-4 * np.abs(g_ref).max(1), floor))
+    tree = O.KDTree(ref)
+    rows = np.random.default_rng(1).choice(2048, 64, replace=False)
+    for j in rows:
+        q = O.transform(th64[j], src[mb])
+        idx, d2 = tree.nn(q)
+        d_gpu = np.linalg.norm(ref[nn[j]].astype(np.float64) - q, axis=1)
+        assert np.all((nn[j] == idx) | (d_gpu - np.sqrt(d2) <= 8 * floor)), j
+    p = S.sicp_default_params(T=2, m=m, lr=0.03, seed=seed, nn_mode=mode)
+    got, _, _ = S.sicp_register(ctx, src, th, p)
+    x, mo, ve = th.copy(), np.zeros_like(th), np.zeros_like(th)
+    for t in range(2):
+        gt, _ = S.sicp_icp_grad(ctx, src, O.minibatch(seed, t, N, m), x, mode, want_nn=False)
+        S.sicp_stein_adam(ctx, x, mo, ve, gt, N, t + 1, p)
+    assert np.array_equal(got, x)
+
+
 # ---------------------------------------------------------------- whole run
 
 def _teacher_forced_run(ctx, d, params, mode, T):
