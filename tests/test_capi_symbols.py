@@ -31,6 +31,17 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert declared == set(S.EXPORTS)
 
 
+def test_checked_library_builds_and_exports_the_same_symbols():
+    """The bounds-checked variant (-DSICP_CHECKED) is the same library with
+    index checks compiled in: same exports, plus a status that says so (the
+    status itself needs a GPU, so only the symbol is checked here)."""
+    path = build.build(checked=True)
+    assert os.path.basename(path) == "libsteinicp_checked.so" and os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 def test_binding_params_layout_matches_defaults():
     p = S.sicp_default_params()
     assert (p.T, p.m, p.nn_mode, p.prior, p.surrogate_iters) == (100, 100, S.SICP_NN_GRID, 0, 0)
