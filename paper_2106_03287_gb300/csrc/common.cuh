@@ -223,6 +223,7 @@ struct GridSearch {
     SearchTable tab;
     const float4* ref4;
     int M;
+    float reach;   // fine-level reach of the far phase, in fine cells
 };
 
 bool pdl_enabled();   // false when the environment sets SICP_NO_PDL

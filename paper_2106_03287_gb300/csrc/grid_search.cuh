@@ -17,7 +17,13 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;  // queries in flight per CTA, one warp each
 constexpr int kGradThreads = 128;      // gradient kernel CTA: one warp per particle
 constexpr int kCoarseFactor = 4;
-constexpr float kFineReach = 6.f;      // the far phase proves on the fine level below this many cells
+// The far phase proves on the fine level while the bound is under this many fine
+// cells, else on the coarse level (GridSearch::reach).  Measured (M particle-point
+// evaluations per second): the kinect run 788 / 793 / 794 / 794 / 792 / 739 at 3 / 4 /
+// 5 / 6 / 10 / 16 cells; the 256 batched problems, each reach with its own autotuned
+// cell size, 767.6 at 3 against 753.1 at 6.
+constexpr float kFineReach = 6.f;          // single problems
+constexpr float kBatchedFineReach = 3.f;   // the persistent batched kernel
 constexpr int kTableRadius = 48;
 constexpr int64_t kMaxCells = 1 << 23;
 constexpr float kSlack = 1.0000005f;
@@ -244,13 +250,13 @@ __device__ __forceinline__ void grid_search(const GridSearch& S, float3 q, Best&
 
 // The exact nearest point of q given a starting answer B (any reference
 // point, or none): walk the table with the shrinking bound on the fine level
-// (bound under kFineReach cells) or the coarse level, and scan everything if
+// (bound under S.reach cells) or the coarse level, and scan everything if
 // the table cannot settle it.
 template <int G>
 __device__ __forceinline__ void prove(const GridSearch& S, float3 q, Best& B, Work& w) {
     const int lane = group_lane<G>();
     const GridView& F = S.fine;
-    const float reach = kFineReach * F.cell;
+    const float reach = S.reach * F.cell;
     const bool fine = B.d <= reach * reach;
     w.far += (lane == 0 && !fine);
     const GridView& L = fine ? S.fine : S.coarse;

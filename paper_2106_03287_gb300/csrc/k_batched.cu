@@ -572,6 +572,7 @@ int build_batched(sicp_ctx* ctx, BatchState& B, int P, const std::vector<int64_t
         hs[p].tab = ctx->search.tab;
         hs[p].ref4 = (const float4*)B.ref4.p + ref_off[p];
         hs[p].M = (int)(ref_off[p + 1] - ref_off[p]);
+        hs[p].reach = gs::kBatchedFineReach;
     }
     if ((rc = ensure(ctx, B.searches, sizeof(GridSearch) * P))) return rc;
     SICP_CUDA(cudaMemcpyAsync(B.searches.p, hs.data(), sizeof(GridSearch) * P, cudaMemcpyHostToDevice, s));

@@ -448,6 +448,7 @@ int grid_build(sicp_ctx* ctx, float cell_size) {
     ctx->search.coarse = ctx->grid2.v;
     ctx->search.ref4 = ctx->ref4;
     ctx->search.M = (int)M;
+    ctx->search.reach = kFineReach;
     // the device copy the captured gradient launches read
     if ((rc = ensure(ctx, ctx->search_dev, sizeof(GridSearch)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->search_dev.p, &ctx->search, sizeof(GridSearch), cudaMemcpyHostToDevice, s));
