@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-single", action="store_true",
                     help="batched workload: skip the single-problem-path comparison")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched workload: only the first P problems (a small case, for profiling)")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="batched workload: T iterations instead of the workload's (a small case, for profiling)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: the library's default tuning, no trial launches")
     return ap.parse_args()
 
 
@@ -807,14 +813,21 @@ def run_ours_batched(args):
     if not os.path.exists(S.LIB_PATH):
         build.build()
     raw, cfg = make_problem("batched", rank_seed(rank))
+    if args.problems:   # a smaller case of the same workload (profiling): the first P problems, T iterations
+        raw = raw[:args.problems]
+    if args.iters:
+        cfg["T"] = args.iters
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = S.sicp_create(local, stream)
     p = S.sicp_default_params(T=cfg["T"], m=cfg["m"], lr=cfg["lr"], seed=0, nn_mode=S.SICP_NN_GRID)
     dev = S.pack_batch([tuple(torch.from_numpy(a).cuda() for a in (d["ref"], d["src"], d["particles"])) for d in raw])
     torch.cuda.synchronize()
-    tuned = S.sicp_autotune_batched(ctx, dev, p, trial_iters=3,
-                                    cache_path=os.path.join(tempfile.gettempdir(), "sicp_tune.json"))
+    if args.no_autotune:   # the library's defaults; no trial launches before the measured ones
+        tuned = (None, None, None)
+    else:
+        tuned = S.sicp_autotune_batched(ctx, dev, p, trial_iters=3,
+                                        cache_path=os.path.join(tempfile.gettempdir(), "sicp_tune.json"))
     Ks = [d["particles"].shape[0] for d in raw]
     evals = sum(Ks) * cfg["m"] * cfg["T"]
     for _ in range(max(args.warmup, 3)):
