@@ -1,8 +1,10 @@
-"""Programmatic dependent launch changes when kernels are scheduled, never what
-they compute: a registration run with it (the default) and one in a process
-with SICP_NO_PDL=1 (plain stream order) return bit-identical particles, for
-every exact search, point-to-point and point-to-plane, Stein and independent
-runs.  The oracle is not involved; the comparison is exact.
+"""Programmatic dependent launch and the captured graph change when kernels are
+scheduled, never what they compute: a registration run with both (the
+default), one in a process with SICP_NO_PDL=1 (plain stream order) and one
+with SICP_NO_GRAPH=1 (plain launches instead of the captured loop) return
+bit-identical particles, for every exact search, point-to-point and
+point-to-plane, Stein and independent runs.  The oracle is not involved; the
+comparison is exact.
 """
 import os
 import subprocess
@@ -63,3 +65,20 @@ def test_programmatic_launch_changes_no_result():
     assert len(a) == len(b) == 10
     for i, (x, y) in enumerate(zip(a, b)):
         assert x == y, f"run {i} differs with and without programmatic launch"
+
+
+def test_uncaptured_loop_changes_no_result():
+    """SICP_NO_GRAPH=1 runs the registration loop as plain launches instead of
+    one captured CUDA graph: the same kernels with the same arguments, so the
+    same particles bit for bit (also with the programmatic launches off)."""
+    from paper_2106_03287_gb300 import build
+    build.build()
+    base = dict(os.environ)
+    base.pop("SICP_NO_PDL", None)
+    base.pop("SICP_NO_GRAPH", None)
+    a = _run(base)
+    b = _run(dict(base, SICP_NO_GRAPH="1"))
+    c = _run(dict(base, SICP_NO_GRAPH="1", SICP_NO_PDL="1"))
+    assert len(a) == len(b) == len(c) == 10
+    for i, (x, y, z) in enumerate(zip(a, b, c)):
+        assert x == y == z, f"run {i} differs without the captured graph"
