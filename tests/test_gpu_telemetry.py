@@ -137,3 +137,22 @@ def test_read_without_rows_and_bad_arguments(kin):
     assert S.lib().sicp_read_telemetry(ctx, None, 0, ctypes.byref(n)) == S.SICP_OK and n.value == 0
     assert S.lib().sicp_read_telemetry(ctx, None, -1, None) == S.SICP_EINVAL
     assert S.lib().sicp_read_telemetry(ctx, None, 4, None) == S.SICP_EINVAL
+
+
+def test_single_particle_and_empty_run(kin):
+    """K = 1: the spread columns are 0 (divisor K - 1 undefined), the mean is
+    the particle itself and the distance that of its own queries; T = 0
+    records no rows and leaves the particles as they came in."""
+    ctx, d, tree = kin
+    parts = d["particles"][:1]
+    N, m, seed = d["src"].shape[0], 64, 8
+    p = S.sicp_default_params(T=4, m=m, lr=0.03, seed=seed, nn_mode=S.SICP_NN_GRID)
+    _, rows = _run(ctx, d, parts, p, True)
+    assert rows.shape == (4, 16) and np.all(rows[:, 6:12] == 0) and np.all(rows[:, 15] == 1.0)
+    np.testing.assert_allclose(rows[0, :6], parts[0], rtol=1e-6, atol=1e-7)
+    _, d2 = tree.nn(O.transform(parts[0].astype(np.float64), d["src"][O.minibatch(seed, 0, N, m)]))
+    want = np.sqrt(d2).mean()
+    assert abs(rows[0, 12] - want) <= 1e-5 * want
+    p0 = S.sicp_default_params(T=0, m=m, lr=0.03, seed=seed, nn_mode=S.SICP_NN_GRID)
+    (th, _, _), rows0 = _run(ctx, d, parts, p0, True)
+    assert np.array_equal(th, parts) and rows0.shape == (0, 16)
