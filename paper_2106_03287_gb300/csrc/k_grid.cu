@@ -178,21 +178,18 @@ __global__ void k_scatter(const float4* __restrict__ ref, int64_t M, const int32
 }
 
 // Order each cell's points by original index, so the layout is deterministic.
-// One warp per cell: rank of each point = number of smaller indices in the cell.
-__global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int64_t ncells, const float4* __restrict__ in,
-                             float4* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = wid; c < ncells; c += nw) {
+// One thread per point (most cells are empty; every point has a cell): its
+// rank in its cell is the number of the cell's points with a smaller index,
+// counted over the cell's unordered copy in `staging`.
+__global__ void k_sort_points(const float4* __restrict__ ref, int64_t M, const int32_t* __restrict__ cell_of,
+                              const int32_t* __restrict__ cell_start, const float4* __restrict__ staging,
+                              float4* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell_of[i];
         const int b = cell_start[c], e = cell_start[c + 1];
-        for (int i = b + lane; i < e; i += 32) {
-            const float4 v = in[i];
-            const int key = __float_as_int(v.w);
-            int rank = 0;
-            for (int k = b; k < e; ++k) rank += __float_as_int(in[k].w) < key;
-            out[b + rank] = v;
-        }
+        int rank = 0;
+        for (int k = b; k < e; ++k) rank += __float_as_int(staging[k].w) < (int)i;
+        out[b + rank] = ref[i];
     }
 }
 
@@ -337,7 +334,7 @@ int build_level(sicp_ctx* ctx, Grid& G, const float lo[3], const float ext[3], d
     SICP_CUDA(cudaMemsetAsync(G.counts, 0, sizeof(int32_t) * ncells, s));
     k_scatter<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, G.cell_of, G.cell_start, G.counts, staging);
     SICP_CUDA(cudaGetLastError());
-    k_sort_cells<<<blocks_for(ncells * 32, 256), 256, 0, s>>>(G.cell_start, ncells, staging, G.sorted);
+    k_sort_points<<<blocks_for(M, 256), 256, 0, s>>>(ctx->ref4, M, G.cell_of, G.cell_start, staging, G.sorted);
     SICP_CUDA(cudaGetLastError());
     if (seeds) {
         int32_t* a = G.seed;
