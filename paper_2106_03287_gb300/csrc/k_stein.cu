@@ -83,20 +83,64 @@ __global__ void k_adam_independent(SteinArgs a) {
     a.theta[idx] = x - a.lr * mh / (sqrtf(vh) + a.eps);
 }
 
-__global__ void k_moments(const float* __restrict__ th, int K, double* __restrict__ out) {
-    __shared__ double mean[6];
-    const int tid = threadIdx.x;
-    if (tid < 6) {
-        double s = 0.0;
-        for (int j = 0; j < K; ++j) s += (double)th[6 * j + tid];
-        mean[tid] = s / (double)K;
+// Mean and covariance (two passes, float64) over kMomThreads threads: thread t
+// takes the particles j = t, t + kMomThreads, ... in order, the warps combine
+// their lanes with a fixed butterfly and thread 0 the warps in order, so the
+// result is deterministic.  (FP64 is the slow unit of this GPU; a few threads
+// walking all K particles took about 28 us for K = 100.)
+constexpr int kMomThreads = 256;
+
+template <int N>
+__device__ __forceinline__ void block_sum_d(double (&v)[N], double (*part)[kMomThreads / 32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+        if (lane == 0) part[i][warp] = v[i];
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < kMomThreads / 32; ++w) s += part[i][w];
+            part[i][0] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMomThreads) k_moments(const float* __restrict__ th, int K, double* __restrict__ out) {
+    __shared__ double part[21][kMomThreads / 32];
+    __shared__ double mean[6];
+    const int tid = threadIdx.x;
+    double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int j = tid; j < K; j += kMomThreads)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) m[a] += (double)th[6 * j + a];
+    block_sum_d(m, part);
+    if (tid < 6) mean[tid] = part[tid][0] / (double)K;
+    __syncthreads();
+    double c[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) c[i] = 0.0;
+    for (int j = tid; j < K; j += kMomThreads) {
+        double d[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) d[a] = (double)th[6 * j + a] - mean[a];
+        int i = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b) c[i++] += d[a] * d[b];
+    }
+    block_sum_d(c, part);
     if (tid < 36) {
         const int a = tid / 6, b = tid % 6;
-        double s = 0.0;
-        for (int j = 0; j < K; ++j) s += ((double)th[6 * j + a] - mean[a]) * ((double)th[6 * j + b] - mean[b]);
-        out[6 + tid] = (K > 1) ? s / (double)(K - 1) : 0.0;
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const int i = lo * 6 - lo * (lo - 1) / 2 + (hi - lo);   // upper-triangle index of (lo, hi)
+        out[6 + tid] = (K > 1) ? part[i][0] / (double)(K - 1) : 0.0;
     }
     if (tid < 6) out[tid] = mean[tid];
 }
@@ -167,7 +211,7 @@ cudaError_t launch_adam_independent(const SteinArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_moments(const float* theta, int32_t K, double* out42, cudaStream_t s) {
-    k_moments<<<1, 64, 0, s>>>(theta, K, out42);
+    k_moments<<<1, kMomThreads, 0, s>>>(theta, K, out42);
     return cudaGetLastError();
 }
 
