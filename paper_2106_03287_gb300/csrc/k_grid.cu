@@ -193,6 +193,15 @@ __global__ void k_sort_points(const float4* __restrict__ ref, int64_t M, const i
     }
 }
 
+// Cell coordinates of cell id c (x fastest).  Grids hold at most kMaxCells
+// (2^23) cells, so the decode runs in 32-bit integer arithmetic.
+__device__ __forceinline__ void cell_xyz(const GridView& g, int64_t c, int& x, int& y, int& z) {
+    const int ci = (int)c, t = ci / g.dims.x;
+    x = ci - t * g.dims.x;
+    z = t / g.dims.y;
+    y = t - z * g.dims.y;
+}
+
 __device__ __forceinline__ float3 cell_centre(const GridView& g, int x, int y, int z) {
     return make_float3(g.origin.x + ((float)x + 0.5f) * g.cell, g.origin.y + ((float)y + 0.5f) * g.cell,
                        g.origin.z + ((float)z + 0.5f) * g.cell);
@@ -204,7 +213,8 @@ __global__ void k_seed_init(GridView g, int64_t ncells, int32_t* __restrict__ se
         const int b = g.cell_start[c], e = g.cell_start[c + 1];
         int best = -1;
         if (e > b) {
-            const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y), z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
+            int x, y, z;
+            cell_xyz(g, c, x, y, z);
             const float3 ct = cell_centre(g, x, y, z);
             float bd = FLT_MAX;
             for (int p = b; p < e; ++p) {
@@ -223,7 +233,8 @@ __global__ void k_seed_init(GridView g, int64_t ncells, int32_t* __restrict__ se
 __global__ void k_seed_step(GridView g, int64_t ncells, int k, const int32_t* __restrict__ in,
                             int32_t* __restrict__ out) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.dims.x), y = (int)((c / g.dims.x) % g.dims.y), z = (int)(c / ((int64_t)g.dims.x * g.dims.y));
+        int x, y, z;
+        cell_xyz(g, c, x, y, z);
         const float3 ct = cell_centre(g, x, y, z);
         int best = in[c];
         float bd = best >= 0 ? dist2(g.sorted[best], ct) : FLT_MAX;
