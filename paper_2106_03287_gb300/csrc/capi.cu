@@ -335,7 +335,7 @@ int sicp_create(sicp_ctx** out, int device, void* cuda_stream) {
     }
     c->graphs = new GraphCache();
     if (kernel_attrs_init() != cudaSuccess || surrogate_kernel_attrs() != cudaSuccess ||
-        bf16_kernel_attrs() != cudaSuccess) {
+        bf16_kernel_attrs() != cudaSuccess || minibatch_kernel_attrs() != cudaSuccess) {
         cudaGetLastError();
         sicp_destroy(c);
         return SICP_ECUDA;

@@ -357,6 +357,7 @@ size_t scan_sums_size(int64_t n);
 cudaError_t launch_exclusive_scan(const int32_t* in, int64_t n, int32_t* out, int32_t* sums, cudaStream_t s);
 // one-time kernel attributes (dynamic shared memory opt-in)
 cudaError_t kernel_attrs_init();
+cudaError_t minibatch_kernel_attrs();   // dynamic shared memory of the minibatch kernels
 
 cudaError_t launch_minibatch(uint64_t seed, int64_t t0, int32_t T, int64_t N, int32_t m,
                              int32_t* out, cudaStream_t s);

@@ -51,9 +51,13 @@ def _nn_ok(ref, q, idx_gpu, rel=1e-6):
 
 # ---------------------------------------------------------------- step 1: minibatch
 
+# rows of at most 12,288 keys keep their keys in shared memory (12,288 / 12,289 straddle it); m = N
+# and small N switch the first pass's cut off or leave it few keys
 @pytest.mark.parametrize("seed,t0,T,N,m", [(0, 0, 4, 500, 100), (7, 3, 3, 10_000, 300),
                                            (2 ** 63 + 1, 10, 2, 111_123, 500), (5, 0, 2, 50, 50),
-                                           (9, 0, 3, 1000, 1), (11, 149, 1, 10_000, 300)])
+                                           (9, 0, 3, 1000, 1), (11, 149, 1, 10_000, 300),
+                                           (3, 0, 2, 12_288, 400), (4, 5, 2, 12_289, 400),
+                                           (6, 0, 1, 3000, 3000), (8, 2, 2, 64, 1)])
 def test_minibatch_bit_exact(ctx, seed, t0, T, N, m):
     got = S.sicp_minibatch(ctx, seed, t0, T, N, m)
     for r in range(T):
