@@ -488,7 +488,12 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         unsigned bi = kNoIdx;
         float4 bp = make_float4(0.f, 0.f, 0.f, 0.f);
 
+        // the radius N_t of the next tile is loaded one step ahead, so that its
+        // round trip overlaps the barrier and the MMA wait of the current step
+        float nt_next = T > 0 ? __ldg(a.nmax + tile_at(0)) : 0.f;
         for (int t = 0; t < T; ++t) {
+            const float nt = nt_next;
+            if (t + 1 < T) nt_next = __ldg(a.nmax + tile_at(t + 1));
             // tile t + 1 has landed (the kAhead - 1 newer groups may still be in
             // flight); its slot is published and its MMA issued
             if (t + 1 < T) {
@@ -519,7 +524,6 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             tmem_ld16_min(tb + 48, r + 48, g[3]);
             tmem_wait_ld();
             const int rt = tile_at(t);
-            const float nt = __ldg(a.nmax + rt);
             const float E = fmaf(aq, nt, fmaf(kEpsRR * nt, nt, eq));
             const float cm = min3f(g[0], g[1], fminf(g[2], g[3]));
             u = fminf(u, cm + E);
