@@ -533,22 +533,28 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                 const int lim = a.M - rt * kRCols - col0;   // columns from lim on are padding
                 const float4* pts =
                     reinterpret_cast<const float4*>(sm + sRing + (t % kSlots) * kSlotBytes + kTileBytes);
+                // the lane's candidates as a bit mask first, then one exact check per
+                // set bit: a warp runs as many checks as its busiest lane has
+                // candidates, not one per column that any lane flags
+                unsigned long long cmask = 0ull;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (g[i] > thr) continue;   // no candidate in this run
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int j = 16 * i + jj;
-                        if (r[j] <= thr && j < lim) {
-                            const float4 r4 = pts[col0 + j];
-                            const float d = dist2(r4, q);
-                            const unsigned id = __float_as_uint(r4.w);
-                            if (better_u(d, id, bd, bi)) {
-                                bd = d;
-                                bi = id;
-                                bp = r4;
-                            }
-                        }
+                    for (int jj = 0; jj < 16; ++jj)
+                        if (r[16 * i + jj] <= thr) cmask |= 1ull << (16 * i + jj);
+                }
+                if (lim < 64) cmask &= lim > 0 ? (1ull << lim) - 1ull : 0ull;
+                while (cmask) {
+                    const int j = __ffsll((long long)cmask) - 1;
+                    cmask &= cmask - 1ull;
+                    const float4 r4 = pts[col0 + j];
+                    const float d = dist2(r4, q);
+                    const unsigned id = __float_as_uint(r4.w);
+                    if (better_u(d, id, bd, bi)) {
+                        bd = d;
+                        bi = id;
+                        bp = r4;
                     }
                 }
             }
