@@ -332,9 +332,14 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // publish tile t's slot and, from thread 0, issue its MMA
-    auto issue_mma = [&](int t) {
+    // publish tile t's slot and, from thread 0, issue its MMA.  With wait_prev, thread 0 first waits
+    // for the MMA of tile t - 1, so that after the barrier every warp may read its accumulators.
+    auto issue_mma = [&](int t, bool wait_prev) {
         tc::fence_async_shared();
+        if (wait_prev && tid == 0 && !s_fail) {
+            const int64_t Np = N0 + t - 1;
+            if (!bwait(&tfull[Np & 1], (uint32_t)((Np >> 1) & 1), a.err, a.polls)) s_fail = 1;
+        }
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         // ---- prologue: tiles 0 .. kAhead in flight, tile 0 landed and its MMA issued
         for (int t = 0; t <= kAhead; ++t) fetch(t);
         asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
-        issue_mma(0);
+        issue_mma(0, false);
         const float4 q4 = qrow[row];
         const float3 q = make_float3(q4.x, q4.y, q4.z);
         const float qn = q4.w;
@@ -495,10 +500,12 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             const float nt = nt_next;
             if (t + 1 < T) nt_next = __ldg(a.nmax + tile_at(t + 1));
             // tile t + 1 has landed (the kAhead - 1 newer groups may still be in
-            // flight); its slot is published and its MMA issued
-            if (t + 1 < T) {
+            // flight); its slot is published and its MMA issued, and the MMA of
+            // tile t is complete (thread 0 waited for it before the barrier)
+            const bool last = t + 1 >= T;
+            if (!last) {
                 asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory");
-                issue_mma(t + 1);
+                issue_mma(t + 1, true);
             }
             // the slot of tile t + 1 + kAhead last held tile t + 1 + kAhead - kSlots = t - 1,
             // consumed before the barrier above
@@ -507,12 +514,16 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
             // ---- accumulators of tile t: warp w reads rows 32 (w % 4) .. + 31, columns of quarter w / 4
             const int64_t N = N0 + t;
             const int b = (int)(N & 1);
-            int ok = 1;
-            if (lane == 0) ok = s_fail ? 0 : bwait(&tfull[b], (uint32_t)((N >> 1) & 1), a.err, a.polls);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            tc::fence_after_sync();
-            if (!ok) {
-                if (lane == 0) s_fail = 1;
+            if (last) {   // no barrier in this step: each warp waits for the MMA itself
+                int ok = 1;
+                if (lane == 0) ok = s_fail ? 0 : bwait(&tfull[b], (uint32_t)((N >> 1) & 1), a.err, a.polls);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                tc::fence_after_sync();
+                if (!ok) {
+                    if (lane == 0) s_fail = 1;
+                    continue;
+                }
+            } else if (s_fail) {
                 continue;
             }
             const uint32_t tb = tmem + (uint32_t)(b * kRCols + qtr * kQuarter) + ((uint32_t)(32 * rq) << 16);
