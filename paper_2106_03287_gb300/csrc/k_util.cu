@@ -180,9 +180,16 @@ __global__ void __launch_bounds__(kGbarThreads) k_qterms_to_gbar(const float* __
     }
     const int e = t / 6, c = t % 6;
     const float* row = qterms + (int64_t)j * m * 6;
+    // up to 16 values in flight per thread, then added in the order of k
     float acc = 0.f;
-#pragma unroll 4
-    for (int k = e; k < m; k += 32) acc += __ldg(row + 6 * k + c);
+    for (int k0 = e; k0 < m; k0 += 32 * 16) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = k0 + 32 * i < m ? __ldg(row + 6 * (k0 + 32 * i) + c) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (k0 + 32 * i < m) acc += v[i];
+    }
     part[c][e] = acc;
     __syncthreads();
     const int w = t >> 5, lane = t & 31;

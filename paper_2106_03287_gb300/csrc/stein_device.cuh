@@ -483,6 +483,15 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
     for (int idx = tid; idx < 6 * K; idx += blockDim.x) th[idx] = __ldcg(a.theta + idx);
     __syncthreads();
     const Team T = {0, (int)blockDim.x, 1};
+    // the Adam moments of this thread's first component (also from the previous Stein step)
+    const int e0 = 3 * i0 + tid;
+    const bool has0 = e0 < 3 * i1;
+    const int idx0 = 6 * (e0 / 3) + c0 + e0 % 3;
+    float am0 = 0.f, av0 = 0.f;
+    if (has0) {
+        am0 = __ldcg(a.adam_m + idx0);
+        av0 = __ldcg(a.adam_v + idx0);
+    }
     float med = 0.f;
     const float h = bandwidth(T, th, K, b, D, cached, hist, s_u, wsum, m_prev, bracket, &med);
     const float inv_h = 1.f / h, two_h = 2.f / h;
@@ -586,8 +595,9 @@ __device__ __forceinline__ void stein_adam_one_block(const SteinArgs& a, int b, 
         const float phi = Ph[idx];
         if (a.out_phi) a.out_phi[idx] = phi;
         const float g = -phi;
-        const float mo = fmaf(a.beta1, a.adam_m[idx], omb1 * g);
-        const float ve = fmaf(a.beta2, a.adam_v[idx], omb2 * g * g);
+        const bool first = e == e0;   // moments loaded before the wait
+        const float mo = fmaf(a.beta1, first ? am0 : __ldcg(a.adam_m + idx), omb1 * g);
+        const float ve = fmaf(a.beta2, first ? av0 : __ldcg(a.adam_v + idx), omb2 * g * g);
         a.adam_m[idx] = mo;
         a.adam_v[idx] = ve;
         const float mh = mo / c1, vh = ve / c2;
