@@ -88,7 +88,12 @@ __host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t s, uint64_t k) {
 // The registration loop chains gradient -> reduction -> Stein step -> next
 // gradient this way.  The gradient kernels trigger only after their own wait,
 // so a Stein step is never scheduled before the previous Stein step has
-// completed, which lets it read the particles before its own wait.
+// completed, which lets it read the particles before its own wait.  Only the
+// reduction triggers before its wait; every other kernel triggers after it, so
+// when a kernel starts, every kernel at least three launches earlier in the
+// stream has completed.  The minibatch rows and the packed source points are
+// written before the chain starts (and never inside it), so the grid gradient
+// kernel reads them before its wait.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

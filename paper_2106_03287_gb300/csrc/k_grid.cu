@@ -111,13 +111,15 @@ __global__ void __launch_bounds__(kGradThreads, 12) k_grad_grid(GradArgs a, cons
     const int grp = threadIdx.x / G, lane = threadIdx.x & (G - 1);
     const int k = blockIdx.x;
     const int j0 = blockIdx.y * kPart;
+    // the minibatch entry and its source point were written before the chain of
+    // launches (see pdl_wait), so they are read before the wait
+    const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + k), a.n_src, kChkSrc));
     pdl_wait();      // the particles of the previous Stein step
     pdl_trigger();   // only after the wait: see pdl_wait
     for (int i = threadIdx.x; i < kPart; i += blockDim.x)
         if (j0 + i < a.K) make_pose(a.theta + 6 * (j0 + i), P[i]);
     __syncthreads();
     const GridSearch& S = kConst ? c_search[slot] : *Sd;
-    const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + k), a.n_src, kChkSrc));
     float3 s = make_float3(s4.x, s4.y, s4.z);
     const float reuse2 = (kReuse * S.fine.cell) * (kReuse * S.fine.cell);
     Work w;
