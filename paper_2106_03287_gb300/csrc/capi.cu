@@ -89,7 +89,7 @@ struct LoopKey {
     int64_t ref_M;          // reference size (the exhaustive kernel takes it by value)
     int64_t wait_polls;     // failure-detection check settings (the kernels take them by value)
     int32_t wait_never, pad2;
-    const void* ptrs[15];
+    const void* ptrs[16];
     bool operator==(const LoopKey& o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -362,7 +362,7 @@ void sicp_destroy(sicp_ctx* c) {
     if (c->surr) surrogate_destroy(c->surr);
     Buf* bufs[] = {&c->src4, &c->mb, &c->theta, &c->adam_m, &c->adam_v, &c->partial, &c->moments,
                    &c->flags, &c->tmp_in, &c->tmp_out, &c->tmp_aux, &c->bbox, &c->stats, &c->gbar,
-                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->resume, &c->tel,
+                   &c->bf16_tiles, &c->normals, &c->search_dev, &c->bf16_ref, &c->bf16_order, &c->bf16_q, &c->resume, &c->tel,
                    &c->tel_nn, &c->tel_part};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
@@ -474,6 +474,7 @@ int sicp_nn(sicp_ctx* ctx, const float* q, int64_t n, int32_t mode, int32_t* out
         SICP_CUDA(launch_nn_grid(ctx->search, (const float*)d_q, n, d_idx, d_d2, stats_ptr(ctx), ctx->stream));
     } else if (mode == SICP_NN_BRUTE_BF16) {
         if ((rc = bf16_prepare(ctx))) return rc;
+        if ((rc = bf16_queries(ctx, n))) return rc;
         SICP_CUDA(launch_nn_bf16(ctx, (const float*)d_q, n, d_idx, d_d2, (int*)ctx->flags.p + 3));
     } else {
         SICP_CUDA(launch_nn_brute(ctx->ref4, ctx->M, (const float*)d_q, n, d_idx, d_d2, ctx->stream));
@@ -539,6 +540,7 @@ int sicp_icp_grad(sicp_ctx* ctx, const float* src_xyz, int64_t N, const int32_t*
         return rc;
     if (surr && (rc = surrogate_prepare(ctx, (int64_t)K * m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
+    if (bf && (rc = bf16_queries(ctx, (int64_t)K * m))) return rc;
     if ((rc = ensure(ctx, ctx->tmp_out, (sizeof(float) * 6 + sizeof(int32_t) * (size_t)m) * K))) return rc;
     float* d_g = (float*)ctx->tmp_out.p;
     int32_t* d_nn = (int32_t*)((char*)ctx->tmp_out.p + sizeof(float) * 6 * K);
@@ -740,6 +742,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     if ((rc = ensure(ctx, ctx->gbar, b_th + 4 * sizeof(float)))) return rc;   // + the two blocks' medians
     if (surr_T > 0 && (rc = surrogate_prepare(ctx, (int64_t)K * p.m))) return rc;
     if (bf && (rc = bf16_prepare(ctx))) return rc;
+    if (bf && (rc = bf16_queries(ctx, (int64_t)K * p.m))) return rc;
     const bool tel = ctx->telemetry;
     ctx->tel_rows = 0;
     if (tel) {
@@ -820,6 +823,7 @@ int register_run(sicp_ctx* ctx, const float* src_xyz, int64_t N, const float* pa
     key.ptrs[12] = tel ? ctx->tel.p : nullptr;
     key.ptrs[13] = tel ? ctx->tel_nn.p : nullptr;
     key.ptrs[14] = tel ? ctx->tel_part.p : nullptr;
+    key.ptrs[15] = bf ? ctx->bf16_q.p : nullptr;   // the tensor-core search's query buffers
 
     GraphCache& gc = *ctx->graphs;
     GraphSlot& slot = gc.slot[stride > 0 ? gc.next : 0];

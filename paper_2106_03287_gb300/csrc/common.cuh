@@ -293,6 +293,8 @@ struct sicp_ctx {
     float3 bf16_centre = {0, 0, 0};
     int bf16_R = 0;                      // reference tiles of 256 points
     sicp::Buf bf16_ref;                  // device copy of what the tensor-core search reads of the reference
+    sicp::Buf bf16_order;                // the reference in brick order, its offsets and the query-key counters
+    sicp::Buf bf16_q;                    // a launch's queries, keyed and in key order
     sicp::Surrogate* surr = nullptr;     // learned closest-point field, created on first use
     uint64_t surr_gen = 0;               // bumped whenever the surrogate's weights or normalisation change
     sicp::Buf search_dev;                // device copy of `search`, rewritten by every reference build
@@ -469,6 +471,7 @@ cudaError_t surrogate_launch_grad(sicp_ctx* ctx, const float4* src, const int32_
 // (k_nn_bf16.cu); same results as launch_nn_brute / the fp32 gradient.
 cudaError_t bf16_kernel_attrs();
 int bf16_prepare(sicp_ctx* ctx);   // reference tiles of the current reference (needs the grid)
+int bf16_queries(sicp_ctx* ctx, int64_t Q);   // a launch's query buffers (before any capture)
 // err: set when a bounded wait gave up
 cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* idx, float* d2, int* err);
 // per-query gradient terms into qterms [K][m][6], then gbar [K][6]; out_nn [K][m] or null;

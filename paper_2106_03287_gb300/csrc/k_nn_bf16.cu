@@ -39,9 +39,10 @@
 // same order as before.
 //
 // Pipeline per CTA (one 128-query tile at a time, persistent over tiles, one
-// CTA per SM, query tiles taken from a counter; the sweep starts at the reference tile holding the
+// CTA per SM, query tiles taken from a counter; the queries in key order and the reference points
+// in brick order, both described below; the sweep starts at the reference tile holding the
 // grid cell of the tile's first query and wraps around): the 16 warps copy each reference tile (8 KB, precomputed per
-// reference cloud in the spatially sorted order of the voxel grid) and its 256
+// reference cloud) and its 256
 // fp32 points into a shared-memory ring with asynchronous 16-byte copies,
 // three tiles ahead; thread 0 issues a landed tile's MMA into one of two
 // 256-column tensor-memory buffers while the warps read the other (four warps
@@ -86,6 +87,9 @@ constexpr int sList = sXP + 3 * kQRows * 16;          // uint16 [kMaxList]: the 
 constexpr int kBfSmemUsed = sList + kMaxList * 2;
 constexpr float kBoxRel = 1e-6f;                      // box gaps shrink by this x the coordinate magnitudes
 constexpr float kSkipRel = 1e-5f;                     // a tile is skipped only if its bound beats U by this
+constexpr int kBrick = 8;                             // fine cells per brick edge (reference order)
+constexpr int kQCell = 4;                             // fine cells per query-key cell edge
+constexpr int kOrderMinTiles = 32;                    // queries put in key order from this many reference tiles
 // Launched with more shared memory than it uses so that no two CTAs share an
 // SM: each holds all 512 tensor-memory columns for its whole life.
 constexpr int kBfSmem = 120 * 1024;
@@ -107,7 +111,7 @@ __device__ __forceinline__ void store_row16(unsigned char* tile, int row, const 
 }
 
 // The B operand of every reference tile (tile t at out + t * kTileBytes) from
-// the grid's sorted points, and N_t = the largest |r'| of each tile (nmax,
+// the points in brick order, and N_t = the largest |r'| of each tile (nmax,
 // zeroed beforehand; non-negative floats order like their bit patterns).
 __global__ void k_bf16_btiles(const float4* __restrict__ sorted, int M, float3 c, int R,
                               unsigned char* __restrict__ out, unsigned* __restrict__ nmax) {
@@ -176,9 +180,20 @@ struct BfRef {
     int M, R;                  // points, tiles of 256
     const unsigned char* btiles;
     const float* nmax;         // [R]
-    GridView grid;             // the fine grid: where each cell's points start in `sorted`
+    GridView grid;             // the fine grid: its seed map and the cells of the queries
     const float4* tbox;        // [R][2]: each tile's bounding box (lo, hi)
     const float* amax;         // largest coordinate magnitude of the cloud
+    // brick order: the fine cells in bricks of kBrick^3 (bricks x fastest, then the cells of a brick
+    // x fastest); the reference tiles hold the points in this order
+    const float4* bsorted;     // [M] the points in brick order (w = original index)
+    const int32_t* bbase;      // [bricks + 1] first position of each brick in bsorted
+    const int32_t* loc_off;    // [cells] position of each cell's first point within its brick
+    int3 nb;                   // bricks per axis
+    // query keys: cells of kQCell^3 fine cells in bricks of 2^3, ordered like the reference
+    int3 qd, qnb;              // key cells and key bricks per axis
+    int nqkeys;
+    int32_t* qcnt;             // [nqkeys] queries per key (zero between launches)
+    int32_t* qstart;           // [nqkeys] first position of each key in key order
     // query-tile scheduling of a launch: next tile, CTAs done (zero between launches: written as
     // zeros with the description, and the last CTA of every launch zeroes them again)
     unsigned long long sched[2];
@@ -198,8 +213,8 @@ struct BfArgs {
     float3 c;
     const unsigned char* btiles;
     const float* nmax;         // [R]
-    const float4* sorted;
-    GridView grid;             // the fine grid: where each cell's points start in `sorted`
+    const float4* sorted;      // the points in brick order (the tiles' fp32 points)
+    GridView grid;             // the fine grid: its seed map and the cells of the queries
     const float4* tbox;
     float amax;
     int M, R;
@@ -212,6 +227,12 @@ struct BfArgs {
     unsigned long long* stats; // work counters or null: [8] query tiles, [9] reference tiles swept
     long long polls;           // polls of an mbarrier wait before it gives up (0: kPolls)
     int never;                 // failure-detection check: first wait on an mbarrier nothing arrives on
+    // the launch's queries in key order: qtmp / qkr by query index (the query; its key and its
+    // rank among the queries of that key), qs by position in key order (w = query index); qs null:
+    // the queries in their own order, computed by the search
+    float4* qtmp;
+    int2* qkr;
+    float4* qs;
 };
 
 // Wait for phase `parity` of the mbarrier; false (and the error flag set)
@@ -259,6 +280,131 @@ __device__ __forceinline__ bool better_u(float d, unsigned i, float bd, unsigned
     return d < bd || (d == bd && i < bi);
 }
 
+// ---------------------------------------------------------------- brick order
+// The reference tiles take the points in brick order: the fine grid's cells
+// grouped in bricks of kBrick^3 cells, bricks x fastest, then the cells of a
+// brick x fastest, each cell's points in the grid's order.  256 consecutive
+// points then fill a compact region, so a query tile's sweep reaches fewer
+// reference tiles than in the grid's row order.  The queries of a launch are
+// ordered the same way at a coarser key (bricks of 2^3 key cells of kQCell^3
+// fine cells), so a query tile is compact too.  Neither order changes any
+// result: the answer is the lowest-index minimiser whatever the tiles hold.
+
+__device__ __forceinline__ int brick_of(int x, int y, int z, int3 nb) {
+    return ((z / kBrick) * nb.y + y / kBrick) * nb.x + x / kBrick;
+}
+
+// One CTA of kBrick^3 threads per brick: each cell's offset within its brick
+// (exclusive sum of the point counts of the brick's cells before it) and the
+// brick's point count.
+__global__ void __launch_bounds__(kBrick* kBrick* kBrick) k_bf16_brick_local(GridView g, int3 nb,
+                                                                              int32_t* __restrict__ loc_off,
+                                                                              int32_t* __restrict__ bsum) {
+    constexpr int kN = kBrick * kBrick * kBrick;
+    __shared__ int wsum[kN / 32];
+    const int b = blockIdx.x, l = threadIdx.x, lane = l & 31, w = l >> 5;
+    const int x = (b % nb.x) * kBrick + l % kBrick;
+    const int y = (b / nb.x % nb.y) * kBrick + l / kBrick % kBrick;
+    const int z = (b / nb.x / nb.y) * kBrick + l / (kBrick * kBrick);
+    const bool in = x < g.dims.x && y < g.dims.y && z < g.dims.z;
+    const int64_t c = in ? ((int64_t)z * g.dims.y + y) * g.dims.x + x : 0;
+    const int cnt = in ? g.cell_start[c + 1] - g.cell_start[c] : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int k = 0; k < w; ++k) base += wsum[k];
+    if (in) loc_off[c] = base + incl - cnt;
+    if (l == kN - 1) bsum[b] = base + incl;
+}
+
+// Each point of the grid's order to its place in brick order.
+__global__ void k_bf16_brick_scatter(GridView g, const int32_t* __restrict__ cell_of, int3 nb,
+                                     const int32_t* __restrict__ bbase, const int32_t* __restrict__ loc_off, int M,
+                                     float4* __restrict__ bsorted) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 r = g.sorted[p];
+        const int c = cell_of[SICP_IDX(__float_as_int(r.w), M, kChkRef)];
+        const int x = c % g.dims.x, y = c / g.dims.x % g.dims.y, z = c / g.dims.x / g.dims.y;
+        const int64_t pos = (int64_t)bbase[brick_of(x, y, z, nb)] + loc_off[c] + (p - g.cell_start[c]);
+        if (pos >= 0 && pos < M) bsorted[SICP_IDX(pos, M, kChkSorted)] = r;
+    }
+}
+
+// Query g of a launch: R_j s_k + u_j for (k, j) = (g / K, g % K) in a
+// registration iteration, else the given point.
+__device__ __forceinline__ float3 bf_query(const BfArgs& a, int64_t g) {
+    if (a.grad) {
+        const int k = (int)(g / a.K), j = (int)(g % a.K);
+        Pose P;
+        make_pose(a.theta + 6 * j, P);
+        const float4 s4 = __ldg(a.src + SICP_IDX(__ldg(a.mb + (int64_t)j * a.mb_stride + k), a.n_src, kChkSrc));
+        return apply_pose(P, make_float3(s4.x, s4.y, s4.z));
+    }
+    return make_float3(a.q[3 * g], a.q[3 * g + 1], a.q[3 * g + 2]);
+}
+
+__device__ __forceinline__ int query_key(const GridView& g, int3 qnb, float3 q) {
+    const int x = cell_coord(q.x, g.origin.x, g.inv_cell, g.dims.x) / kQCell;
+    const int y = cell_coord(q.y, g.origin.y, g.inv_cell, g.dims.y) / kQCell;
+    const int z = cell_coord(q.z, g.origin.z, g.inv_cell, g.dims.z) / kQCell;
+    return (((z >> 1) * qnb.y + (y >> 1)) * qnb.x + (x >> 1)) * 8 + (z & 1) * 4 + (y & 1) * 2 + (x & 1);
+}
+
+// The launch's queries, their keys, and their ranks among the queries of a key.
+__global__ void __launch_bounds__(256) k_bf16_qkey(BfArgs a, int64_t Q) {
+    const BfRef* r = a.ref;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Q) return;
+    const float3 q = bf_query(a, g);
+    const int key = query_key(r->grid, r->qnb, q);
+    a.qtmp[g] = make_float4(q.x, q.y, q.z, 0.f);
+    a.qkr[g] = make_int2(key, atomicAdd(r->qcnt + key, 1));
+}
+
+// One CTA: qstart = exclusive sums of qcnt, and qcnt back to zero.
+__global__ void __launch_bounds__(1024) k_bf16_qscan(const BfRef* __restrict__ r) {
+    __shared__ int wsum[32];
+    const int n = r->nqkeys, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (n + 1023) / 1024;
+    const int b = min(n, t * per), e = min(n, b + per);
+    int32_t* cnt = r->qcnt;
+    int s = 0;
+    for (int i = b; i < e; ++i) s += cnt[i];
+    int incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int run = incl - s;
+    for (int k = 0; k < w; ++k) run += wsum[k];
+    for (int i = b; i < e; ++i) {
+        const int c = cnt[i];
+        r->qstart[i] = run;
+        run += c;
+        cnt[i] = 0;
+    }
+}
+
+// Query g to its position in key order (qs[pos].w = g).
+__global__ void __launch_bounds__(256) k_bf16_qscatter(BfArgs a, int64_t Q) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Q) return;
+    const int2 kr = a.qkr[g];
+    const int64_t pos = (int64_t)a.ref->qstart[kr.x] + kr.y;
+    const float4 q = a.qtmp[g];
+    // (always in range: the counts start at zero and each query took one rank of its key)
+    if (pos >= 0 && pos < Q) a.qs[SICP_IDX(pos, Q, kChkSorted)] = make_float4(q.x, q.y, q.z, __int_as_float((int)g));
+}
+
 __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     pdl_wait();      // the particles of the previous Stein step (and the reference description)
     pdl_trigger();   // only after the wait: see pdl_wait
@@ -271,7 +417,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
         a.btiles = r->btiles;
         a.nmax = r->nmax;
         a.grid = r->grid;
-        a.sorted = r->grid.sorted;
+        a.sorted = r->bsorted;
         a.tbox = r->tbox;
         a.amax = *r->amax;
     }
@@ -358,25 +504,26 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
     const bool dyn = ntiles > (int64_t)gridDim.x;
     if (tid == 0) s_tile = skip ? ntiles : dyn ? (long long)atomicAdd(sched, 1ull) : (long long)blockIdx.x;
     __syncthreads();
+    int64_t g_row = Q;   // query index of row tid (tid < kQRows) of the current query tile
     for (int64_t tile = s_tile; tile < ntiles && !skip; tile = s_tile) {
-        // ---- A operand and the fp32 queries of this tile.  In a registration
-        // iteration the rows go minibatch-major (the K particles' images of one
-        // source point are neighbours), which keeps a tile's queries close.
+        // ---- A operand and the fp32 queries of this tile: the rows in key order, each with its
+        // query index g (padding rows: g = Q), kept by the thread that writes the row's result
         if (tid < kQRows) {
-            const int64_t g = tile * kQRows + tid;
+            const int64_t gp = tile * kQRows + tid;
             float3 q = make_float3(0.f, 0.f, 0.f);
-            if (g < Q) {
-                if (a.grad) {
-                    const int k = (int)(g / a.K), j = (int)(g % a.K);
-                    Pose P;
-                    make_pose(a.theta + 6 * j, P);
-                    const float4 s4 =
-                        __ldg(a.src + SICP_IDX(__ldg(a.mb + (int64_t)j * a.mb_stride + k), a.n_src, kChkSrc));
-                    q = apply_pose(P, make_float3(s4.x, s4.y, s4.z));
-                } else {
-                    q = make_float3(a.q[3 * g], a.q[3 * g + 1], a.q[3 * g + 2]);
+            int64_t g = Q;
+            if (gp < Q) {
+                if (a.qs) {
+                    const float4 e = a.qs[gp];
+                    q = make_float3(e.x, e.y, e.z);
+                    g = __float_as_int(e.w);
+                    if (g < 0 || g >= Q) g = Q;
+                } else {   // a small reference: the queries in their own order
+                    q = bf_query(a, gp);
+                    g = gp;
                 }
             }
+            g_row = g;
             const float p[3] = {q.x - a.c.x, q.y - a.c.y, q.z - a.c.z};
             const float n2 = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
             qrow[tid] = make_float4(q.x, q.y, q.z, sqrtf(n2));
@@ -421,8 +568,10 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                 const int cx = cell_coord(q.x, G.origin.x, G.inv_cell, G.dims.x);
                 const int cy = cell_coord(q.y, G.origin.y, G.inv_cell, G.dims.y);
                 const int cz = cell_coord(q.z, G.origin.z, G.inv_cell, G.dims.z);
-                const int32_t start = __ldg(G.cell_start + ((int64_t)cz * G.dims.y + cy) * G.dims.x + cx);
-                s_rot = min(start / kRCols, a.R - 1);
+                const BfRef* r = args.ref;
+                const int32_t start = __ldg(r->bbase + brick_of(cx, cy, cz, r->nb)) +
+                                      __ldg(r->loc_off + ((int64_t)cz * G.dims.y + cy) * G.dims.x + cx);
+                s_rot = max(0, min(start / kRCols, a.R - 1));
             }
         }
         __syncthreads();
@@ -589,7 +738,7 @@ __global__ void __launch_bounds__(kBfThreads, 1) k_nn_bf16(BfArgs args) {
                     bp = xp[o * kQRows + row];
                 }
             }
-            const int64_t g = tile * kQRows + row;
+            const int64_t g = g_row;   // this thread set up the row (row == tid for qtr == 0)
             const bool found = !s_fail && bi != kNoIdx;
             if (g < Q) {
                 if (a.grad) {
@@ -655,13 +804,49 @@ int bf16_prepare(sicp_ctx* ctx) {
     unsigned* nmax = (unsigned*)((char*)ctx->bf16_tiles.p + tiles_bytes);
     unsigned* amax = nmax + R;
     float4* tbox = (float4*)((char*)ctx->bf16_tiles.p + box_off);
+
+    // brick order of the fine grid's cells, and the query keys
+    const GridView& gv = ctx->grid.v;
+    const int3 d = gv.dims;
+    const int3 nb = make_int3((d.x + kBrick - 1) / kBrick, (d.y + kBrick - 1) / kBrick, (d.z + kBrick - 1) / kBrick);
+    const int64_t nbricks = (int64_t)nb.x * nb.y * nb.z;
+    const int64_t ncells = (int64_t)d.x * d.y * d.z;
+    const int3 qd = make_int3((d.x + kQCell - 1) / kQCell, (d.y + kQCell - 1) / kQCell, (d.z + kQCell - 1) / kQCell);
+    const int3 qnb = make_int3((qd.x + 1) / 2, (qd.y + 1) / 2, (qd.z + 1) / 2);
+    const int64_t nqkeys = (int64_t)qnb.x * qnb.y * qnb.z * 8;
+    // bf16_order: bsorted [M], loc_off [cells], bsum [bricks], bbase [bricks + 1], scan scratch,
+    // qcnt [keys], qstart [keys] (each part 16-byte aligned)
+    auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t o_loc = al(sizeof(float4) * (size_t)ctx->M);
+    const size_t o_bsum = o_loc + al(sizeof(int32_t) * (size_t)ncells);
+    const size_t o_bbase = o_bsum + al(sizeof(int32_t) * (size_t)nbricks);
+    const size_t o_sums = o_bbase + al(sizeof(int32_t) * ((size_t)nbricks + 1));
+    const size_t o_qcnt = o_sums + al(sizeof(int32_t) * scan_sums_size(nbricks));
+    const size_t o_qstart = o_qcnt + al(sizeof(int32_t) * (size_t)nqkeys);
+    if ((rc = ensure(ctx, ctx->bf16_order, o_qstart + al(sizeof(int32_t) * (size_t)nqkeys)))) return rc;
+    char* ob = (char*)ctx->bf16_order.p;
+    float4* bsorted = (float4*)ob;
+    int32_t* loc_off = (int32_t*)(ob + o_loc);
+    int32_t* bsum = (int32_t*)(ob + o_bsum);
+    int32_t* bbase = (int32_t*)(ob + o_bbase);
+    int32_t* sums = (int32_t*)(ob + o_sums);
+    int32_t* qcnt = (int32_t*)(ob + o_qcnt);
+    int32_t* qstart = (int32_t*)(ob + o_qstart);
+    SICP_CUDA(cudaMemsetAsync(qcnt, 0, sizeof(int32_t) * (size_t)nqkeys, ctx->stream));
+    k_bf16_brick_local<<<(unsigned)nbricks, kBrick * kBrick * kBrick, 0, ctx->stream>>>(gv, nb, loc_off, bsum);
+    SICP_CUDA(cudaGetLastError());
+    SICP_CUDA(launch_exclusive_scan(bsum, nbricks, bbase, sums, ctx->stream));
+    k_bf16_brick_scatter<<<(unsigned)((ctx->M + 255) / 256), 256, 0, ctx->stream>>>(
+        gv, ctx->grid.cell_of, nb, bbase, loc_off, (int)ctx->M, bsorted);
+    SICP_CUDA(cudaGetLastError());
+
     SICP_CUDA(cudaMemsetAsync(nmax, 0, sizeof(float) * ((size_t)R + 1), ctx->stream));
     const int64_t rows = (int64_t)R * kRCols;
     k_bf16_btiles<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->grid.v.sorted, (int)ctx->M, c, R, (unsigned char*)ctx->bf16_tiles.p, nmax);
+        bsorted, (int)ctx->M, c, R, (unsigned char*)ctx->bf16_tiles.p, nmax);
     SICP_CUDA(cudaGetLastError());
-    k_bf16_tbox<<<(unsigned)(((int64_t)R * 32 + 255) / 256), 256, 0, ctx->stream>>>(ctx->grid.v.sorted, (int)ctx->M,
-                                                                                  R, tbox, amax);
+    k_bf16_tbox<<<(unsigned)(((int64_t)R * 32 + 255) / 256), 256, 0, ctx->stream>>>(bsorted, (int)ctx->M, R, tbox,
+                                                                                  amax);
     SICP_CUDA(cudaGetLastError());
     ctx->bf16_centre = c;
     ctx->bf16_R = R;
@@ -674,6 +859,15 @@ int bf16_prepare(sicp_ctx* ctx) {
     h.grid = ctx->grid.v;
     h.tbox = tbox;
     h.amax = (const float*)amax;
+    h.bsorted = bsorted;
+    h.bbase = bbase;
+    h.loc_off = loc_off;
+    h.nb = nb;
+    h.qd = qd;
+    h.qnb = qnb;
+    h.nqkeys = (int)nqkeys;
+    h.qcnt = qcnt;
+    h.qstart = qstart;
     h.sched[0] = h.sched[1] = 0ull;
     if ((rc = ensure(ctx, ctx->bf16_ref, sizeof(BfRef)))) return rc;
     SICP_CUDA(cudaMemcpyAsync(ctx->bf16_ref.p, &h, sizeof(BfRef), cudaMemcpyHostToDevice, ctx->stream));
@@ -691,6 +885,31 @@ static BfArgs bf_args(sicp_ctx* ctx, int* err) {
     return a;
 }
 
+// The Q queries of a launch: qtmp [Q] float4, qs [Q] float4, qkr [Q] int2.
+int bf16_queries(sicp_ctx* ctx, int64_t Q) {
+    return ensure(ctx, ctx->bf16_q, (size_t)(Q > 0 ? Q : 1) * (2 * sizeof(float4) + sizeof(int2)));
+}
+
+// Put the launch's queries in key order (three launches; the buffers come from bf16_queries).
+// Below kOrderMinTiles reference tiles a query tile sweeps nearly all of them whatever its
+// queries, so the search takes the queries in their own order (qs null).
+static cudaError_t bf_order_queries(sicp_ctx* ctx, BfArgs& a, int64_t Q) {
+    float4* base = (float4*)ctx->bf16_q.p;
+    a.qtmp = base;
+    a.qs = nullptr;
+    a.qkr = (int2*)(base + 2 * Q);
+    if (Q <= 0 || ctx->bf16_R < kOrderMinTiles) return cudaSuccess;
+    a.qs = base + Q;
+    const unsigned blocks = (unsigned)((Q + 255) / 256);
+    k_bf16_qkey<<<blocks, 256, 0, ctx->stream>>>(a, Q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bf16_qscan<<<1, 1024, 0, ctx->stream>>>(a.ref);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bf16_qscatter<<<blocks, 256, 0, ctx->stream>>>(a, Q);
+    return cudaGetLastError();
+}
+
 static unsigned bf_grid(sicp_ctx* ctx, int64_t Q) {
     const int64_t tiles = (Q + kQRows - 1) / kQRows;
     return (unsigned)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
@@ -703,6 +922,8 @@ cudaError_t launch_nn_bf16(sicp_ctx* ctx, const float* q, int64_t n, int32_t* id
     a.n = n;
     a.out_idx = idx;
     a.out_d2 = d2;
+    const cudaError_t e = bf_order_queries(ctx, a, n);
+    if (e != cudaSuccess) return e;
     return launch_pdl(k_nn_bf16, dim3(bf_grid(ctx, n)), dim3(kBfThreads), kBfSmem, ctx->stream, a);
 }
 
@@ -721,7 +942,9 @@ cudaError_t launch_grad_bf16(sicp_ctx* ctx, const float4* src, const int32_t* mb
     a.K = K;
     a.qterms = qterms;
     a.out_idx = out_nn;
-    cudaError_t e = launch_pdl(k_nn_bf16, dim3(bf_grid(ctx, (int64_t)K * m)), dim3(kBfThreads), kBfSmem, ctx->stream, a);
+    cudaError_t e = bf_order_queries(ctx, a, (int64_t)K * m);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_nn_bf16, dim3(bf_grid(ctx, (int64_t)K * m)), dim3(kBfThreads), kBfSmem, ctx->stream, a);
     if (e != cudaSuccess) return e;
     return launch_qterms_to_gbar(qterms, K, m, 1.f / (float)m, gbar, nullptr, ctx->stream);
 }
