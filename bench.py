@@ -588,8 +588,9 @@ def run_ours(args):
         mma_flops = 2.0 * 16 * 128 * 256 * (rtiles / cfg["T"]) if qtiles else 2.0 * 16 * queries_per_launch * 256 * R
         alg_flops = 2.0 * 4 * queries_per_launch * M
         achieved = alg_flops / (grad_ms * 1e-3) / 1e12 if grad_ms else None
-        roofline = {"kernel": "k_nn_bf16 (transform + tensor-core distance tiles + fp32 re-check + gradient terms) "
-                              "and the per-particle reduction, one iteration", "bound": "tensor",
+        roofline = {"kernel": "k_nn_bf16 (tensor-core distance tiles + fp32 re-check + gradient terms), the "
+                              "three launches that put the queries in key order (from 32 reference tiles) and the "
+                              "per-particle reduction, one iteration", "bound": "tensor",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "peak_kind": f"{peak_kind} dense bf16 (burst)",
                     "frac": achieved / peak if achieved else None, "traffic": None,
                     "algorithmic_flops_per_launch": alg_flops,
